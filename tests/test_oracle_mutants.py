@@ -1,0 +1,103 @@
+"""The pins have teeth: plausible mistakes planted in copies of the oracle
+source (dropped terms, wrong signs or indices, transposed operands, a
+missing conjugate) are each caught by at least one pin.
+
+Each mutant is a textual substitution applied to a temporary copy of the
+oracle; the oracle in the repository is never modified.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+
+import pytest
+
+import oracle
+from oracle import build as obuild
+from tests import test_oracle_pins as P
+
+BODY = "mlb_oracle_body.h"
+MAIN = "mlb_oracle.c"
+
+# (name, file, original text, planted mistake)
+MUTANTS = [
+    ("beta_tilde_sign", BODY, "S bt = -e / c[i];", "S bt = e / c[i];"),
+    ("q_sweep_wrong_c", BODY,
+     "bt = -SFX(dot)(N, Q + (int64_t)s * N, wi, ops) / c[s];",
+     "bt = -SFX(dot)(N, Q + (int64_t)s * N, wi, ops) / c[s - 1];"),
+    ("omega_mul_not_div", BODY, "g[i] = z[i] - g[i] / omega;",
+     "g[i] = z[i] - g[i] * omega;"),
+    ("f_sweep_uses_q", BODY,
+     "S beta = -SFX(dot)(N, F + (int64_t)s * N, gi, ops) / c[s];",
+     "S beta = -SFX(dot)(N, Q + (int64_t)s * N, gi, ops) / c[s];"),
+    ("ahq_not_transposed", BODY, "f[ci[k]] += CONJ(av[k]) * q[r];",
+     "f[r] += CONJ(av[k]) * q[ci[k]];"),
+    ("dot_without_conj", BODY, "s += CONJ(u[i]) * v[i];", "s += u[i] * v[i];"),
+    ("dropped_g_term", BODY,
+     "SFX(axpy)(N, bt, G + (int64_t)s * N, gi, ops);\n                }",
+     "\n                }"),
+    ("block_end_wrong_c", BODY, "alpha = e / c[n - 1];", "alpha = e / c[0];"),
+    ("e_wrong_shadow", BODY, "e = SFX(dot)(N, Q + (int64_t)i * N, r, ops);",
+     "e = SFX(dot)(N, Q + (int64_t)(i - 1) * N, r, ops);"),
+    ("omega_inverted", BODY, "omega = zu / zz;", "omega = zz / zu;"),
+    ("kappa_inverted", BODY, "omega = omega * kappa / arho;",
+     "omega = omega * arho / kappa;"),
+    ("q_sweep_short", BODY, "for (int32_t s = i + 1; s <= n - 1; ++s) {",
+     "for (int32_t s = i + 1; s < n - 1; ++s) {"),
+    ("r_update_sign", BODY,
+     "SFX(axpy)(N, -alpha, W + (int64_t)(i - 1) * N, r, ops);",
+     "SFX(axpy)(N, alpha, W + (int64_t)(i - 1) * N, r, ops);"),
+    ("gn_truncates", MAIN, "q -= 1;", "q -= 0;"),
+    ("j0_branch_wrong_g", BODY, "SFX(xpay)(N, r, beta, G, gi, ops);",
+     "SFX(xpay)(N, r, beta, gi, gi, ops);"),
+]
+
+# fast pins, in the order they are tried
+PINS = [
+    lambda o: P.test_table_2_1_bit_exact(o),
+    lambda o: P.test_index_identity_eq_2_1(o, 3),
+    lambda o: P.test_spmv_and_ahq_match_dense_products(o),
+    lambda o: P.test_finite_termination_within_N_steps(o, 8, 8, False),
+    lambda o: P.test_finite_termination_within_N_steps(o, 6, 9, True),
+    lambda o: P.test_finite_termination_within_N_steps(o, 8, 3, False),
+    lambda o: P.test_finite_termination_within_N_steps(o, 10, 2, True),
+    lambda o: P.test_n1_matches_textbook_bicgstab(o, 300, "random"),
+    lambda o: P.test_n1_matches_textbook_bicgstab_complex(o),
+    lambda o: P.test_kappa_guard_matches_safeguarded_bicgstab(o),
+    lambda o: P.test_block0_biorthogonality(o, True),
+    lambda o: P.test_table_4_3_operation_counts_per_block(o, 4),
+    lambda o: P.test_cd2d_agrees_with_dense_lu(o, 4),
+]
+
+
+def _caught(bound) -> bool:
+    for pin in PINS:
+        try:
+            pin(bound)
+        except (AssertionError, FloatingPointError, ValueError,
+                ZeroDivisionError, OverflowError):
+            return True
+    return False
+
+
+def test_unmutated_copy_passes_every_pin(tmp_path):
+    src = tmp_path / "src"
+    shutil.copytree(os.path.dirname(oracle.__file__), src,
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    so = obuild.compile_oracle(str(src / MAIN), str(tmp_path / "orc.so"),
+                               include_dir=str(src))
+    assert not _caught(oracle.Bound(oracle.load(so)))
+
+
+@pytest.mark.parametrize("name,fname,orig,mut", MUTANTS,
+                         ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, name, fname, orig, mut):
+    src = tmp_path / "src"
+    shutil.copytree(os.path.dirname(oracle.__file__), src,
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    text = (src / fname).read_text()
+    assert text.count(orig) >= 1, f"mutation site for {name} not found"
+    (src / fname).write_text(text.replace(orig, mut, 1))
+    so = obuild.compile_oracle(str(src / MAIN), str(tmp_path / "orc.so"),
+                               include_dir=str(src))
+    assert _caught(oracle.Bound(oracle.load(so))), name
