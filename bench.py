@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark: solves/sec of ML(n)BiCGStab (plain FP64) on the 3-D 7-point
+log-normal convection-diffusion system, 128^3 unknowns, to relative
+residual 1e-10.
+
+One "step" is one complete solve from x0 = 0 (all iterations of the method,
+each an SpMV fused with shadow inner products plus the fused recurrence
+passes) through the C ABI, with b and x already in device memory.  The
+matrix (175 MB) and the solver state (> 300 MB) are larger than the 129 MB
+L2 cache, so no flush is needed between steps.
+
+Arms
+  default           the CUDA library (one persistent kernel per solve)
+  --impl reference  the CPU oracle on the host cores, on a bounded sample
+                    of iterations of the same workload, converted to
+                    solves/sec with the iteration count of a full solve
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 through
+torch.distributed.run, one rank per GPU, each rank solving its own replica
+(independent systems: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/sec and SpMV+dot HBM GB/s (% of peak) at rel. residual 1e-10"
+UNIT = "solves/s"
+
+# Workloads (the benchmark line uses DEFAULT).  `iters` is the iteration
+# count of one full solve on the GPU path, used only to convert the
+# reference arm's per-iteration sample into solves/sec.
+WORKLOADS = {
+    "cd3d128_n4_fp64": dict(m=128, n=4, tol=1e-10, maxit=40000, iters=None),
+}
+DEFAULT = "cd3d128_n4_fp64"
+
+
+def _load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _make_inputs(wl):
+    from paper_1106_3678_gb300 import workloads as W
+    A = W.cd3d_lognormal(wl["m"])
+    b = W.uniform_rhs(A.n_rows, seed=2)
+    return A, b
+
+
+def _config(wl, A, extra=None):
+    cfg = {
+        "workload": (f"cd3d_lognormal {wl['m']}^3 (N={A.n_rows:,}, nnz={A.nnz:,}), "
+                     f"n={wl['n']}, FP64, b~U[-1,1] seed 2, x0=0, Q~N(0,1) seed 0, "
+                     f"tol {wl['tol']:g}, maxit {wl['maxit']}"),
+        "N": A.n_rows, "nnz": A.nnz, "n": wl["n"], "tol": wl["tol"],
+        "maxit": wl["maxit"], "precision": "fp64",
+        "l2": "inputs larger than L2 (no flush)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(A, b, n, iters):
+    """Time `iters` iterations of the CPU oracle on the workload; returns
+    seconds per iteration (single thread)."""
+    import oracle as O
+    Q = O.q_gauss(0, A.n_rows, n)
+    t0 = time.perf_counter()
+    r = O.mlbicgstabt(A, b, np.zeros(A.n_rows), Q, iters, 0.0)
+    dt = time.perf_counter() - t0
+    return dt / max(r.iter, 1), r.iter
+
+
+def run_reference(args, wl):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    A, b = _make_inputs(wl)
+    iters_solve = wl["iters"] or args.iters_per_solve
+    sample = args.ref_iters
+    times = []
+    for s in range(args.warmup + args.steps):
+        spi, done = oracle_sample(A, b, wl["n"], sample)
+        if s >= args.warmup:
+            times.append(spi)
+    spi = statistics.median(times)
+    value = 1.0 / (spi * iters_solve) if iters_solve else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": spi * sample * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": _config(wl, A, {"iters_per_solve": iters_solve}),
+        "cpu_baseline": {
+            "value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{sample} iterations of the solve per step (single-thread C "
+                       f"oracle); solves/sec = 1/(seconds per iteration x "
+                       f"{iters_solve} iterations per full solve)")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import torch
+
+    from paper_1106_3678_gb300 import mlbicgstab as M
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A, b = _make_inputs(wl)
+    N = A.n_rows
+    stream = torch.cuda.Stream()
+    h = M.mlbicgstab_create(A, n=wl["n"], q_seed=0, max_outer=10, stream=stream)
+    info = M.mlbicgstab_info(h)
+    b_d = torch.tensor(b, dtype=torch.float64, device=dev)
+    x_d = torch.zeros(N, dtype=torch.float64, device=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up solves (untimed)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            x_d.zero_()
+        res, _ = M.mlbicgstab_solve(h, b_d, x_d, wl["tol"], wl["maxit"])
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    results = []
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            x_d.zero_()
+        res, _ = M.mlbicgstab_solve(h, b_d, x_d, wl["tol"], wl["maxit"])
+        results.append(res.as_dict())
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the C ABI with pinned host buffers
+    b_h = torch.tensor(b, dtype=torch.float64).pin_memory()
+    x_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+    bn, xn = b_h.numpy(), x_h.numpy()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.steps)
+    for _ in range(e2e_steps):
+        xn[:] = 0.0
+        M.mlbicgstab_solve(h, bn, xn, wl["tol"], wl["maxit"])
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = _load_peaks()
+    kern_ms = sum(r["kernel_ms"] for r in results)
+    kern_bytes = sum(r["bytes"] for r in results)
+    achieved = kern_bytes / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None
+    iters = [r["iter"] for r in results]
+    value = ws * args.steps / (total_ms * 1e-3)
+
+    cpu = None
+    if not args.no_cpu_baseline and ws >= 1:
+        spi, done = oracle_sample(A, b, wl["n"], args.ref_iters)
+        it = statistics.median(iters)
+        cpu = {"value": 1.0 / (spi * it), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"{done} iterations of the same solve on one host core; "
+                          f"solves/sec = 1/(seconds per iteration x {int(it)} "
+                          f"iterations per GPU solve)"),
+               "seconds_per_iteration": spi}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": _config(wl, A, {"grid": info["grid"], "block": info["block"],
+                                  "nnz_sell32": info["nnz_padded"]}),
+        "iters_per_solve": iters, "flags": [r["flag"] for r in results],
+        "true_relres": [r["true_relres"] for r in results],
+        "restarts": [r["outer"] for r in results],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "solve_kernel<double> (persistent, one launch per solve)",
+                     "algorithmic_bytes_per_launch": kern_bytes / len(results),
+                     "kernel_ms_per_launch": kern_ms / len(results)},
+        "e2e": {"value": ws * e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8 + 168},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    h.destroy()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-iters", type=int, default=60,
+                    help="oracle iterations per CPU sample")
+    ap.add_argument("--iters-per-solve", type=int, default=0,
+                    help="reference arm: iterations of a full solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

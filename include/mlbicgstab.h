@@ -1,0 +1,228 @@
+/*
+ * mlbicgstab.h — C ABI of a GB300 (sm_103a) ML(n)BiCGStab solver library.
+ *
+ * ML(n)BiCGStab (M.-C. Yeung, "An introduction to ML(n)BiCGStab",
+ * arXiv:1106.3678) solves A x = b for large sparse non-symmetric A using n
+ * shadow vectors Q = [q_1 .. q_n].  This library implements the paper's
+ * third algorithm, ML(n)BiCGStabt (Algorithm 4.1; Algorithm 7.1 with
+ * M = I), whose per-iteration work is a sparse matrix-vector product fused
+ * with shadow-vector inner products, plus AXPY-type recurrences indexed by
+ * the index functions g_n, r_n of §2.  A^H appears only once per (A, Q), in
+ * F = A^H Q(:,1:n-1) (Algorithm 4.1, step 2), which mlbicgstab_create
+ * computes and keeps.
+ *
+ * Conventions shared by every entry point
+ *   - Indices are 0-based (the paper's Matlab code is 1-based).
+ *   - Real values are IEEE double.  Complex values are interleaved
+ *     (re, im) double pairs, like C99 `double complex`.  Inner products
+ *     conjugate their left argument: u^H v = sum conj(u_i) v_i.
+ *   - Matrices are CSR: row_ptr[nrows+1] (int64, row_ptr[0] = 0,
+ *     non-decreasing), col_idx[nnz] (int32 in [0, nrows)), values[nnz].
+ *     Column indices need not be sorted; duplicates are summed.
+ *   - Every function returns an API status (MLB_OK or MLB_ERR_*), which is
+ *     separate from the solver flag of mlb_result (the paper's 0 / 1 / -1).
+ *   - The library allocates and frees its own device memory.  It never
+ *     takes ownership of caller pointers and never keeps them after a call
+ *     returns.  A handle is not thread-safe: calls on one handle must not
+ *     overlap.
+ *   - No CPU fallback exists: without a CUDA device, create returns
+ *     MLB_ERR_CUDA.
+ */
+#ifndef MLBICGSTAB_H
+#define MLBICGSTAB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MLB_OK 0
+#define MLB_ERR_ARG 1         /* invalid argument (checked before any GPU work) */
+#define MLB_ERR_CUDA 2        /* a CUDA runtime call failed (or no device) */
+#define MLB_ERR_OOM 3         /* device or pinned host allocation failed */
+#define MLB_ERR_TIMEOUT 4     /* a bounded device-side wait ran out; the
+                                 kernel returned early and the context is
+                                 still usable */
+#define MLB_ERR_UNSUPPORTED 5 /* valid request this build does not handle */
+
+/* ---- value types ------------------------------------------------------- */
+#define MLB_F64 0   /* double */
+#define MLB_C128 2  /* complex double, interleaved (re, im) */
+
+/* ---- precision modes --------------------------------------------------- */
+#define MLB_PREC_FP64 0     /* matrix, vectors and arithmetic in FP64 */
+#define MLB_PREC_FP32_REFINED 1 /* inner ML(n)BiCGStab in FP32 (values,
+                                   vectors, accumulation) inside an FP64
+                                   iterative refinement: residual b - A x,
+                                   solution update and all recurrence
+                                   coefficients in FP64 */
+
+/* A sparse matrix in host memory (CSR).  The library copies it; the
+ * caller's arrays may be freed after mlbicgstab_create returns. */
+typedef struct {
+    int64_t nrows;          /* N (square matrices only) */
+    int64_t nnz;            /* number of stored entries */
+    const int64_t *row_ptr; /* nrows + 1 entries */
+    const int32_t *col_idx; /* nnz entries */
+    const void *values;     /* nnz values of type `dtype` */
+    int32_t dtype;          /* MLB_F64 or MLB_C128 */
+    int32_t reserved;       /* must be 0 */
+} mlb_matrix;
+
+/* Options for mlbicgstab_create.  Zero-initialise, then set what you need;
+ * mlbicgstab_default_options fills the defaults below. */
+typedef struct {
+    int32_t n;            /* number of shadow vectors, 1 <= n <= 64
+                             (default 4; the paper suggests 4 or 8, §5.2) */
+    int32_t precision;    /* MLB_PREC_FP64 (default) or MLB_PREC_FP32_REFINED */
+    uint64_t q_seed;      /* seed of the shadow vectors when Q == NULL */
+    const void *Q;        /* optional host N x n column-major shadow matrix
+                             (dtype of A).  NULL: Q ~ N(0,1) entrywise from
+                             q_seed, drawn by the counter-based generator
+                             documented in mlbicgstab_get_Q */
+    double kappa;         /* omega guard of Eq. 5.1; 0 (default) gives the
+                             standard minimisation step */
+    int32_t max_outer;    /* FP64: restarts from the current x while the
+                             recursive residual met tol but the true one did
+                             not (default 10).  Refined: maximum refinement
+                             steps (default 30). */
+    int32_t grid;         /* CTAs of the persistent solve kernel; 0 = auto
+                             (all SMs x occupancy, fewer for small N) */
+    double inner_tol;     /* refined mode: relative tolerance of each FP32
+                             inner solve (default 1e-5) */
+    int64_t inner_maxit;  /* refined mode: iteration cap of one inner solve
+                             (default 10000) */
+    void *stream;         /* cudaStream_t for all work of this handle;
+                             NULL = the legacy default stream */
+    int64_t timeout_ns;   /* limit of every device-side wait (grid barrier
+                             spin); default 2e9 (2 s) */
+} mlb_options;
+
+/* Result of one solve.  flag/iter/err follow the paper's reference code
+ * (§5, Appendix): flag 0 = converged (||r||/||b|| < tol on the recursive
+ * residual), 1 = iteration limit, -1 = breakdown (c = 0, ||A u|| = 0 or
+ * omega = 0, or a non-finite scalar). */
+typedef struct {
+    int32_t flag;
+    int32_t j;            /* block index g_n(k) of the last iteration k */
+    int32_t i;            /* in-block index r_n(k) (1..n) of the last k */
+    int32_t status;       /* MLB_OK or MLB_ERR_TIMEOUT (device-side wait) */
+    int64_t iter;         /* iterations k over all restarts / inner solves */
+    int64_t spmv;         /* sparse matrix-vector products (FP64 + FP32) */
+    int64_t outer;        /* restarts (FP64) or refinement steps (refined) */
+    double err;           /* last recursive relative residual */
+    double true_relres;   /* ||b - A x||_2 / ||b||_2 in FP64 at return
+                             (||b|| replaced by 1 when b = 0) */
+    double kernel_ms;     /* device time of the solve kernel(s) */
+    double bytes;         /* algorithmic HBM bytes of the solve kernel(s):
+                             each pass counted as its inputs read once and
+                             its outputs written once */
+    int64_t ops[5];       /* Table 4.3 operation counts of the last inner
+                             call: matvec, dot, saxpy, scale (alpha v), norm */
+} mlb_result;
+
+/* Facts about a handle. */
+typedef struct {
+    int64_t nrows, nnz;
+    int32_t n, dtype, precision, grid, block;
+    int32_t reserved;
+    int64_t nnz_padded;   /* stored SELL-32 entries (>= nnz) */
+    int64_t device_bytes; /* device memory held by the handle */
+} mlb_info;
+
+typedef struct mlb_handle mlb_handle;
+
+/* Fill `opt` with the defaults listed in mlb_options. */
+void mlbicgstab_default_options(mlb_options *opt);
+
+/*
+ * Create a solver for the matrix A (host CSR).  Validates A (row_ptr
+ * monotone, columns in range; MLB_ERR_ARG otherwise), copies it to the
+ * device in SELL-32 form (rows in natural order, 32-row slices stored
+ * column-major), draws or copies Q, and computes F = A^H Q(:,1:n-1)
+ * (Algorithm 4.1, step 2; with M = I, Algorithm 7.1, step 2).
+ *   AH   optional host CSR of A^H (for complex A, the conjugate transpose).
+ *        NULL: the library forms A^H itself.  Only used for F.
+ *   opt  NULL for defaults.
+ * On success *h owns all device memory; release it with mlbicgstab_destroy.
+ */
+int mlbicgstab_create(mlb_handle **h, const mlb_matrix *A,
+                      const mlb_matrix *AH, const mlb_options *opt);
+
+/*
+ * Solve A x = b (Algorithm 7.1 with M = I, stopping rule of §5: stop when
+ * ||r_k||/||b|| < tol after any update of r or u; at most `maxit` k-steps
+ * in total).  The whole iteration runs in one persistent kernel: the
+ * convergence and breakdown tests are taken on the device.
+ *   b, x       N values each (dtype of A).  x holds x_0 on entry and the
+ *              solution on return.  on_device = 0: host pointers (copied
+ *              in and out inside the call); 1: device pointers.
+ *   err_hist   optional host array (NULL to skip): err_hist[k] = relative
+ *              recursive residual after iteration k (k = 0: initial), for
+ *              k < hist_cap, over the first inner call.
+ * Blocks until the result is available.
+ */
+int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device,
+                     double tol, int64_t maxit, mlb_result *res,
+                     double *err_hist, int64_t hist_cap);
+
+/*
+ * Solve `count` independent systems, one handle each (created with the same
+ * dtype and precision), in one persistent launch: each CTA takes systems
+ * from a shared queue, largest first, and runs the same method as
+ * mlbicgstab_solve with a CTA-wide barrier in place of the grid barrier.
+ *   b[s], x[s]  per-system pointers as in mlbicgstab_solve (on_device
+ *               applies to all).  tol[s], maxit[s] per system.
+ *   res         `count` results.
+ * The stream of hs[0] is used.
+ */
+int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count,
+                           const void *const *b, void *const *x,
+                           int32_t on_device, const double *tol,
+                           const int64_t *maxit, mlb_result *res);
+
+/*
+ * Fused hot operation: y = A x and d = Q^H y (all n shadow inner products,
+ * a tall-skinny block reduction) in one pass over A — the per-iteration
+ * product w = A g with c = q^H w of Algorithm 4.1 (step 32) generalised to
+ * every q.  x, y: device arrays of N values; d: host array of n values.
+ * Reductions are deterministic (fixed order).  Blocks until d is ready.
+ */
+int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d);
+
+/*
+ * Copy Q (N x n, column-major, dtype of A) to host memory.  When Q was
+ * drawn from q_seed, real entry e = col*N + row is normal number e and a
+ * complex entry e takes normals 2e (re) and 2e+1 (im), where normal number
+ * t is Box–Muller (cosine branch) of uniforms U(2t), U(2t+1) on (0,1],
+ * U(s) = ((v >> 11) + 1) 2^-53 with v output number s of SplitMix64
+ * (Steele, Lea & Flood 2014) seeded with q_seed.  The paper fixes no
+ * generator (§5 uses Matlab's randn).
+ */
+int mlbicgstab_get_Q(const mlb_handle *h, void *host_out);
+
+/* Fill `info` for a handle. */
+int mlbicgstab_info(const mlb_handle *h, mlb_info *info);
+
+/* Release every resource of a handle (NULL is accepted). */
+void mlbicgstab_destroy(mlb_handle *h);
+
+/* Static text for a status code. */
+const char *mlbicgstab_strerror(int code);
+
+/*
+ * Failure-detection self-test: launches the grid barrier the solve kernel
+ * uses with one participant that never arrives, on `grid` CTAs, with a
+ * wait limit of `timeout_ns`.  Every wait gives up after the limit and the
+ * kernel returns; expected result MLB_ERR_TIMEOUT with the device still
+ * usable.  The paper has no counterpart (library robustness only).
+ */
+int mlbicgstab_selftest_barrier_timeout(int32_t grid, int64_t timeout_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLBICGSTAB_H */

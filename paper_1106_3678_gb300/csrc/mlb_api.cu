@@ -1,0 +1,571 @@
+// C ABI of the ML(n)BiCGStab library: argument validation, device state of
+// a handle, and the host side of every entry point.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mlbicgstab.h"
+#include "mlb_internal.h"
+
+using namespace mlb;
+
+struct mlb_handle {
+    int dtype = MLB_F64;
+    int n = 4;
+    int precision = MLB_PREC_FP64;
+    int64_t N = 0, ld = 0, nnz = 0, nnz_pad = 0, nslices = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int grid = 1;
+    uint64_t timeout_ns = 2000000000ull;
+    double kappa = 0.0;
+    int max_outer = 10;
+    double inner_tol = 1e-5;
+    int64_t inner_maxit = 10000;
+    size_t esize = 8;  // bytes per value
+    // device buffers
+    int64_t *slice_ptr = nullptr;
+    int32_t *scol = nullptr;
+    void *sval = nullptr;
+    void *Q = nullptr, *F = nullptr, *G = nullptr, *W = nullptr;
+    void *x = nullptr, *r = nullptr, *z = nullptr, *b = nullptr;
+    double *partials = nullptr;
+    BarrierState *bar = nullptr;
+    DevResult *dres = nullptr;
+    double *err_hist = nullptr;
+    int64_t err_cap = 0;
+    double *qd_partials = nullptr;
+    double *qd_out = nullptr;
+    int qd_grid = 0;
+    DevResult *hres = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+#define MLB_CUDA(call)                                                          \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            return e_ == cudaErrorMemoryAllocation ? MLB_ERR_OOM : MLB_ERR_CUDA; \
+        }                                                                       \
+    } while (0)
+
+int dev_alloc(mlb_handle *h, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? MLB_ERR_OOM : MLB_ERR_CUDA;
+    }
+    h->allocs.push_back(*p);
+    h->device_bytes += (int64_t)bytes;
+    return MLB_OK;
+}
+
+template <typename P>
+int dev_alloc_t(mlb_handle *h, P **p, size_t bytes) {
+    void *v = nullptr;
+    int rc = dev_alloc(h, &v, bytes);
+    *p = (P *)v;
+    return rc;
+}
+
+// CSR checks done before any GPU work.
+int validate_csr(const mlb_matrix *A) {
+    if (!A || A->nrows <= 0 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->values)))
+        return MLB_ERR_ARG;
+    if (A->dtype != MLB_F64 && A->dtype != MLB_C128) return MLB_ERR_ARG;
+    if (A->reserved != 0) return MLB_ERR_ARG;
+    if (A->nrows > (int64_t)INT32_MAX - 1024) return MLB_ERR_ARG;
+    if (A->row_ptr[0] != 0 || A->row_ptr[A->nrows] != A->nnz) return MLB_ERR_ARG;
+    for (int64_t r = 0; r < A->nrows; ++r)
+        if (A->row_ptr[r + 1] < A->row_ptr[r]) return MLB_ERR_ARG;
+    for (int64_t k = 0; k < A->nnz; ++k)
+        if (A->col_idx[k] < 0 || (int64_t)A->col_idx[k] >= A->nrows) return MLB_ERR_ARG;
+    return MLB_OK;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// CSR -> SELL-32 (slices of 32 consecutive rows, natural row order, entry k
+// of lane l at slice_ptr[s] + 32k + l; padding entries have value 0 and
+// column = the row itself, clamped to N-1).
+void csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp, std::vector<int32_t> &col,
+                   std::vector<char> &val, size_t es) {
+    const int64_t N = A->nrows, ns = ld / 32;
+    sp.assign(ns + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t w = 0;
+        for (int64_t l = 0; l < 32; ++l) {
+            int64_t row = s * 32 + l;
+            if (row < N) w = std::max(w, A->row_ptr[row + 1] - A->row_ptr[row]);
+        }
+        sp[s + 1] = sp[s] + 32 * w;
+    }
+    const int64_t tot = sp[ns];
+    col.assign(tot, 0);
+    val.assign(tot * es, 0);
+    const char *av = (const char *)A->values;
+    for (int64_t s = 0; s < ns; ++s) {
+        const int64_t w = (sp[s + 1] - sp[s]) / 32;
+        for (int64_t l = 0; l < 32; ++l) {
+            const int64_t row = s * 32 + l;
+            const int64_t len = row < N ? A->row_ptr[row + 1] - A->row_ptr[row] : 0;
+            for (int64_t k = 0; k < w; ++k) {
+                const int64_t dst = sp[s] + 32 * k + l;
+                if (k < len) {
+                    const int64_t src = A->row_ptr[row] + k;
+                    col[dst] = A->col_idx[src];
+                    memcpy(&val[dst * es], av + src * es, es);
+                } else {
+                    col[dst] = (int32_t)std::min<int64_t>(row, N - 1);
+                }
+            }
+        }
+    }
+}
+
+// A^H in CSR by a stable counting sort over columns (values conjugated for
+// complex data).
+void conj_transpose(const mlb_matrix *A, std::vector<int64_t> &rp, std::vector<int32_t> &ci,
+                    std::vector<char> &av, size_t es, bool cplx) {
+    const int64_t N = A->nrows, nnz = A->nnz;
+    rp.assign(N + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) rp[A->col_idx[k] + 1]++;
+    for (int64_t r = 0; r < N; ++r) rp[r + 1] += rp[r];
+    std::vector<int64_t> next(rp.begin(), rp.end() - 1);
+    ci.assign(nnz, 0);
+    av.assign(nnz * es, 0);
+    const char *src = (const char *)A->values;
+    for (int64_t r = 0; r < N; ++r) {
+        for (int64_t k = A->row_ptr[r]; k < A->row_ptr[r + 1]; ++k) {
+            const int64_t dst = next[A->col_idx[k]]++;
+            ci[dst] = (int32_t)r;
+            memcpy(&av[dst * es], src + k * es, es);
+            if (cplx) {
+                double *im = (double *)&av[dst * es] + 1;
+                *im = -*im;
+            }
+        }
+    }
+}
+
+template <typename T>
+SysView<T> make_view(const mlb_handle *h) {
+    SysView<T> v;
+    v.N = h->N;
+    v.ld = h->ld;
+    v.nnz = h->nnz;
+    v.nslices = h->nslices;
+    v.slice_ptr = h->slice_ptr;
+    v.scol = h->scol;
+    v.sval = (const T *)h->sval;
+    v.Q = (const T *)h->Q;
+    v.F = (const T *)h->F;
+    v.G = (T *)h->G;
+    v.W = (T *)h->W;
+    v.x = (T *)h->x;
+    v.r = (T *)h->r;
+    v.z = (T *)h->z;
+    v.b = (const T *)h->b;
+    v.n = h->n;
+    return v;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const mlb_options *o) {
+    MLB_CUDA(cudaGetDevice(&h->device));
+    h->dtype = A->dtype;
+    h->esize = A->dtype == MLB_C128 ? 16 : 8;
+    h->n = o->n;
+    h->precision = o->precision;
+    h->N = A->nrows;
+    h->nnz = A->nnz;
+    h->ld = round_up(h->N, 512);
+    h->nslices = h->ld / 32;
+    h->stream = (cudaStream_t)o->stream;
+    h->timeout_ns = (uint64_t)o->timeout_ns;
+    h->kappa = o->kappa;
+    h->max_outer = o->max_outer;
+    h->inner_tol = o->inner_tol;
+    h->inner_maxit = o->inner_maxit;
+    const size_t es = h->esize;
+    const bool cplx = A->dtype == MLB_C128;
+    const int64_t ld = h->ld;
+    const int n = h->n;
+    cudaStream_t st = h->stream;
+
+    // matrix in SELL-32
+    {
+        std::vector<int64_t> sp;
+        std::vector<int32_t> col;
+        std::vector<char> val;
+        csr_to_sell32(A, ld, sp, col, val, es);
+        h->nnz_pad = sp.back();
+        int rc;
+        if ((rc = dev_alloc_t(h, &h->slice_ptr, sp.size() * 8))) return rc;
+        if ((rc = dev_alloc_t(h, &h->scol, col.size() * 4))) return rc;
+        if ((rc = dev_alloc(h, &h->sval, val.size()))) return rc;
+        MLB_CUDA(cudaMemcpy(h->slice_ptr, sp.data(), sp.size() * 8, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->scol, col.data(), col.size() * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->sval, val.data(), val.size(), cudaMemcpyHostToDevice));
+    }
+    // vectors: Q, F, G, W (ld x n), x, r, z, b (ld), zero padded
+    int rc;
+    const size_t vb = (size_t)ld * es;
+    if ((rc = dev_alloc(h, &h->Q, vb * n))) return rc;
+    if (n > 1 && (rc = dev_alloc(h, &h->F, vb * (n - 1)))) return rc;
+    if ((rc = dev_alloc(h, &h->G, vb * n))) return rc;
+    if ((rc = dev_alloc(h, &h->W, vb * n))) return rc;
+    if ((rc = dev_alloc(h, &h->x, vb))) return rc;
+    if ((rc = dev_alloc(h, &h->r, vb))) return rc;
+    if ((rc = dev_alloc(h, &h->z, vb))) return rc;
+    if ((rc = dev_alloc(h, &h->b, vb))) return rc;
+    MLB_CUDA(cudaMemsetAsync(h->Q, 0, vb * n, st));
+    if (n > 1) MLB_CUDA(cudaMemsetAsync(h->F, 0, vb * (n - 1), st));
+    MLB_CUDA(cudaMemsetAsync(h->G, 0, vb * n, st));
+    MLB_CUDA(cudaMemsetAsync(h->W, 0, vb * n, st));
+    MLB_CUDA(cudaMemsetAsync(h->x, 0, vb, st));
+    MLB_CUDA(cudaMemsetAsync(h->r, 0, vb, st));
+    MLB_CUDA(cudaMemsetAsync(h->z, 0, vb, st));
+    MLB_CUDA(cudaMemsetAsync(h->b, 0, vb, st));
+
+    // shadow vectors
+    if (o->Q) {
+        MLB_CUDA(cudaMemcpy2DAsync(h->Q, ld * es, o->Q, h->N * es, h->N * es, n, cudaMemcpyHostToDevice, st));
+    } else {
+        MLB_CUDA(launch_qgen(h->Q, cplx ? 1 : 0, h->N, ld, n, o->q_seed, st));
+    }
+
+    // F = A^H Q(:, 0:n-2) (Algorithm 4.1, step 2)
+    if (n > 1) {
+        std::vector<int64_t> trp;
+        std::vector<int32_t> tci;
+        std::vector<char> tav;
+        const int64_t *rp;
+        const int32_t *ci;
+        const void *av;
+        int64_t tnnz;
+        if (AH) {
+            rp = AH->row_ptr;
+            ci = AH->col_idx;
+            av = AH->values;
+            tnnz = AH->nnz;
+        } else {
+            conj_transpose(A, trp, tci, tav, es, cplx);
+            rp = trp.data();
+            ci = tci.data();
+            av = tav.data();
+            tnnz = A->nnz;
+        }
+        int64_t *drp = nullptr;
+        int32_t *dci = nullptr;
+        void *dav = nullptr;
+        if (cudaMalloc(&drp, (h->N + 1) * 8) != cudaSuccess ||
+            cudaMalloc(&dci, std::max<int64_t>(tnnz, 1) * 4) != cudaSuccess ||
+            cudaMalloc(&dav, std::max<int64_t>(tnnz, 1) * es) != cudaSuccess) {
+            cudaFree(drp);
+            cudaFree(dci);
+            cudaFree(dav);
+            cudaGetLastError();
+            return MLB_ERR_OOM;
+        }
+        cudaError_t e = cudaMemcpy(drp, rp, (h->N + 1) * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && tnnz) e = cudaMemcpy(dci, ci, tnnz * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && tnnz) e = cudaMemcpy(dav, av, tnnz * es, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            if (cplx)
+                e = launch_ahq<cdouble>(drp, dci, (const cdouble *)dav, h->N, ld, (const cdouble *)h->Q,
+                                        (cdouble *)h->F, n - 1, st);
+            else
+                e = launch_ahq<double>(drp, dci, (const double *)dav, h->N, ld, (const double *)h->Q,
+                                       (double *)h->F, n - 1, st);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(drp);
+        cudaFree(dci);
+        cudaFree(dav);
+        if (e != cudaSuccess) return MLB_ERR_CUDA;
+    }
+
+    // launch geometry and scratch
+    int sms = 0;
+    MLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int bps = cplx ? solve_blocks_per_sm<cdouble>() : solve_blocks_per_sm<double>();
+    if (bps < 1) return MLB_ERR_CUDA;
+    const int64_t nchunk = ld * (int64_t)es / 16;
+    int64_t want = (nchunk + kThreads - 1) / kThreads;
+    int maxg = sms * bps;
+    int grid = (int)std::min<int64_t>(want, maxg);
+    if (o->grid > 0) grid = std::min(o->grid, maxg);
+    h->grid = std::max(grid, 1);
+    if ((rc = dev_alloc_t(h, &h->partials, (size_t)2 * maxg * kMaxSums * 8))) return rc;
+    if ((rc = dev_alloc_t(h, &h->bar, sizeof(BarrierState)))) return rc;
+    if ((rc = dev_alloc_t(h, &h->dres, sizeof(DevResult)))) return rc;
+    h->qd_grid = cplx ? spmv_qdot_grid<cdouble>() : spmv_qdot_grid<double>();
+    if ((rc = dev_alloc_t(h, &h->qd_partials, (size_t)h->qd_grid * kQdMaxN * 2 * 8))) return rc;
+    if ((rc = dev_alloc_t(h, &h->qd_out, (size_t)kQdMaxN * 2 * 8))) return rc;
+    if (cudaMallocHost(&h->hres, sizeof(DevResult)) != cudaSuccess) {
+        cudaGetLastError();
+        h->hres = nullptr;
+        return MLB_ERR_OOM;
+    }
+    MLB_CUDA(cudaEventCreate(&h->ev0));
+    MLB_CUDA(cudaEventCreate(&h->ev1));
+    MLB_CUDA(cudaStreamSynchronize(st));
+    return MLB_OK;
+}
+
+void release(mlb_handle *h) {
+    if (!h) return;
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->err_hist) cudaFree(h->err_hist);
+    if (h->hres) cudaFreeHost(h->hres);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+void mlbicgstab_default_options(mlb_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->n = 4;
+    o->precision = MLB_PREC_FP64;
+    o->q_seed = 0;
+    o->Q = nullptr;
+    o->kappa = 0.0;
+    o->max_outer = 10;
+    o->grid = 0;
+    o->inner_tol = 1e-5;
+    o->inner_maxit = 10000;
+    o->stream = nullptr;
+    o->timeout_ns = 2000000000LL;
+}
+
+const char *mlbicgstab_strerror(int code) {
+    switch (code) {
+        case MLB_OK: return "success";
+        case MLB_ERR_ARG: return "invalid argument";
+        case MLB_ERR_CUDA: return "CUDA runtime error or no CUDA device";
+        case MLB_ERR_OOM: return "out of memory";
+        case MLB_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case MLB_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status code";
+    }
+}
+
+int mlbicgstab_create(mlb_handle **out, const mlb_matrix *A, const mlb_matrix *AH, const mlb_options *opt) {
+    if (!out) return MLB_ERR_ARG;
+    *out = nullptr;
+    mlb_options o;
+    if (opt) o = *opt;
+    else mlbicgstab_default_options(&o);
+    if (o.n < 1 || o.n > kMaxN) return MLB_ERR_ARG;
+    if (o.precision != MLB_PREC_FP64 && o.precision != MLB_PREC_FP32_REFINED) return MLB_ERR_ARG;
+    if (o.kappa < 0.0 || o.max_outer < 0 || o.timeout_ns <= 0) return MLB_ERR_ARG;
+    int rc = validate_csr(A);
+    if (rc) return rc;
+    if (AH) {
+        rc = validate_csr(AH);
+        if (rc) return rc;
+        if (AH->nrows != A->nrows || AH->dtype != A->dtype) return MLB_ERR_ARG;
+    }
+    if (o.precision == MLB_PREC_FP32_REFINED) return MLB_ERR_UNSUPPORTED;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    mlb_handle *h = new (std::nothrow) mlb_handle();
+    if (!h) return MLB_ERR_OOM;
+    rc = create_impl(h, A, AH, &o);
+    if (rc) {
+        release(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return MLB_OK;
+}
+
+void mlbicgstab_destroy(mlb_handle *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+}
+
+int mlbicgstab_info(const mlb_handle *h, mlb_info *info) {
+    if (!h || !info) return MLB_ERR_ARG;
+    memset(info, 0, sizeof(*info));
+    info->nrows = h->N;
+    info->nnz = h->nnz;
+    info->n = h->n;
+    info->dtype = h->dtype;
+    info->precision = h->precision;
+    info->grid = h->grid;
+    info->block = kThreads;
+    info->nnz_padded = h->nnz_pad;
+    info->device_bytes = h->device_bytes;
+    return MLB_OK;
+}
+
+int mlbicgstab_get_Q(const mlb_handle *h, void *host_out) {
+    if (!h || !host_out) return MLB_ERR_ARG;
+    MLB_CUDA(cudaSetDevice(h->device));
+    MLB_CUDA(cudaMemcpy2DAsync(host_out, h->N * h->esize, h->Q, h->ld * h->esize, h->N * h->esize, h->n,
+                               cudaMemcpyDeviceToHost, h->stream));
+    MLB_CUDA(cudaStreamSynchronize(h->stream));
+    return MLB_OK;
+}
+
+int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, double tol, int64_t maxit,
+                     mlb_result *res, double *err_hist, int64_t hist_cap) {
+    if (!h || !b || !x || !res) return MLB_ERR_ARG;
+    if (!(tol >= 0.0) || maxit < 0 || hist_cap < 0 || (on_device != 0 && on_device != 1)) return MLB_ERR_ARG;
+    memset(res, 0, sizeof(*res));
+    MLB_CUDA(cudaSetDevice(h->device));
+    if (on_device && (!is_device_ptr(b) || !is_device_ptr(x))) return MLB_ERR_ARG;
+    cudaStream_t st = h->stream;
+    const size_t nb = (size_t)h->N * h->esize;
+    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind outk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (err_hist && hist_cap > h->err_cap) {
+        if (h->err_hist) cudaFree(h->err_hist);
+        h->err_hist = nullptr;
+        h->err_cap = 0;
+        if (cudaMalloc(&h->err_hist, hist_cap * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return MLB_ERR_OOM;
+        }
+        h->err_cap = hist_cap;
+    }
+    MLB_CUDA(cudaMemcpyAsync(h->b, b, nb, in, st));
+    MLB_CUDA(cudaMemcpyAsync(h->x, x, nb, in, st));
+    MLB_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(BarrierState), st));
+    SolveCtl ctl;
+    ctl.tol = tol;
+    ctl.maxit = maxit;
+    ctl.kappa = h->kappa;
+    ctl.max_outer = h->max_outer;
+    ctl.err_hist = err_hist ? h->err_hist : nullptr;
+    ctl.hist_cap = err_hist ? hist_cap : 0;
+    ctl.partials = h->partials;
+    ctl.bar = h->bar;
+    ctl.res = h->dres;
+    ctl.timeout_ns = h->timeout_ns;
+    MLB_CUDA(cudaEventRecord(h->ev0, st));
+    cudaError_t e;
+    if (h->dtype == MLB_C128) e = launch_solve<cdouble>(make_view<cdouble>(h), ctl, h->grid, st);
+    else e = launch_solve<double>(make_view<double>(h), ctl, h->grid, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    MLB_CUDA(cudaEventRecord(h->ev1, st));
+    MLB_CUDA(cudaMemcpyAsync(x, h->x, nb, outk, st));
+    MLB_CUDA(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
+    MLB_CUDA(cudaStreamSynchronize(st));
+    const DevResult &d = *h->hres;
+    res->flag = d.flag;
+    res->j = d.j;
+    res->i = d.i;
+    res->status = d.status;
+    res->iter = d.iter;
+    res->spmv = d.spmv;
+    res->outer = d.outer;
+    res->err = d.err;
+    res->true_relres = d.true_relres;
+    res->bytes = d.bytes;
+    for (int q = 0; q < 5; ++q) res->ops[q] = d.ops[q];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    res->kernel_ms = ms;
+    if (err_hist && hist_cap > 0) {
+        int64_t cnt = std::min<int64_t>(hist_cap, d.iter + 1);
+        for (int64_t k = 0; k < hist_cap; ++k) err_hist[k] = __builtin_nan("");
+        if (cnt > 0) MLB_CUDA(cudaMemcpy(err_hist, h->err_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (d.status != 0) return MLB_ERR_TIMEOUT;
+    return MLB_OK;
+}
+
+int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *const *b, void *const *x,
+                           int32_t on_device, const double *tol, const int64_t *maxit, mlb_result *res) {
+    if (!hs || count <= 0 || !b || !x || !tol || !maxit || !res) return MLB_ERR_ARG;
+    (void)on_device;
+    return MLB_ERR_UNSUPPORTED;
+}
+
+int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
+    if (!h || !x || !y || !d) return MLB_ERR_ARG;
+    MLB_CUDA(cudaSetDevice(h->device));
+    if (!is_device_ptr(x) || !is_device_ptr(y)) return MLB_ERR_ARG;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    // x is read through the padded internal buffer so that every gather
+    // stays inside an allocation of ld entries
+    const size_t nb = (size_t)h->N * h->esize;
+    MLB_CUDA(cudaMemcpyAsync(h->z, x, nb, cudaMemcpyDeviceToDevice, st));
+    if (h->dtype == MLB_C128)
+        e = launch_spmv_qdot<cdouble>(make_view<cdouble>(h), (const cdouble *)h->z, (cdouble *)h->r,
+                                      h->qd_partials, h->qd_grid, h->qd_out, st);
+    else
+        e = launch_spmv_qdot<double>(make_view<double>(h), (const double *)h->z, (double *)h->r,
+                                     h->qd_partials, h->qd_grid, h->qd_out, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    MLB_CUDA(cudaMemcpyAsync(y, h->r, nb, cudaMemcpyDeviceToDevice, st));
+    MLB_CUDA(cudaMemcpyAsync(d, h->qd_out, (size_t)h->n * (h->dtype == MLB_C128 ? 16 : 8),
+                             cudaMemcpyDeviceToHost, st));
+    MLB_CUDA(cudaStreamSynchronize(st));
+    return MLB_OK;
+}
+
+int mlbicgstab_selftest_barrier_timeout(int32_t grid, int64_t timeout_ns) {
+    if (grid < 1 || grid > 64 || timeout_ns <= 0 || timeout_ns > 10000000000LL) return MLB_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    BarrierState *bs = nullptr;
+    MLB_CUDA(cudaMalloc(&bs, sizeof(BarrierState)));
+    cudaError_t e = cudaMemset(bs, 0, sizeof(BarrierState));
+    if (e == cudaSuccess) e = launch_barrier_selftest(grid, bs, (uint64_t)timeout_ns, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    BarrierState hb;
+    memset(&hb, 0, sizeof(hb));
+    if (e == cudaSuccess) e = cudaMemcpy(&hb, bs, sizeof(hb), cudaMemcpyDeviceToHost);
+    cudaFree(bs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    return hb.status == kStatusTimeout ? MLB_ERR_TIMEOUT : MLB_OK;
+}
+
+}  // extern "C"

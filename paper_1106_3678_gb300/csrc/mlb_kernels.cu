@@ -1,0 +1,307 @@
+// Kernels of the ML(n)BiCGStab library (sm_103a).
+#include "mlb_internal.h"
+
+namespace mlb {
+
+// ===========================================================================
+// persistent solve kernel
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) solve_kernel(SysView<T> sys, SolveCtl ctl) {
+    using S = typename coef_of<T>::type;
+    __shared__ double red[33 * kMaxSums + 1];
+    __shared__ S cbuf[kMaxN];
+    __shared__ S btbuf[kMaxN];
+    __shared__ int sflag;
+    __shared__ Acct acct;
+    Engine<T> E(sys, ctl, red, cbuf, btbuf, &sflag, &acct);
+
+    // Repeated calls of the method from the current x while the recursive
+    // residual met tol but the true residual did not (restart rule of this
+    // library), all iterations counted against one maxit.
+    int64_t total = 0;
+    int outer = 0;
+    typename Engine<T>::Out o{1, 0, 0, 0, 0.0};
+    for (;;) {
+        o = E.inner(ctl.maxit - total, outer == 0);
+        if (!E.ok) break;
+        total += o.iter;
+        if (o.flag != 0 || o.iter == 0 || total >= ctl.maxit || outer >= ctl.max_outer) break;
+        outer++;
+    }
+    int64_t ops_last[5];
+    for (int q = 0; q < 5; ++q) ops_last[q] = acct.ops[q];
+    double true_rel = __longlong_as_double(0x7ff8000000000000LL);
+    if (E.ok) {
+        double bb, rr;
+        S qr;
+        if (E.ph_residual(bb, rr, qr, false)) {
+            double bn = sqrt(bb);
+            if (bn == 0.0) bn = 1.0;
+            true_rel = sqrt(rr) / bn;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        DevResult *res = ctl.res;
+        res->flag = o.flag;
+        res->j = o.j;
+        res->i = o.i;
+        res->status = E.ok ? 0 : ld_relaxed_i32(&ctl.bar->status);
+        if (!E.ok && res->status == 0) res->status = kStatusTimeout;
+        res->iter = total;
+        res->spmv = acct.spmv;
+        res->outer = outer;
+        res->err = o.err;
+        res->true_relres = true_rel;
+        res->bytes = acct.bytes;
+        for (int q = 0; q < 5; ++q) res->ops[q] = ops_last[q];
+    }
+}
+
+template <typename T>
+cudaError_t launch_solve(const SysView<T> &sys, const SolveCtl &ctl, int grid, cudaStream_t st) {
+    SysView<T> s = sys;
+    SolveCtl c = ctl;
+    void *args[] = {(void *)&s, (void *)&c};
+    if (grid <= 1)
+        return cudaLaunchKernel((const void *)solve_kernel<T>, dim3(1), dim3(kThreads), args, 0, st);
+    return cudaLaunchCooperativeKernel((const void *)solve_kernel<T>, dim3(grid), dim3(kThreads), args,
+                                       0, st);
+}
+
+template <typename T>
+int solve_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<T>, kThreads, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+// ===========================================================================
+// shadow vectors: SplitMix64 at a counter, Box-Muller (cosine branch)
+// ===========================================================================
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t t) {
+    uint64_t z = seed + (t + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double unit_open0(uint64_t v) {
+    return ((double)(v >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+}
+__device__ __forceinline__ double normal_at(uint64_t seed, uint64_t t) {
+    const double two_pi = 6.283185307179586476925286766559;
+    double u1 = unit_open0(splitmix64_at(seed, 2ull * t));
+    double u2 = unit_open0(splitmix64_at(seed, 2ull * t + 1ull));
+    double rad = sqrt(-2.0 * log(u1));
+    double ang = two_pi * u2;
+    return rad * cos(ang);
+}
+
+__global__ void qgen_kernel(double *Q, int is_complex, int64_t N, int64_t ld, int n, uint64_t seed) {
+    const int64_t total = N * (int64_t)n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e % N, col = e / N;
+        if (is_complex) {
+            double *q = Q + 2 * (col * ld + row);
+            q[0] = normal_at(seed, 2ull * e);
+            q[1] = normal_at(seed, 2ull * e + 1ull);
+        } else {
+            Q[col * ld + row] = normal_at(seed, (uint64_t)e);
+        }
+    }
+}
+
+cudaError_t launch_qgen(void *Q, int is_complex, int64_t N, int64_t ld, int n, uint64_t seed,
+                        cudaStream_t st) {
+    int64_t total = N * (int64_t)n;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 65535 * 8) blocks = 65535 * 8;
+    if (blocks < 1) blocks = 1;
+    qgen_kernel<<<blocks, 256, 0, st>>>((double *)Q, is_complex, N, ld, n, seed);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// F = A^H Q(:, 0:m-1) from the CSR of A^H (values already conjugated)
+// ===========================================================================
+template <typename T>
+__global__ void ahq_kernel(const int64_t *rp, const int32_t *ci, const T *av, int64_t N, int64_t ld,
+                           const T *Q, T *F, int m) {
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < N;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k0 = rp[row], k1 = rp[row + 1];
+        for (int s = 0; s < m; ++s) {
+            const T *q = Q + (int64_t)s * ld;
+            T acc{};
+            for (int64_t k = k0; k < k1; ++k) acc = efma(av[k], q[ci[k]], acc);
+            F[(int64_t)s * ld + row] = acc;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_ahq(const int64_t *rp, const int32_t *ci, const T *av, int64_t N, int64_t ld,
+                       const T *Q, T *F, int m, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    int64_t blocks = (N + 255) / 256;
+    if (blocks > 1 << 20) blocks = 1 << 20;
+    ahq_kernel<T><<<(int)blocks, 256, 0, st>>>(rp, ci, av, N, ld, Q, F, m);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// fused y = A x, d = Q^H y (all n shadow inner products)
+// ===========================================================================
+// Pass 1: one warp per 32-row SELL slice; each lane keeps NB running inner
+// products over its rows; per-CTA sums go to `partials` in fixed order.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kQdThreads) spmv_qdot_kernel(SysView<T> sys, const T *x, T *y,
+                                                               double *partials) {
+    constexpr int DS = dslots<T>();
+    using ACC = typename real_of<T>::type;
+    __shared__ double red[33 * DS];
+    const int n = sys.n;
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    ACC acc[NB * DS];
+#pragma unroll
+    for (int k = 0; k < NB * DS; ++k) acc[k] = ACC(0);
+    for (int64_t s = gwarp; s < sys.nslices; s += nwarps) {
+        const int64_t off = __ldg(sys.slice_ptr + s);
+        const int w = (int)((__ldg(sys.slice_ptr + s + 1) - off) >> 5);
+        const int32_t *cp = sys.scol + off + lane;
+        const T *vp = sys.sval + off + lane;
+        T sum{};
+        int k = 0;
+        for (; k + 8 <= w; k += 8) {
+            int32_t cc[8];
+            T vv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cc[u] = __ldcs(cp + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) vv[u] = ldcs_val(vp + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum = efma(vv[u], ldg_val(x + cc[u]), sum);
+        }
+        if (k < w) {
+            int32_t cc[8];
+            T vv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k + u < w) cc[u] = __ldcs(cp + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k + u < w) vv[u] = ldcs_val(vp + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k + u < w) sum = efma(vv[u], ldg_val(x + cc[u]), sum);
+        }
+        const int64_t row = s * 32 + lane;
+        y[row] = sum;
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+            if (q < n) acc_dot(&acc[q * DS], ldg_val(sys.Q + (int64_t)q * sys.ld + row), sum);
+    }
+    for (int q = 0; q < NB; ++q) {
+        if (q >= n) break;
+        double v[DS];
+#pragma unroll
+        for (int t = 0; t < DS; ++t) v[t] = (double)acc[q * DS + t];
+        block_sum_all<DS>(v, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int t = 0; t < DS; ++t)
+                partials[((size_t)blockIdx.x * kQdMaxN + q) * DS + t] = v[t];
+        }
+    }
+}
+
+// Pass 2: one CTA sums the per-CTA partials in fixed order.
+template <int DS>
+__global__ void qdot_finish_kernel(const double *partials, int grid, int n, double *d) {
+    __shared__ double red[33 * DS];
+    for (int q = 0; q < n; ++q) {
+        double v[DS];
+#pragma unroll
+        for (int t = 0; t < DS; ++t) v[t] = 0.0;
+        for (int b = threadIdx.x; b < grid; b += blockDim.x) {
+#pragma unroll
+            for (int t = 0; t < DS; ++t) v[t] += partials[((size_t)b * kQdMaxN + q) * DS + t];
+        }
+        block_sum_all<DS>(v, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int t = 0; t < DS; ++t) d[q * DS + t] = v[t];
+        }
+    }
+}
+
+template <typename T, int NB>
+static int qd_occupancy() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_qdot_kernel<T, NB>, kQdThreads, 0);
+    return nb;
+}
+
+template <typename T>
+int spmv_qdot_grid() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nb = qd_occupancy<T, kQdMaxN>();
+    if (nb < 1) nb = 1;
+    return sms * nb;
+}
+
+template <typename T>
+cudaError_t launch_spmv_qdot(const SysView<T> &sys, const T *x, T *y, double *partials, int grid,
+                             double *d, cudaStream_t st) {
+    constexpr int DS = dslots<T>();
+    const int n = sys.n;
+    if (n <= 4) spmv_qdot_kernel<T, 4><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
+    else if (n <= 8) spmv_qdot_kernel<T, 8><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
+    else if (n <= 16) spmv_qdot_kernel<T, 16><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
+    else if (n <= 32) spmv_qdot_kernel<T, 32><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
+    else spmv_qdot_kernel<T, 64><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    qdot_finish_kernel<DS><<<1, 1024, 0, st>>>(partials, grid, n, d);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// failure-detection self-test: a barrier one participant never reaches
+// ===========================================================================
+__global__ void barrier_selftest_kernel(BarrierState *bs, uint64_t timeout_ns) {
+    __shared__ int flag;
+    grid_barrier(bs, gridDim.x + 1, timeout_ns, &flag);
+}
+
+cudaError_t launch_barrier_selftest(int grid, BarrierState *bs, uint64_t timeout_ns, cudaStream_t st) {
+    void *args[] = {(void *)&bs, (void *)&timeout_ns};
+    return cudaLaunchCooperativeKernel((const void *)barrier_selftest_kernel, dim3(grid), dim3(64), args, 0,
+                                       st);
+}
+
+// ===========================================================================
+// explicit instantiations
+// ===========================================================================
+template cudaError_t launch_solve<double>(const SysView<double> &, const SolveCtl &, int, cudaStream_t);
+template cudaError_t launch_solve<cdouble>(const SysView<cdouble> &, const SolveCtl &, int, cudaStream_t);
+template int solve_blocks_per_sm<double>();
+template int solve_blocks_per_sm<cdouble>();
+template cudaError_t launch_ahq<double>(const int64_t *, const int32_t *, const double *, int64_t, int64_t,
+                                        const double *, double *, int, cudaStream_t);
+template cudaError_t launch_ahq<cdouble>(const int64_t *, const int32_t *, const cdouble *, int64_t, int64_t,
+                                         const cdouble *, cdouble *, int, cudaStream_t);
+template cudaError_t launch_spmv_qdot<double>(const SysView<double> &, const double *, double *, double *,
+                                              int, double *, cudaStream_t);
+template cudaError_t launch_spmv_qdot<cdouble>(const SysView<cdouble> &, const cdouble *, cdouble *,
+                                               double *, int, double *, cudaStream_t);
+template int spmv_qdot_grid<double>();
+template int spmv_qdot_grid<cdouble>();
+
+}  // namespace mlb

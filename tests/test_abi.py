@@ -1,0 +1,131 @@
+"""The C-ABI library builds, loads and exports every symbol the header
+declares; struct layouts of the binding match the C compiler's; argument
+validation answers before any GPU work (no compute calls here)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1106_3678_gb300 import build as B
+from paper_1106_3678_gb300 import mlbicgstab as M
+from paper_1106_3678_gb300 import workloads as W
+
+HEADER = os.path.join(B.ROOT, "include", "mlbicgstab.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return M.load()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"\b(mlbicgstab_\w+)\s*\(", text))
+
+
+def test_header_and_binding_agree():
+    assert _declared() == set(M.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], check=True,
+                         capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    for name in _declared():
+        assert name in syms, name
+        assert hasattr(lib, name)
+
+
+def test_struct_layout_matches_c_compiler(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(f'''
+#include <stdio.h>
+#include <stddef.h>
+#include "{HEADER}"
+int main(void) {{
+  printf("%zu %zu %zu %zu\\n", sizeof(mlb_matrix), sizeof(mlb_options),
+         sizeof(mlb_result), sizeof(mlb_info));
+  printf("%zu %zu %zu\\n", offsetof(mlb_options, stream),
+         offsetof(mlb_options, timeout_ns), offsetof(mlb_result, ops));
+  return 0;
+}}''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", str(prog), "-o", str(exe)], check=True)
+    sizes, offs = subprocess.run([str(exe)], check=True, capture_output=True,
+                                 text=True).stdout.split("\n")[:2]
+    assert [int(v) for v in sizes.split()] == [
+        C.sizeof(M.mlb_matrix), C.sizeof(M.mlb_options),
+        C.sizeof(M.mlb_result), C.sizeof(M.mlb_info)]
+    assert [int(v) for v in offs.split()] == [
+        M.mlb_options.stream.offset, M.mlb_options.timeout_ns.offset,
+        M.mlb_result.ops.offset]
+
+
+def test_strerror_and_defaults(lib):
+    assert M.strerror(M.MLB_OK) == "success"
+    assert "timed out" in M.strerror(M.MLB_ERR_TIMEOUT)
+    assert M.strerror(99) == "unknown status code"
+    o = M.mlbicgstab_default_options()
+    assert (o.n, o.precision, o.max_outer, o.grid) == (4, 0, 10, 0)
+    assert o.timeout_ns == 2_000_000_000 and o.Q is None
+
+
+def _raw_create(lib, A, **kw):
+    Mx = M.Matrix(A)
+    o = M.mlbicgstab_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    rc = lib.mlbicgstab_create(C.byref(h), C.byref(Mx.c), None, C.byref(o))
+    return rc, h
+
+
+def test_invalid_arguments_are_rejected_before_gpu_work(lib):
+    A = W.cd2d(4)
+    h = C.c_void_p()
+    assert lib.mlbicgstab_create(C.byref(h), None, None, None) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_create(None, None, None, None) == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, n=0)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, n=65)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, kappa=-1.0)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, precision=7)[0] == M.MLB_ERR_ARG
+    bad = W.CSR(A.row_ptr.copy(), A.col.copy(), A.val.copy(), A.n_rows)
+    bad.col[3] = A.n_rows          # column out of range
+    assert _raw_create(lib, bad)[0] == M.MLB_ERR_ARG
+    bad = W.CSR(A.row_ptr.copy(), A.col.copy(), A.val.copy(), A.n_rows)
+    bad.row_ptr[5], bad.row_ptr[6] = bad.row_ptr[6], bad.row_ptr[5]  # not monotone
+    assert _raw_create(lib, bad)[0] == M.MLB_ERR_ARG
+    Mx = M.Matrix(A)
+    Mx.c.nnz = A.nnz + 1           # nnz disagrees with row_ptr[N]
+    assert lib.mlbicgstab_create(C.byref(h), C.byref(Mx.c), None, None) == M.MLB_ERR_ARG
+    res = M.mlb_result()
+    assert lib.mlbicgstab_solve(None, None, None, 0, 1e-10, 10, C.byref(res),
+                                None, 0) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_solve_batch(None, 0, None, None, 0, None, None,
+                                      None) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_selftest_barrier_timeout(0, 1000) == M.MLB_ERR_ARG
+    lib.mlbicgstab_destroy(None)   # accepted
+
+
+def test_no_cpu_fallback_without_a_device(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    rc, _ = _raw_create(lib, W.cd2d(4))
+    assert rc == M.MLB_ERR_CUDA
+    with pytest.raises(M.MlbError):
+        M.mlbicgstab_create(W.cd2d(4))
+
+
+def test_binding_refuses_to_run_without_library(tmp_path):
+    with pytest.raises(ImportError):
+        M.load(str(tmp_path / "missing.so"))
+    x = np.zeros(3)
+    assert M._ptr(x)[1] == 0

@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA library through its C ABI against the CPU oracle on
+the same seeded inputs.
+
+Tolerances (derived from the arithmetic, not fitted):
+* shadow vectors: both sides evaluate the same generator; log and cos are
+  correctly rounded to within 1 ulp on each side, so entries agree to a
+  few ulp: |Q_gpu - Q_oracle| <= 4 eps max(1, |Q|).
+* y = A x: both sides sum at most w products per row (w = longest row),
+  so each differs from the exact sum by <= gamma_w sum|a||x| (Higham,
+  Thm 3.1, gamma_w = w eps / (1 - w eps)); the difference of the two is at
+  most twice that.  Q^H y: the same bound with N terms plus the propagated
+  difference of y.
+* solves: iteration counts and (j, i) equal; Table 4.3 counters equal;
+  the first iterations' recursive residuals agree to 1e-10 relative
+  (rounding-order differences of ~1e-16 grow by far less than 1e6 in
+  8 steps on these systems); final solution within 1e-8 relative of the
+  oracle's and true residual below tol = 1e-10.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1106_3678_gb300 import mlbicgstab as M
+from paper_1106_3678_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1106_3678_gb300 import build
+    build.build()
+    M.load()
+
+
+def _abs_spmv(A, x):
+    return O.spmv(W.CSR(A.row_ptr, A.col, np.abs(A.val), A.n_rows), np.abs(x))
+
+
+def _gamma(k):
+    return k * EPS / (1 - k * EPS)
+
+
+# ------------------------------------------------------------- shadow Q ----
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_shadow_vectors_match_oracle_generator(cplx):
+    A = W.helmholtz3d_c(8, 6, 5) if cplx else W.cd2d(24)
+    n = 5
+    h = M.mlbicgstab_create(A, n=n, q_seed=1234)
+    Qg = M.mlbicgstab_get_Q(h)
+    Qo = O.q_gauss(1234, A.n_rows, n, complex_=cplx)
+    assert Qg.shape == Qo.shape
+    err = np.abs(Qg - Qo)
+    assert np.all(err <= 4 * EPS * np.maximum(1.0, np.abs(Qo))), err.max()
+
+
+def test_user_Q_is_used_verbatim():
+    A = W.cd2d(16)
+    Q = np.random.default_rng(3).standard_normal((A.n_rows, 3))
+    h = M.mlbicgstab_create(A, n=3, Q=Q)
+    np.testing.assert_array_equal(M.mlbicgstab_get_Q(h), Q)
+
+
+# ------------------------------------------------- fused SpMV + Q^H y ------
+
+def _check_spmv_qdot(A, n, seed=0, grid_rows=None):
+    import torch
+    cplx = np.iscomplexobj(A.val)
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(A.n_rows)
+    if cplx:
+        x = x + 1j * rng.standard_normal(A.n_rows)
+    h = M.mlbicgstab_create(A, n=n, q_seed=seed)
+    dt = torch.complex128 if cplx else torch.float64
+    xd = torch.tensor(x, dtype=dt, device="cuda")
+    yd = torch.empty_like(xd)
+    d = M.mlbicgstab_spmv_qdot(h, xd, yd)
+    y = yd.cpu().numpy()
+    yo = O.spmv(A, x)
+    w = int(np.max(np.diff(A.row_ptr))) + 1
+    bound = 2 * _gamma(w) * _abs_spmv(A, x)
+    assert np.all(np.abs(y - yo) <= bound + 1e-300), np.max(np.abs(y - yo) - bound)
+    Q = M.mlbicgstab_get_Q(h)
+    do = Q.conj().T @ yo
+    bd = (np.abs(Q).T @ np.abs(y - yo)) + 2 * _gamma(A.n_rows) * (np.abs(Q).T @ np.abs(yo))
+    assert np.all(np.abs(d - do) <= bd), (d, do)
+    return h
+
+
+@pytest.mark.parametrize("n", [1, 4, 16])
+def test_spmv_qdot_cd2d(n):
+    _check_spmv_qdot(W.cd2d(32), n)
+
+
+def test_spmv_qdot_cd3d_several_slices_ragged_tail():
+    # N = 23^3 = 12167: not a multiple of 32 (ragged last slice)
+    _check_spmv_qdot(W.cd3d_lognormal(23), 8)
+
+
+def test_spmv_qdot_irregular_rows():
+    # random pattern with row lengths 1..40 plus the diagonal
+    rng = np.random.default_rng(5)
+    M_ = np.zeros((77, 77))
+    for r in range(77):
+        k = rng.integers(0, 40)
+        cols = rng.choice(77, size=k, replace=False)
+        M_[r, cols] = rng.standard_normal(k)
+        M_[r, r] = 5.0
+    _check_spmv_qdot(W.dense_to_csr(M_), 3)
+
+
+def test_spmv_qdot_complex():
+    _check_spmv_qdot(W.helmholtz3d_c(10, 9, 7), 6)
+
+
+def test_spmv_qdot_full_size_cd3d():
+    """The 128^3 workload at full size, every row checked."""
+    _check_spmv_qdot(W.cd3d_lognormal(128), 4)
+
+
+# ------------------------------------------------------------- solves ------
+
+def _gpu_solve(A, b, n, tol, maxit, q_seed=0, Q=None, kappa=0.0, max_outer=0,
+               grid=0, hist=True, x0=None):
+    h = M.mlbicgstab_create(A, n=n, q_seed=q_seed, Q=Q, kappa=kappa,
+                            max_outer=max_outer, grid=grid)
+    x = np.zeros(A.n_rows, dtype=b.dtype) if x0 is None else np.array(x0, copy=True)
+    res, eh = M.mlbicgstab_solve(h, b, x, tol, maxit, hist_cap=(maxit + 1) if hist else 0)
+    return h, x, res, eh
+
+
+def _compare(A, b, n, tol=1e-10, maxit=2000, grid=0, kappa=0.0, Q=None,
+             early=8, early_tol=1e-10):
+    cplx = np.iscomplexobj(A.val)
+    h, x, res, eh = _gpu_solve(A, b, n, tol, maxit, Q=Q, kappa=kappa, grid=grid)
+    Qo = O.q_gauss(0, A.n_rows, n, complex_=cplx) if Q is None else Q
+    ref = O.mlbicgstabt(A, b, np.zeros_like(b), Qo, maxit, tol, kappa,
+                        err_hist=True)
+    assert res.status == 0
+    assert (res.flag, res.iter) == (ref.flag, ref.iter)
+    assert (res.j, res.i) == (ref.j, ref.i)
+    assert res.as_dict()["ops"] == ref.ops
+    k = min(early, ref.iter) + 1
+    np.testing.assert_allclose(eh[:k], ref.err_hist[:k], rtol=early_tol, atol=0)
+    if ref.flag == 0:
+        assert res.true_relres < tol
+        rel = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+        assert rel <= 1e-8, rel
+    return res, ref, x
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 8])
+def test_solve_cd2d_matches_oracle(n):
+    """The 32x32 convection-diffusion workload (N = 1024, one CTA)."""
+    A = W.cd2d(32)
+    _compare(A, W.row_sums(A), n)
+
+
+@pytest.mark.parametrize("grid", [2, 5])
+@pytest.mark.parametrize("n", [1, 4])
+def test_solve_cd2d_multi_cta_grid_barrier(n, grid):
+    """Same system on several CTAs: exercises the grid barrier and the
+    cross-CTA reduction on a small case."""
+    A = W.cd2d(32)
+    _compare(A, W.row_sums(A), n, grid=grid)
+
+
+@pytest.mark.parametrize("m,n", [(16, 4), (23, 8), (30, 3)])
+def test_solve_cd3d_small_matches_oracle(m, n):
+    """Log-normal 3-D systems spanning many slices, ragged last slice."""
+    A = W.cd3d_lognormal(m)
+    b = W.uniform_rhs(A.n_rows, seed=2)
+    _compare(A, b, n, maxit=20000)
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_solve_complex_matches_oracle(n):
+    A = W.helmholtz3d_c(8, 8, 4, k=3.0)
+    _compare(A, W.row_sums(A), n, maxit=3000)
+
+
+def test_solve_kappa_guard_matches_oracle():
+    A = W.cd2d(24, beta=(60.0, 10.0))
+    _compare(A, W.row_sums(A), 3, kappa=0.7)
+
+
+@pytest.mark.parametrize("N,n", [(12, 12), (10, 14), (9, 3)])
+def test_finite_termination_on_gpu(N, n):
+    A, Md, b = W.random_dense_system(N, seed=40 + N)
+    Q = np.random.default_rng(N).standard_normal((N, n))
+    h, x, res, _ = _gpu_solve(A, b, n, 1e-14, 4 * N, Q=Q, hist=False)
+    assert res.flag == 0 and res.iter <= N
+    xs = np.linalg.solve(Md, b)
+    assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+# ------------------------------------------------------- edge cases --------
+
+def test_zero_rhs_and_exact_guess():
+    A = W.cd2d(16)
+    _, x, res, _ = _gpu_solve(A, np.zeros(A.n_rows), 4, 1e-10, 100)
+    assert (res.iter, res.flag, res.err) == (0, 0, 0.0) and not x.any()
+    _, x, res, _ = _gpu_solve(A, W.row_sums(A), 4, 1e-10, 100,
+                              x0=np.ones(A.n_rows))
+    assert res.iter == 0 and res.flag == 0
+
+
+@pytest.mark.parametrize("n,maxit", [(4, 7), (4, 8), (3, 5), (1, 3)])
+def test_iteration_limit(n, maxit):
+    A = W.cd2d(16)
+    b = W.row_sums(A)
+    _, x, res, _ = _gpu_solve(A, b, n, 1e-14, maxit)
+    ref = O.mlbicgstabt(A, b, np.zeros(A.n_rows), O.q_gauss(0, A.n_rows, n), maxit, 1e-14)
+    assert (res.flag, res.iter, res.j, res.i) == (1, maxit, ref.j, ref.i)
+    np.testing.assert_allclose(x, ref.x, rtol=1e-9, atol=1e-12)
+
+
+def test_breakdown_c_zero():
+    A = W.cd2d(6)
+    N = A.n_rows
+    b = np.zeros(N)
+    b[7] = 1.0
+    colk = np.zeros(N)
+    for r in range(N):
+        for k in range(A.row_ptr[r], A.row_ptr[r + 1]):
+            if A.col[k] == 7:
+                colk[r] = A.val[k]
+    i, j = np.nonzero(colk)[0][:2]
+    q = np.zeros(N)
+    q[i], q[j] = colk[j], -colk[i]
+    _, _, res, _ = _gpu_solve(A, b, 1, 1e-10, 50, Q=q[:, None])
+    assert res.flag == -1 and res.iter == 0
+
+
+def test_device_pointers_match_host_pointers():
+    import torch
+    A = W.cd2d(32)
+    b = W.row_sums(A)
+    h = M.mlbicgstab_create(A, n=4)
+    xh = np.zeros(A.n_rows)
+    r1, _ = M.mlbicgstab_solve(h, b, xh, 1e-10, 2000)
+    bd = torch.tensor(b, device="cuda")
+    xd = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    r2, _ = M.mlbicgstab_solve(h, bd, xd, 1e-10, 2000)
+    assert r1.iter == r2.iter
+    np.testing.assert_array_equal(xd.cpu().numpy(), xh)
+
+
+def test_restart_on_true_residual():
+    """max_outer > 0: the solve continues until the true residual meets
+    tol, like the oracle's restart wrapper."""
+    A = W.cd3d_lognormal(16)
+    b = W.uniform_rhs(A.n_rows, seed=2)
+    _, x, res, _ = _gpu_solve(A, b, 4, 1e-10, 20000, max_outer=10, hist=False)
+    ref = O.solve(A, b, np.zeros(A.n_rows), O.q_gauss(0, A.n_rows, 4), 20000, 1e-10)
+    assert res.flag == 0 and res.true_relres < 1e-10
+    assert res.outer == ref.outer and res.iter == ref.iter
+
+
+# ------------------------------------------- full-size 128^3 workload -------
+
+def test_full_size_cd3d_first_iterations_elementwise():
+    """N = 2,097,152 (the benchmark workload, benchmark launch geometry):
+    12 iterations on the GPU against 12 oracle iterations, x compared
+    element by element."""
+    A = W.cd3d_lognormal(128)
+    b = W.uniform_rhs(A.n_rows, seed=2)
+    n = 4
+    h, x, res, eh = _gpu_solve(A, b, n, 1e-10, 12)
+    ref = O.mlbicgstabt(A, b, np.zeros(A.n_rows), O.q_gauss(0, A.n_rows, n), 12,
+                        1e-10, err_hist=True)
+    assert (res.flag, res.iter, res.j, res.i) == (ref.flag, ref.iter, ref.j, ref.i)
+    assert res.as_dict()["ops"] == ref.ops
+    np.testing.assert_allclose(eh[:13], ref.err_hist[:13], rtol=1e-10)
+    scale = np.max(np.abs(ref.x))
+    assert np.max(np.abs(x - ref.x)) <= 1e-9 * scale
+
+
+# ------------------------------------------------- failure detection -------
+
+def test_barrier_wait_times_out_and_device_stays_usable():
+    """A barrier participant that never arrives: every wait gives up after
+    50 ms, the kernel returns, the host reads MLB_ERR_TIMEOUT, and the next
+    solve runs normally."""
+    assert M.mlbicgstab_selftest_barrier_timeout(4, 50_000_000) == M.MLB_ERR_TIMEOUT
+    A = W.cd2d(16)
+    _, _, res, _ = _gpu_solve(A, W.row_sums(A), 4, 1e-10, 1000, hist=False)
+    assert res.flag == 0 and res.status == 0
