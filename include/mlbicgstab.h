@@ -193,6 +193,42 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count,
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d);
 
 /*
+ * Allocation-free variant of mlbicgstab_spmv_qdot: y = A x and d = Q^H y
+ * with every array supplied by the caller in device memory and no handle.
+ * The paper has no counterpart; it exists for callers that cannot allocate
+ * device memory: code inside a framework whose memory pool owns the
+ * device's memory budget, plug-ins whose host application forbids them to
+ * allocate, and latency-critical loops that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.  This call performs no
+ * cudaMalloc, cudaFree or other allocation.
+ *   nrows, nnz, row_ptr, col_idx, values  CSR of A in device memory
+ *                (row_ptr int64, col_idx int32 in [0, nrows): the caller
+ *                guarantees a valid CSR; it is not re-checked here)
+ *   dtype        MLB_F64 or MLB_C128
+ *   x            nrows values (device)
+ *   Q            n columns of leading dimension ldq >= nrows (device)
+ *   n            1 <= n <= 64; larger n returns MLB_ERR_ARG
+ *   y            nrows values (device, written)
+ *   d            n values (device, written)
+ *   stream       cudaStream_t or NULL; the call returns once the work is
+ *                enqueued (no host synchronisation)
+ * Scratch: per-CTA partial sums live in one fixed 512 KiB array of this
+ * library's device memory, held on every GPU that loads the library until
+ * the process exits; the launch uses at most as many CTAs as fit in it.
+ * Calls share that array: two calls that overlap on the GPU (on different
+ * streams, or from different host threads) race and give wrong results.
+ * The first call on a device looks up the array's device address (set-up);
+ * make that first call before any stream capture.  Returns MLB_ERR_ARG for
+ * invalid sizes or non-device pointers, MLB_ERR_CUDA on launch failure.
+ */
+int mlbicgstab_spmv_qdot_noalloc(int64_t nrows, int64_t nnz,
+                                 const int64_t *row_ptr,
+                                 const int32_t *col_idx, const void *values,
+                                 int32_t dtype, const void *x, const void *Q,
+                                 int64_t ldq, int32_t n, void *y, void *d,
+                                 void *stream);
+
+/*
  * Copy Q (N x n, column-major, dtype of A) to host memory.  When Q was
  * drawn from q_seed, real entry e = col*N + row is normal number e and a
  * complex entry e takes normals 2e (re) and 2e+1 (im), where normal number

@@ -26,7 +26,7 @@ EXPORTS = (
     "mlbicgstab_default_options", "mlbicgstab_create", "mlbicgstab_solve",
     "mlbicgstab_solve_batch", "mlbicgstab_spmv_qdot", "mlbicgstab_get_Q",
     "mlbicgstab_info", "mlbicgstab_destroy", "mlbicgstab_strerror",
-    "mlbicgstab_selftest_barrier_timeout",
+    "mlbicgstab_selftest_barrier_timeout", "mlbicgstab_spmv_qdot_noalloc",
 )
 
 
@@ -113,6 +113,9 @@ def load(path: str | None = None):
     lib.mlbicgstab_strerror.argtypes = [C.c_int]
     lib.mlbicgstab_selftest_barrier_timeout.restype = C.c_int
     lib.mlbicgstab_selftest_barrier_timeout.argtypes = [C.c_int32, C.c_int64]
+    lib.mlbicgstab_spmv_qdot_noalloc.restype = C.c_int
+    lib.mlbicgstab_spmv_qdot_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, C.c_int32,
+                                                 P, P, C.c_int64, C.c_int32, P, P, P]
     if path is None:
         _LIB = lib
     return lib
@@ -287,6 +290,28 @@ def mlbicgstab_spmv_qdot(h: Handle, x, y) -> np.ndarray:
     _check(load().mlbicgstab_spmv_qdot(h.ptr, px, py, d.ctypes.data),
            "mlbicgstab_spmv_qdot")
     return d
+
+
+def mlbicgstab_spmv_qdot_noalloc(row_ptr, col_idx, values, x, Q, y, d,
+                                 stream=None) -> None:
+    """Allocation-free y = A x, d = Q^H y.  Every argument is a CUDA tensor:
+    CSR arrays (int64, int32, float64/complex128), x and y (N), Q (n x ldq
+    row-major, i.e. column q of the shadow matrix is Q[q]), d (n).  Only
+    enqueues the work on `stream` (torch.cuda.Stream, raw handle or None)."""
+    N = int(row_ptr.numel()) - 1
+    nnz = int(col_idx.numel())
+    cplx = values.is_complex()
+    n, ldq = int(Q.shape[0]), int(Q.shape[1])
+    ptrs = [_ptr(a) for a in (row_ptr, col_idx, values, x, Q, y, d)]
+    if not all(dv for _, dv in ptrs):
+        raise ValueError("all arrays must be CUDA tensors")
+    st = None
+    if stream is not None:
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = load().mlbicgstab_spmv_qdot_noalloc(
+        N, nnz, ptrs[0][0], ptrs[1][0], ptrs[2][0], MLB_C128 if cplx else MLB_F64,
+        ptrs[3][0], ptrs[4][0], ldq, n, ptrs[5][0], ptrs[6][0], st)
+    _check(rc, "mlbicgstab_spmv_qdot_noalloc")
 
 
 def mlbicgstab_get_Q(h: Handle) -> np.ndarray:
