@@ -42,9 +42,17 @@ UNIT = "solves/s"
 # count of one full solve on the GPU path, used only to convert the
 # reference arm's per-iteration sample into solves/sec.
 WORKLOADS = {
-    "cd3d128_n4_fp64": dict(m=128, n=4, tol=1e-10, maxit=40000, iters=18468),
+    "cd3d128_n4_fp64": dict(m=128, n=4, tol=1e-10, maxit=40000, iters=18468, precision=0),
+    "cd3d128_n4_refined": dict(m=128, n=4, tol=1e-10, maxit=80000, iters=None, precision=1,
+                               inner_tol=1e-5),
 }
+for _n in (1, 8, 16):
+    WORKLOADS[f"cd3d128_n{_n}_fp64"] = dict(m=128, n=_n, tol=1e-10, maxit=60000, iters=None,
+                                           precision=0)
+    WORKLOADS[f"cd3d128_n{_n}_refined"] = dict(m=128, n=_n, tol=1e-10, maxit=120000, iters=None,
+                                              precision=1, inner_tol=1e-5)
 DEFAULT = "cd3d128_n4_fp64"
+VARIANTS = ["cd3d128_n4_refined"]
 
 
 def _load_peaks():
@@ -64,13 +72,17 @@ def _make_inputs(wl):
     return A, b
 
 
+def _prec_name(wl):
+    return "fp32-inner/fp64-refined" if wl.get("precision", 0) == 1 else "fp64"
+
+
 def _config(wl, A, extra=None):
     cfg = {
         "workload": (f"cd3d_lognormal {wl['m']}^3 (N={A.n_rows:,}, nnz={A.nnz:,}), "
-                     f"n={wl['n']}, FP64, b~U[-1,1] seed 2, x0=0, Q~N(0,1) seed 0, "
-                     f"tol {wl['tol']:g}, maxit {wl['maxit']}"),
+                     f"n={wl['n']}, {_prec_name(wl)}, b~U[-1,1] seed 2, x0=0, "
+                     f"Q~N(0,1) seed 0, tol {wl['tol']:g}, maxit {wl['maxit']}"),
         "N": A.n_rows, "nnz": A.nnz, "n": wl["n"], "tol": wl["tol"],
-        "maxit": wl["maxit"], "precision": "fp64",
+        "maxit": wl["maxit"], "precision": _prec_name(wl),
         "l2": "inputs larger than L2 (no flush)",
     }
     if extra:
@@ -188,6 +200,34 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def _timed_solves(M, h, b_d, x_d, wl, stream, steps, warmup, barrier):
+    """Warm-up solves, then `steps` timed solves; returns (total_ms, results)."""
+    import torch
+    for _ in range(warmup):
+        with torch.cuda.stream(stream):
+            x_d.zero_()
+        M.mlbicgstab_solve(h, b_d, x_d, wl["tol"], wl["maxit"])
+    results = []
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            x_d.zero_()
+        res, _ = M.mlbicgstab_solve(h, b_d, x_d, wl["tol"], wl["maxit"])
+        results.append(res.as_dict())
+    ev1.record(stream)
+    barrier()
+    return ev0.elapsed_time(ev1), results
+
+
+def _create(M, A, wl, stream):
+    return M.mlbicgstab_create(A, n=wl["n"], q_seed=0, max_outer=10, stream=stream,
+                               precision=wl.get("precision", 0),
+                               inner_tol=wl.get("inner_tol"))
+
+
 def run_ours(args, wl):
     import torch
 
@@ -204,7 +244,7 @@ def run_ours(args, wl):
     A, b = _make_inputs(wl)
     N = A.n_rows
     stream = torch.cuda.Stream()
-    h = M.mlbicgstab_create(A, n=wl["n"], q_seed=0, max_outer=10, stream=stream)
+    h = _create(M, A, wl, stream)
     info = M.mlbicgstab_info(h)
     b_d = torch.tensor(b, dtype=torch.float64, device=dev)
     x_d = torch.zeros(N, dtype=torch.float64, device=dev)
@@ -215,33 +255,45 @@ def run_ours(args, wl):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up solves (untimed)
-    for _ in range(args.warmup):
-        with torch.cuda.stream(stream):
-            x_d.zero_()
-        res, _ = M.mlbicgstab_solve(h, b_d, x_d, wl["tol"], wl["maxit"])
-
     clocks = ClockSampler(torch.cuda.current_device())
-    results = []
-    barrier()
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            x_d.zero_()
-        res, _ = M.mlbicgstab_solve(h, b_d, x_d, wl["tol"], wl["maxit"])
-        results.append(res.as_dict())
-    ev1.record(stream)
-    barrier()
+    total_ms, results = _timed_solves(M, h, b_d, x_d, wl, stream, args.steps, args.warmup, barrier)
     clk = clocks.stop()
-    total_ms = ev0.elapsed_time(ev1)
+
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
+
+    # variants on the same matrix: other precisions / shadow counts
+    variants = []
+    for name in ([] if args.no_variants else (args.variant or VARIANTS)):
+        vwl = dict(WORKLOADS[name])
+        if args.maxit > 0:
+            vwl["maxit"] = args.maxit
+        hv = _create(M, A, vwl, stream)
+        vms, vres = _timed_solves(M, hv, b_d, x_d, vwl, stream, max(1, args.variant_steps),
+                                  1, barrier)
+        hv.destroy()
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([vms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            vms = float(t.item())
+        vsteps = len(vres)
+        kb = sum(r["bytes"] for r in vres)
+        kms = sum(r["kernel_ms"] for r in vres)
+        variants.append({
+            "workload": name, "precision": _prec_name(vwl), "n": vwl["n"],
+            "value": ws * vsteps / (vms * 1e-3), "unit": UNIT,
+            "ms_per_step": vms / vsteps,
+            "iters_per_solve": [r["iter"] for r in vres],
+            "outer": [r["outer"] for r in vres],
+            "flags": [r["flag"] for r in vres],
+            "true_relres": [r["true_relres"] for r in vres],
+            "achieved_gbs": kb / (kms * 1e-3) / 1e9 if kms > 0 else None,
+        })
 
     # end to end through the C ABI with pinned host buffers
     b_h = torch.tensor(b, dtype=torch.float64).pin_memory()
@@ -306,6 +358,7 @@ def run_ours(args, wl):
         "gpu_launches": args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "variants": [dict(v, speedup_vs_fp64=v["value"] / value) for v in variants],
     }
     print(json.dumps(line), flush=True)
     h.destroy()
@@ -327,6 +380,10 @@ def main():
                     help="reference arm: iterations of a full solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant", action="append", choices=sorted(WORKLOADS),
+                    help="extra workloads measured on the same matrix (repeatable)")
+    ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--maxit", type=int, default=0,
                     help="override the iteration cap (short runs for profiling)")
     args = ap.parse_args()

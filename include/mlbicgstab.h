@@ -86,14 +86,15 @@ typedef struct {
                              standard minimisation step */
     int32_t max_outer;    /* FP64: restarts from the current x while the
                              recursive residual met tol but the true one did
-                             not (default 10).  Refined: maximum refinement
-                             steps (default 30). */
+                             not.  Refined: maximum refinement steps (each
+                             one FP32 inner solve).  Default 10. */
     int32_t grid;         /* CTAs of the persistent solve kernel; 0 = auto
                              (all SMs x occupancy, fewer for small N) */
     double inner_tol;     /* refined mode: relative tolerance of each FP32
                              inner solve (default 1e-5) */
     int64_t inner_maxit;  /* refined mode: iteration cap of one inner solve
-                             (default 10000) */
+                             (default 1e6; all inner iterations together
+                             are capped by the maxit of the solve) */
     void *stream;         /* cudaStream_t for all work of this handle;
                              NULL = the legacy default stream */
     int64_t timeout_ns;   /* limit of every device-side wait (grid barrier
@@ -170,13 +171,16 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device,
 
 /*
  * Solve `count` independent systems, one handle each (created with the same
- * dtype and precision), in one persistent launch: each CTA takes systems
- * from a shared queue, largest first, and runs the same method as
- * mlbicgstab_solve with a CTA-wide barrier in place of the grid barrier.
+ * dtype, precision and device), in one persistent launch: each CTA takes
+ * systems from a device queue, largest first (by N + nnz), and runs the
+ * same method as mlbicgstab_solve (restarts and refinement included) with
+ * CTA-wide barriers and shared-memory reductions.
  *   b[s], x[s]  per-system pointers as in mlbicgstab_solve (on_device
  *               applies to all).  tol[s], maxit[s] per system.
- *   res         `count` results.
- * The stream of hs[0] is used.
+ *   res         `count` results; kernel_ms is the time of the whole launch.
+ * The stream of hs[0] is used; hs[0] keeps a workspace (items, order,
+ * results) that grows to the largest batch it has run.  No residual
+ * history is recorded.  Handles must not be used by other calls meanwhile.
  */
 int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count,
                            const void *const *b, void *const *x,

@@ -32,6 +32,11 @@ struct mlb_handle {
     void *sval = nullptr;
     void *Q = nullptr, *F = nullptr, *G = nullptr, *W = nullptr;
     void *x = nullptr, *r = nullptr, *z = nullptr, *b = nullptr;
+    // refined mode: FP32 copies of the matrix values, Q, F and the inner
+    // solver's vectors (x, r, b above stay FP64: solution, true residual,
+    // right-hand side)
+    void *sval32 = nullptr, *Q32 = nullptr, *F32 = nullptr, *G32 = nullptr, *W32 = nullptr;
+    void *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *b32 = nullptr;
     double *partials = nullptr;
     BarrierState *bar = nullptr;
     DevResult *dres = nullptr;
@@ -41,6 +46,11 @@ struct mlb_handle {
     double *qd_out = nullptr;
     int qd_grid = 0;
     DevResult *hres = nullptr;  // pinned
+    // batch workspace (owned by the first handle of a batch call)
+    void *bws = nullptr;
+    size_t bws_bytes = 0;
+    void *bhost = nullptr;      // pinned staging of items and results
+    size_t bhost_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t device_bytes = 0;
     std::vector<void *> allocs;
@@ -174,8 +184,46 @@ SysView<T> make_view(const mlb_handle *h) {
     v.x = (T *)h->x;
     v.r = (T *)h->r;
     v.z = (T *)h->z;
-    v.b = (const T *)h->b;
+    v.b = (T *)h->b;
     v.n = h->n;
+    return v;
+}
+
+template <typename T32>
+SysView<T32> make_view32(const mlb_handle *h) {
+    SysView<T32> v;
+    v.N = h->N;
+    v.ld = h->ld;
+    v.nnz = h->nnz;
+    v.nslices = h->nslices;
+    v.slice_ptr = h->slice_ptr;
+    v.scol = h->scol;
+    v.sval = (const T32 *)h->sval32;
+    v.Q = (const T32 *)h->Q32;
+    v.F = (const T32 *)h->F32;
+    v.G = (T32 *)h->G32;
+    v.W = (T32 *)h->W32;
+    v.x = (T32 *)h->x32;
+    v.r = (T32 *)h->r32;
+    v.z = (T32 *)h->z32;
+    v.b = (T32 *)h->b32;
+    v.n = h->n;
+    return v;
+}
+
+template <typename T64>
+RefView<T64> make_ref_view(const mlb_handle *h) {
+    RefView<T64> v;
+    v.N = h->N;
+    v.ld = h->ld;
+    v.nnz = h->nnz;
+    v.nslices = h->nslices;
+    v.slice_ptr = h->slice_ptr;
+    v.scol = h->scol;
+    v.sval = (const T64 *)h->sval;
+    v.x = (T64 *)h->x;
+    v.b = (const T64 *)h->b;
+    v.r = (T64 *)h->r;
     return v;
 }
 
@@ -230,19 +278,22 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     const size_t vb = (size_t)ld * es;
     if ((rc = dev_alloc(h, &h->Q, vb * n))) return rc;
     if (n > 1 && (rc = dev_alloc(h, &h->F, vb * (n - 1)))) return rc;
-    if ((rc = dev_alloc(h, &h->G, vb * n))) return rc;
-    if ((rc = dev_alloc(h, &h->W, vb * n))) return rc;
+    const bool refined = h->precision == MLB_PREC_FP32_REFINED;
+    if (!refined) {
+        if ((rc = dev_alloc(h, &h->G, vb * n))) return rc;
+        if ((rc = dev_alloc(h, &h->W, vb * n))) return rc;
+        if ((rc = dev_alloc(h, &h->z, vb))) return rc;
+        MLB_CUDA(cudaMemsetAsync(h->G, 0, vb * n, st));
+        MLB_CUDA(cudaMemsetAsync(h->W, 0, vb * n, st));
+        MLB_CUDA(cudaMemsetAsync(h->z, 0, vb, st));
+    }
     if ((rc = dev_alloc(h, &h->x, vb))) return rc;
     if ((rc = dev_alloc(h, &h->r, vb))) return rc;
-    if ((rc = dev_alloc(h, &h->z, vb))) return rc;
     if ((rc = dev_alloc(h, &h->b, vb))) return rc;
     MLB_CUDA(cudaMemsetAsync(h->Q, 0, vb * n, st));
     if (n > 1) MLB_CUDA(cudaMemsetAsync(h->F, 0, vb * (n - 1), st));
-    MLB_CUDA(cudaMemsetAsync(h->G, 0, vb * n, st));
-    MLB_CUDA(cudaMemsetAsync(h->W, 0, vb * n, st));
     MLB_CUDA(cudaMemsetAsync(h->x, 0, vb, st));
     MLB_CUDA(cudaMemsetAsync(h->r, 0, vb, st));
-    MLB_CUDA(cudaMemsetAsync(h->z, 0, vb, st));
     MLB_CUDA(cudaMemsetAsync(h->b, 0, vb, st));
 
     // shadow vectors
@@ -303,10 +354,36 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         if (e != cudaSuccess) return MLB_ERR_CUDA;
     }
 
+    // refined mode: FP32 copies of the values, Q and F; FP32 work vectors
+    if (refined) {
+        const size_t vb32 = vb / 2;
+        if ((rc = dev_alloc(h, &h->sval32, (size_t)h->nnz_pad * es / 2))) return rc;
+        if ((rc = dev_alloc(h, &h->Q32, vb32 * n))) return rc;
+        if (n > 1 && (rc = dev_alloc(h, &h->F32, vb32 * (n - 1)))) return rc;
+        if ((rc = dev_alloc(h, &h->G32, vb32 * n))) return rc;
+        if ((rc = dev_alloc(h, &h->W32, vb32 * n))) return rc;
+        if ((rc = dev_alloc(h, &h->x32, vb32))) return rc;
+        if ((rc = dev_alloc(h, &h->r32, vb32))) return rc;
+        if ((rc = dev_alloc(h, &h->z32, vb32))) return rc;
+        if ((rc = dev_alloc(h, &h->b32, vb32))) return rc;
+        MLB_CUDA(cudaMemsetAsync(h->G32, 0, vb32 * n, st));
+        MLB_CUDA(cudaMemsetAsync(h->W32, 0, vb32 * n, st));
+        MLB_CUDA(cudaMemsetAsync(h->x32, 0, vb32, st));
+        MLB_CUDA(cudaMemsetAsync(h->r32, 0, vb32, st));
+        MLB_CUDA(cudaMemsetAsync(h->z32, 0, vb32, st));
+        MLB_CUDA(cudaMemsetAsync(h->b32, 0, vb32, st));
+        MLB_CUDA(launch_narrow((const double *)h->sval, (float *)h->sval32, h->nnz_pad * (int64_t)es / 8, st));
+        MLB_CUDA(launch_narrow((const double *)h->Q, (float *)h->Q32, ld * (int64_t)n * (int64_t)es / 8, st));
+        if (n > 1)
+            MLB_CUDA(launch_narrow((const double *)h->F, (float *)h->F32, ld * (int64_t)(n - 1) * (int64_t)es / 8,
+                                   st));
+    }
+
     // launch geometry and scratch
     int sms = 0;
     MLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    const int bps = cplx ? solve_blocks_per_sm<cdouble>() : solve_blocks_per_sm<double>();
+    const int bps = refined ? (cplx ? refine_blocks_per_sm<cfloat, cdouble>() : refine_blocks_per_sm<float, double>())
+                            : (cplx ? solve_blocks_per_sm<cdouble>() : solve_blocks_per_sm<double>());
     if (bps < 1) return MLB_ERR_CUDA;
     const int64_t nchunk = ld * (int64_t)es / 16;
     int64_t want = (nchunk + kThreads - 1) / kThreads;
@@ -337,6 +414,8 @@ void release(mlb_handle *h) {
     h->allocs.clear();
     if (h->err_hist) cudaFree(h->err_hist);
     if (h->hres) cudaFreeHost(h->hres);
+    if (h->bws) cudaFree(h->bws);
+    if (h->bhost) cudaFreeHost(h->bhost);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     cudaGetLastError();
@@ -357,7 +436,7 @@ void mlbicgstab_default_options(mlb_options *o) {
     o->max_outer = 10;
     o->grid = 0;
     o->inner_tol = 1e-5;
-    o->inner_maxit = 10000;
+    o->inner_maxit = 1000000;
     o->stream = nullptr;
     o->timeout_ns = 2000000000LL;
 }
@@ -390,7 +469,6 @@ int mlbicgstab_create(mlb_handle **out, const mlb_matrix *A, const mlb_matrix *A
         if (rc) return rc;
         if (AH->nrows != A->nrows || AH->dtype != A->dtype) return MLB_ERR_ARG;
     }
-    if (o.precision == MLB_PREC_FP32_REFINED) return MLB_ERR_UNSUPPORTED;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
         cudaGetLastError();
@@ -477,8 +555,20 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     ctl.timeout_ns = h->timeout_ns;
     MLB_CUDA(cudaEventRecord(h->ev0, st));
     cudaError_t e;
-    if (h->dtype == MLB_C128) e = launch_solve<cdouble>(make_view<cdouble>(h), ctl, h->grid, st);
-    else e = launch_solve<double>(make_view<double>(h), ctl, h->grid, st);
+    if (h->precision == MLB_PREC_FP32_REFINED) {
+        RefCtl rc;
+        rc.inner_tol = h->inner_tol;
+        rc.inner_maxit = h->inner_maxit;
+        if (h->dtype == MLB_C128)
+            e = launch_refine<cfloat, cdouble>(make_view32<cfloat>(h), make_ref_view<cdouble>(h), ctl, rc, h->grid,
+                                               st);
+        else
+            e = launch_refine<float, double>(make_view32<float>(h), make_ref_view<double>(h), ctl, rc, h->grid, st);
+    } else if (h->dtype == MLB_C128) {
+        e = launch_solve<cdouble>(make_view<cdouble>(h), ctl, h->grid, st);
+    } else {
+        e = launch_solve<double>(make_view<double>(h), ctl, h->grid, st);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return MLB_ERR_CUDA;
@@ -514,8 +604,150 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
 int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *const *b, void *const *x,
                            int32_t on_device, const double *tol, const int64_t *maxit, mlb_result *res) {
     if (!hs || count <= 0 || !b || !x || !tol || !maxit || !res) return MLB_ERR_ARG;
-    (void)on_device;
-    return MLB_ERR_UNSUPPORTED;
+    if (on_device != 0 && on_device != 1) return MLB_ERR_ARG;
+    mlb_handle *h0 = hs[0];
+    if (!h0) return MLB_ERR_ARG;
+    for (int32_t s = 0; s < count; ++s) {
+        const mlb_handle *h = hs[s];
+        if (!h || !b[s] || !x[s] || !(tol[s] >= 0.0) || maxit[s] < 0) return MLB_ERR_ARG;
+        if (h->dtype != h0->dtype || h->precision != h0->precision || h->device != h0->device)
+            return MLB_ERR_ARG;
+    }
+    memset(res, 0, sizeof(mlb_result) * (size_t)count);
+    MLB_CUDA(cudaSetDevice(h0->device));
+    cudaStream_t st = h0->stream;
+    const bool refined = h0->precision == MLB_PREC_FP32_REFINED;
+    const bool cplx = h0->dtype == MLB_C128;
+    const size_t item_bytes = refined ? (cplx ? sizeof(BatchItemR<cfloat, cdouble>) : sizeof(BatchItemR<float, double>))
+                                      : (cplx ? sizeof(BatchItem<cdouble>) : sizeof(BatchItem<double>));
+    // workspace: [queue (256 B)] [order: count ints, padded] [items] [results]
+    const size_t off_order = 256;
+    const size_t off_items = off_order + ((size_t)count * 4 + 255) / 256 * 256;
+    const size_t off_res = off_items + ((size_t)count * item_bytes + 255) / 256 * 256;
+    const size_t need = off_res + (size_t)count * sizeof(DevResult);
+    if (need > h0->bws_bytes) {
+        if (h0->bws) cudaFree(h0->bws);
+        h0->bws = nullptr;
+        h0->bws_bytes = 0;
+        if (cudaMalloc(&h0->bws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return MLB_ERR_OOM;
+        }
+        h0->bws_bytes = need;
+    }
+    if (need > h0->bhost_bytes) {
+        if (h0->bhost) cudaFreeHost(h0->bhost);
+        h0->bhost = nullptr;
+        h0->bhost_bytes = 0;
+        if (cudaMallocHost(&h0->bhost, need) != cudaSuccess) {
+            cudaGetLastError();
+            return MLB_ERR_OOM;
+        }
+        h0->bhost_bytes = need;
+    }
+    char *dws = (char *)h0->bws;
+    char *hws = (char *)h0->bhost;
+    DevResult *dres = (DevResult *)(dws + off_res);
+    // largest systems first (longest-processing-time order)
+    std::vector<int> order(count);
+    for (int s = 0; s < count; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return hs[a]->nnz + hs[a]->N > hs[c]->nnz + hs[c]->N; });
+    memset(hws, 0, off_items);
+    memcpy(hws + off_order, order.data(), (size_t)count * 4);
+    for (int s = 0; s < count; ++s) {
+        const mlb_handle *h = hs[s];
+        SolveCtl ctl;
+        memset(&ctl, 0, sizeof(ctl));
+        ctl.tol = tol[s];
+        ctl.maxit = maxit[s];
+        ctl.kappa = h->kappa;
+        ctl.max_outer = h->max_outer;
+        ctl.res = dres + s;
+        ctl.timeout_ns = h->timeout_ns;
+        char *dst = hws + off_items + (size_t)s * item_bytes;
+        if (refined) {
+            RefCtl rc;
+            rc.inner_tol = h->inner_tol;
+            rc.inner_maxit = h->inner_maxit;
+            if (cplx) {
+                BatchItemR<cfloat, cdouble> it{make_view32<cfloat>(h), make_ref_view<cdouble>(h), ctl, rc};
+                memcpy(dst, &it, sizeof(it));
+            } else {
+                BatchItemR<float, double> it{make_view32<float>(h), make_ref_view<double>(h), ctl, rc};
+                memcpy(dst, &it, sizeof(it));
+            }
+        } else if (cplx) {
+            BatchItem<cdouble> it{make_view<cdouble>(h), ctl};
+            memcpy(dst, &it, sizeof(it));
+        } else {
+            BatchItem<double> it{make_view<double>(h), ctl};
+            memcpy(dst, &it, sizeof(it));
+        }
+    }
+    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind outk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int s = 0; s < count; ++s) {
+        const size_t nb = (size_t)hs[s]->N * hs[s]->esize;
+        MLB_CUDA(cudaMemcpyAsync(hs[s]->b, b[s], nb, in, st));
+        MLB_CUDA(cudaMemcpyAsync(hs[s]->x, x[s], nb, in, st));
+    }
+    MLB_CUDA(cudaMemcpyAsync(dws, hws, off_res, cudaMemcpyHostToDevice, st));
+    int sms = 0;
+    MLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h0->device));
+    int bps = refined ? (cplx ? batch_refine_blocks_per_sm<cfloat, cdouble>() : batch_refine_blocks_per_sm<float, double>())
+                      : (cplx ? batch_blocks_per_sm<cdouble>() : batch_blocks_per_sm<double>());
+    if (bps < 1) return MLB_ERR_CUDA;
+    const int grid = std::min(count, sms * bps);
+    const int *dorder = (const int *)(dws + off_order);
+    unsigned *queue = (unsigned *)dws;
+    const void *ditems = dws + off_items;
+    MLB_CUDA(cudaEventRecord(h0->ev0, st));
+    cudaError_t e;
+    if (refined) {
+        if (cplx)
+            e = launch_batch_refine<cfloat, cdouble>((const BatchItemR<cfloat, cdouble> *)ditems, dorder, count, queue,
+                                                     grid, st);
+        else
+            e = launch_batch_refine<float, double>((const BatchItemR<float, double> *)ditems, dorder, count, queue,
+                                                   grid, st);
+    } else if (cplx) {
+        e = launch_batch<cdouble>((const BatchItem<cdouble> *)ditems, dorder, count, queue, grid, st);
+    } else {
+        e = launch_batch<double>((const BatchItem<double> *)ditems, dorder, count, queue, grid, st);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    MLB_CUDA(cudaEventRecord(h0->ev1, st));
+    for (int s = 0; s < count; ++s) {
+        const size_t nb = (size_t)hs[s]->N * hs[s]->esize;
+        MLB_CUDA(cudaMemcpyAsync(x[s], hs[s]->x, nb, outk, st));
+    }
+    DevResult *hres = (DevResult *)(hws + off_res);
+    MLB_CUDA(cudaMemcpyAsync(hres, dres, (size_t)count * sizeof(DevResult), cudaMemcpyDeviceToHost, st));
+    MLB_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h0->ev0, h0->ev1);
+    int rc = MLB_OK;
+    for (int s = 0; s < count; ++s) {
+        const DevResult &d = hres[s];
+        res[s].flag = d.flag;
+        res[s].j = d.j;
+        res[s].i = d.i;
+        res[s].status = d.status;
+        res[s].iter = d.iter;
+        res[s].spmv = d.spmv;
+        res[s].outer = d.outer;
+        res[s].err = d.err;
+        res[s].true_relres = d.true_relres;
+        res[s].bytes = d.bytes;
+        res[s].kernel_ms = ms;
+        for (int q = 0; q < 5; ++q) res[s].ops[q] = d.ops[q];
+        if (d.status != 0) rc = MLB_ERR_TIMEOUT;
+    }
+    return rc;
 }
 
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
@@ -527,12 +759,12 @@ int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
     // x is read through the padded internal buffer so that every gather
     // stays inside an allocation of ld entries
     const size_t nb = (size_t)h->N * h->esize;
-    MLB_CUDA(cudaMemcpyAsync(h->z, x, nb, cudaMemcpyDeviceToDevice, st));
+    MLB_CUDA(cudaMemcpyAsync(h->b, x, nb, cudaMemcpyDeviceToDevice, st));
     if (h->dtype == MLB_C128)
-        e = launch_spmv_qdot<cdouble>(make_view<cdouble>(h), (const cdouble *)h->z, (cdouble *)h->r,
+        e = launch_spmv_qdot<cdouble>(make_view<cdouble>(h), (const cdouble *)h->b, (cdouble *)h->r,
                                       h->qd_partials, h->qd_grid, h->qd_out, st);
     else
-        e = launch_spmv_qdot<double>(make_view<double>(h), (const double *)h->z, (double *)h->r,
+        e = launch_spmv_qdot<double>(make_view<double>(h), (const double *)h->b, (double *)h->r,
                                      h->qd_partials, h->qd_grid, h->qd_out, st);
     if (e != cudaSuccess) {
         cudaGetLastError();

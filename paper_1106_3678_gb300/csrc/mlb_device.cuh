@@ -196,51 +196,57 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-// Barrier state in global memory (zeroed before the first launch).
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Barrier state in global memory (zeroed before every launch).
 struct BarrierState {
-    unsigned count;   // arrivals in the current generation
-    unsigned gen;     // generation counter
+    unsigned count;   // arrivals since the launch began (monotonic)
+    unsigned pad0;
     int status;       // 0, or an MLB_ERR_* code set by a CTA that gave up
-    int pad;
+    int pad1;
 };
 
 constexpr int kStatusTimeout = 4;  // == MLB_ERR_TIMEOUT
 
-// All `expected` CTAs of the launch meet here.  Thread 0 of each CTA
-// arrives with a release, spins with acquire loads for at most timeout_ns
-// (checking for another CTA's failure), and on expiry records
-// kStatusTimeout.  Returns false (uniformly in the CTA) when the barrier
-// failed; the caller must then return from the kernel.
-__device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned expected,
-                                             uint64_t timeout_ns, int *s_flag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        unsigned gen = ld_acquire_u32(&bs->gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&bs->count, 1u);
-        if (arrived == expected - 1) {
-            atomicExch(&bs->count, 0u);
-            __threadfence();
-            st_release_u32(&bs->gen, gen + 1);
-        } else {
-            const uint64_t t0 = globaltimer_ns();
-            unsigned spins = 0;
-            while (ld_acquire_u32(&bs->gen) == gen) {
-                if ((++spins & 63u) == 0) {
-                    if (ld_relaxed_i32(&bs->status) != 0) { ok = 0; break; }
-                    if (globaltimer_ns() - t0 > timeout_ns) {
-                        atomicCAS(&bs->status, 0, kStatusTimeout);
-                        ok = 0;
-                        break;
-                    }
-                }
-                __nanosleep(32);
+// Arrive-and-wait of one CTA, executed by thread 0 only, after the CTA's
+// writes have been ordered before it (a __syncthreads, or thread 0's own
+// writes).  `epoch` counts the barriers this CTA has passed; all CTAs pass
+// the same sequence, so barrier e completes when the counter reaches
+// e * expected.  The spin is bounded by timeout_ns (%globaltimer) and
+// gives up early when another CTA has already recorded a failure.
+__device__ __forceinline__ bool grid_arrive_wait(BarrierState *bs, unsigned &epoch, unsigned expected,
+                                                 uint64_t timeout_ns) {
+    epoch += 1;
+    const unsigned target = epoch * expected;
+    red_release_add_u32(&bs->count, 1u);
+    uint64_t t0 = 0;
+    unsigned spins = 0;
+    while ((int)(ld_acquire_u32(&bs->count) - target) < 0) {
+        if ((++spins & 31u) == 0) {
+            if (ld_relaxed_i32(&bs->status) != 0) return false;
+            const uint64_t t = globaltimer_ns();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > timeout_ns) {
+                atomicCAS(&bs->status, 0, kStatusTimeout);
+                return false;
             }
         }
-        __threadfence();
-        *s_flag = ok;
+        __nanosleep(16);
     }
+    fence_acq_rel_gpu();
+    return true;
+}
+
+// Whole-CTA grid barrier: every thread calls it; returns false (uniformly
+// in the CTA) when the wait failed, and the caller must then return.
+__device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned &epoch, unsigned expected,
+                                             uint64_t timeout_ns, int *s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_flag = grid_arrive_wait(bs, epoch, expected, timeout_ns) ? 1 : 0;
     __syncthreads();
     return *s_flag != 0;
 }

@@ -67,7 +67,7 @@ struct SysView {
     const T *F;                 // ld x (n-1), F = A^H Q(:,0:n-2)
     T *G, *W;                   // ld x n rings
     T *x, *r, *z;               // ld
-    const T *b;                 // ld
+    T *b;                       // ld (written only by the refined-mode inner start)
     int n;
 };
 
@@ -78,7 +78,7 @@ struct SolveCtl {
     int max_outer;
     double *err_hist;           // device, may be null
     int64_t hist_cap;
-    double *partials;           // [2][gridDim][kMaxSums]
+    double *partials;           // [2][kMaxSums][gridDim]
     BarrierState *bar;
     DevResult *res;
     uint64_t timeout_ns;
@@ -111,12 +111,159 @@ __device__ __forceinline__ cfloat ldcs_val(const cfloat *p) {
     return {v.x, v.y};
 }
 
+// FP32 counterpart of an FP64 element type, and the FP64 element type of
+// an FP32 one (refined mode).
+template <typename T> struct wide_of { using type = T; };
+template <> struct wide_of<float> { using type = double; };
+template <> struct wide_of<cfloat> { using type = cdouble; };
+template <typename T> struct is_narrow { static constexpr bool value = false; };
+template <> struct is_narrow<float> { static constexpr bool value = true; };
+template <> struct is_narrow<cfloat> { static constexpr bool value = true; };
+
+__device__ __forceinline__ float narrow_scaled(double v, double s) { return (float)(v * s); }
+__device__ __forceinline__ cfloat narrow_scaled(cdouble v, double s) {
+    return {(float)(v.re * s), (float)(v.im * s)};
+}
+
+// SELL-32 product over this thread's slices: for every row,
+// y = sum_k a_{row,k} xin[col_k], then epi(row, y, acc).  One warp per
+// 32-row slice, slices gwarp, gwarp + nwarps, ...
+template <typename T, typename Epi, typename AccArr>
+__device__ __forceinline__ void sell_spmv(int64_t nslices, const int64_t *slice_ptr, const int32_t *scol,
+                                          const T *sval, const T *xin, int64_t gwarp, int64_t nwarps,
+                                          int lane, Epi epi, AccArr &acc) {
+    for (int64_t s = gwarp; s < nslices; s += nwarps) {
+        const int64_t off = __ldg(slice_ptr + s);
+        const int w = (int)((__ldg(slice_ptr + s + 1) - off) >> 5);
+        const int32_t *cp = scol + off + lane;
+        const T *vp = sval + off + lane;
+        T sum{};
+        int k = 0;
+        for (; k + 4 <= w; k += 4) {
+            int32_t cc[4];
+            T vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cc[u] = __ldcs(cp + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) vv[u] = ldcs_val(vp + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sum = efma(vv[u], xin[cc[u]], sum);
+        }
+        if (k < w) {
+            int32_t cc[3];
+            T vv[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+                if (k + u < w) cc[u] = __ldcs(cp + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+                if (k + u < w) vv[u] = ldcs_val(vp + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+                if (k + u < w) sum = efma(vv[u], xin[cc[u]], sum);
+        }
+        epi(s * 32 + lane, sum, acc);
+    }
+}
+
 // Coefficient from reduced sums (re[, im]).
 template <typename T>
 __device__ __forceinline__ typename coef_of<T>::type mk_coef(const double *v) {
     if constexpr (is_cx<T>::value) return cdouble{v[0], v[1]};
     else return v[0];
 }
+
+// Synchronisation state of one CTA within the team of CTAs that solves one
+// system: the whole grid (a single solve), or the CTA alone (a batch, one
+// system per CTA).  Every CTA of a team passes the same sequence of
+// barriers and reductions, so `epoch` and the slots advance in lock step.
+// Several engines in one kernel share one GridSync.
+struct GridSync {
+    unsigned nblocks;   // CTAs in the team
+    unsigned bid;       // this CTA's rank in the team
+    BarrierState *bar;
+    double *partials;   // [2][kMaxSums][gridDim]
+    double *red;        // shared, 2 * 32 * kMaxSums
+    int *sflag;         // shared
+    uint64_t timeout_ns;
+    unsigned epoch;
+    int slot, rslot;
+    bool ok;            // false once a barrier failed
+
+    // Team = the whole grid.
+    __device__ GridSync(BarrierState *b, double *p, double *r, int *f, uint64_t to)
+        : nblocks(gridDim.x), bid(blockIdx.x), bar(b), partials(p), red(r), sflag(f), timeout_ns(to), epoch(0),
+          slot(0), rslot(0), ok(true) {}
+    // Team = this CTA alone.
+    __device__ GridSync(double *r, int *f)
+        : nblocks(1), bid(0), bar(nullptr), partials(nullptr), red(r), sflag(f), timeout_ns(0), epoch(0), slot(0),
+          rslot(0), ok(true) {}
+
+    // Thread 0 arrives/waits; all threads of the CTA then proceed.  Returns
+    // false (uniformly) when the barrier failed.
+    __device__ __forceinline__ bool gbar() {
+        if (threadIdx.x == 0) *sflag = grid_arrive_wait(bar, epoch, nblocks, timeout_ns) ? 1 : 0;
+        __syncthreads();
+        if (*sflag == 0) { ok = false; return false; }
+        return true;
+    }
+
+    // Sum K values over the grid; every thread of every CTA receives the
+    // same bits.  Order: warp xor-tree, warps in index order (one CTA) or a
+    // warp xor-tree over the warp totals, then over the CTAs: lane l adds
+    // CTAs l, l+32, ... in order, then an xor-tree over the lanes.
+    template <int K>
+    __device__ __forceinline__ bool reduce(double (&v)[K]) {
+        const int lane = threadIdx.x & 31;
+        const int warp = threadIdx.x >> 5;
+        const int nw = blockDim.x >> 5;
+        warp_sum<K>(v);
+        double *sr = red + rslot * (32 * kMaxSums);
+        rslot ^= 1;
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) sr[k * 32 + warp] = v[k];
+        }
+        __syncthreads();
+        if (nblocks == 1) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                double t = 0.0;
+                for (int w = 0; w < nw; ++w) t += sr[k * 32 + w];
+                v[k] = t;
+            }
+            return true;
+        }
+        const unsigned G = nblocks;
+        double *part = partials + (size_t)slot * kMaxSums * G;
+        if (warp == 0) {
+            double t[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) t[k] = lane < nw ? sr[k * 32 + lane] : 0.0;
+            warp_sum<K>(t);
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) part[(size_t)k * G + bid] = t[k];
+            }
+        }
+        if (!gbar()) return false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (unsigned b = lane; b < G; b += 32) t += part[(size_t)k * G + b];
+            v[k] = t;
+        }
+        warp_sum<K>(v);
+        slot ^= 1;
+        return true;
+    }
+
+    __device__ __forceinline__ bool sync() {
+        __syncthreads();
+        if (nblocks == 1) return true;
+        return gbar();
+    }
+};
 
 template <typename T>
 struct Engine {
@@ -130,31 +277,20 @@ struct Engine {
     // CTA geometry
     int64_t gtid, gstride, gwarp, nwarps, nchunk;
     int lane;
+    GridSync &gs;
     // shared memory
-    double *red;     // 33 * kMaxSums
     S *c;            // kMaxN
     S *bt;           // kMaxN
-    int *sflag;
     Acct *acct;      // accounting, kept by thread 0 (uniform in the grid)
-    int slot;        // partials double-buffer slot
-    bool ok;         // false once a barrier failed
 
-    __device__ Engine(const SysView<T> &s, const SolveCtl &k, double *red_, S *c_, S *bt_, int *flag_,
-                      Acct *acct_)
-        : sys(s), ctl(k), red(red_), c(c_), bt(bt_), sflag(flag_), acct(acct_) {
-        gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        gstride = (int64_t)gridDim.x * blockDim.x;
+    __device__ Engine(const SysView<T> &s, const SolveCtl &k, GridSync &g, S *c_, S *bt_, Acct *acct_)
+        : sys(s), ctl(k), gs(g), c(c_), bt(bt_), acct(acct_) {
+        gtid = (int64_t)g.bid * blockDim.x + threadIdx.x;
+        gstride = (int64_t)g.nblocks * blockDim.x;
         gwarp = gtid >> 5;
         nwarps = gstride >> 5;
         lane = threadIdx.x & 31;
         nchunk = s.ld / PW;
-        slot = 0;
-        ok = true;
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < 5; ++q) acct->ops[q] = 0;
-            acct->spmv = 0;
-            acct->bytes = 0.0;
-        }
     }
     __device__ __forceinline__ void op(int which, int cnt = 1) {
         if (threadIdx.x == 0) acct->ops[which] += cnt;
@@ -178,36 +314,9 @@ struct Engine {
         }
     }
 
-    // ---- grid-wide reduction -------------------------------------------
     template <int K>
-    __device__ __forceinline__ bool reduce(double (&v)[K]) {
-        block_sum_all<K>(v, red);
-        if (gridDim.x == 1) return true;
-        double *part = ctl.partials + (size_t)slot * gridDim.x * kMaxSums;
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) part[(size_t)blockIdx.x * kMaxSums + k] = v[k];
-        }
-        if (!grid_barrier(ctl.bar, gridDim.x, ctl.timeout_ns, sflag)) { ok = false; return false; }
-        double t[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) t[k] = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) t[k] += part[(size_t)b * kMaxSums + k];
-        }
-        block_sum_all<K>(t, red);
-#pragma unroll
-        for (int k = 0; k < K; ++k) v[k] = t[k];
-        slot ^= 1;
-        return true;
-    }
-
-    __device__ __forceinline__ bool sync() {
-        if (gridDim.x == 1) { __syncthreads(); return true; }
-        if (!grid_barrier(ctl.bar, gridDim.x, ctl.timeout_ns, sflag)) { ok = false; return false; }
-        return true;
-    }
+    __device__ __forceinline__ bool reduce(double (&v)[K]) { return gs.template reduce<K>(v); }
+    __device__ __forceinline__ bool sync() { return gs.sync(); }
 
     // Streaming pass: fn(chunk, acc) for every 16-byte chunk owned by this
     // thread, then a grid reduction of K accumulators.
@@ -228,42 +337,10 @@ struct Engine {
         return sync();
     }
 
-    // SELL-32 SpMV pass: for every row, y = sum_k a_{row,k} xin[col_k], then
-    // epi(row, y, acc); one warp per 32-row slice.
+    // SELL-32 SpMV pass over this thread's slices.
     template <int K, typename Epi>
     __device__ __forceinline__ void spmv_rows(const T *xin, Epi epi, ACC (&acc)[K]) {
-        for (int64_t s = gwarp; s < sys.nslices; s += nwarps) {
-            const int64_t off = __ldg(sys.slice_ptr + s);
-            const int w = (int)((__ldg(sys.slice_ptr + s + 1) - off) >> 5);
-            const int32_t *cp = sys.scol + off + lane;
-            const T *vp = sys.sval + off + lane;
-            T sum{};
-            int k = 0;
-            for (; k + 4 <= w; k += 4) {
-                int32_t cc[4];
-                T vv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) cc[u] = __ldcs(cp + 32 * (k + u));
-#pragma unroll
-                for (int u = 0; u < 4; ++u) vv[u] = ldcs_val(vp + 32 * (k + u));
-#pragma unroll
-                for (int u = 0; u < 4; ++u) sum = efma(vv[u], xin[cc[u]], sum);
-            }
-            if (k < w) {
-                int32_t cc[3];
-                T vv[3];
-#pragma unroll
-                for (int u = 0; u < 3; ++u)
-                    if (k + u < w) cc[u] = __ldcs(cp + 32 * (k + u));
-#pragma unroll
-                for (int u = 0; u < 3; ++u)
-                    if (k + u < w) vv[u] = ldcs_val(vp + 32 * (k + u));
-#pragma unroll
-                for (int u = 0; u < 3; ++u)
-                    if (k + u < w) sum = efma(vv[u], xin[cc[u]], sum);
-            }
-            epi(s * 32 + lane, sum, acc);
-        }
+        sell_spmv(sys.nslices, sys.slice_ptr, sys.scol, sys.sval, xin, gwarp, nwarps, lane, epi, acc);
     }
 
     // ------------------------------------------------------------------
@@ -295,6 +372,48 @@ struct Engine {
         rr = v[1];
         qr = mk_coef<T>(v + 2);
         sbytes(write_g0 ? 4 : 3);
+        return true;
+    }
+
+    // Refined mode, inner start with x_0 = 0: b = r = g_0 = src * scale
+    // (src is the FP64 residual of the outer iteration), x = 0; sums
+    // ||b||^2, ||r||^2, q_1^H r.
+    __device__ __noinline__ bool ph_init_narrow(const typename wide_of<T>::type *src, double scale, double &bb,
+                                                double &rr, S &qr) {
+        using TW = typename wide_of<T>::type;
+        constexpr int K = 2 + DS;
+        static_assert(PW * sizeof(TW) == 32, "a chunk of the FP32 vector is two 16-byte source loads");
+        const T *q1 = Qc(0);
+        T *g0 = Gc(0);
+        double v[K];
+        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
+            const uint4 *sp = reinterpret_cast<const uint4 *>(src) + 2 * ch;
+            uint4 w2[2] = {sp[0], sp[1]};
+            TW tw[PW];
+            memcpy(tw, w2, sizeof(tw));
+            Pack<T> p, zero;
+            Pack<T> qq = ldp_ro(q1, ch);
+#pragma unroll
+            for (int e = 0; e < PW; ++e) {
+                p.e[e] = narrow_scaled(tw[e], scale);
+                zero.e[e] = T{};
+            }
+            stp(sys.b, ch, p);
+            stp(sys.r, ch, p);
+            stp(g0, ch, p);
+            stp(sys.x, ch, zero);
+#pragma unroll
+            for (int e = 0; e < PW; ++e) {
+                acc_nrm(&acc[0], p.e[e]);
+                acc_nrm(&acc[1], p.e[e]);
+                acc_dot(&acc[2], qq.e[e], p.e[e]);
+            }
+        }, v);
+        if (!okk) return false;
+        bb = v[0];
+        rr = v[1];
+        qr = mk_coef<T>(v + 2);
+        if (threadIdx.x == 0) acct->bytes += (double)sys.N * (sizeof(TW) + 5.0 * sizeof(T));
         return true;
     }
 
@@ -575,7 +694,7 @@ struct Engine {
     // ------------------------------------------------------------------
 
     __device__ __forceinline__ void record(bool rec, int64_t iter, double err) {
-        if (rec && ctl.err_hist && iter < ctl.hist_cap && blockIdx.x == 0 && threadIdx.x == 0)
+        if (rec && ctl.err_hist && iter < ctl.hist_cap && gs.bid == 0 && threadIdx.x == 0)
             ctl.err_hist[iter] = err;
     }
 
@@ -589,9 +708,11 @@ struct Engine {
         double err;
     };
 
-    __device__ Out inner(int64_t maxit, bool rec) {
+    // `init` (refined mode only): start from x_0 = 0 with b = init * scale
+    // instead of reading b and x.
+    __device__ Out inner(int64_t maxit, bool rec, double tol,
+                         const typename wide_of<T>::type *init = nullptr, double scale = 1.0) {
         const int n = sys.n;
-        const double tol = ctl.tol;
         Out o{1, 0, 0, 0, 0.0};
         if (threadIdx.x == 0)
             for (int q = 0; q < 5; ++q) acct->ops[q] = 0;
@@ -599,9 +720,19 @@ struct Engine {
         // r_0 = b - A x_0 (step 2) with the stopping-rule denominator
         double bb, rr;
         S e, fr{}, d{};
-        if (!ph_residual(bb, rr, e, true)) return o;
-        op(OP_NORM, 2);
-        op(OP_MATVEC, 1);
+        bool started = false;
+        if constexpr (is_narrow<T>::value) {
+            if (init) {
+                if (!ph_init_narrow(init, scale, bb, rr, e)) return o;
+                op(OP_NORM, 2);
+                started = true;
+            }
+        }
+        if (!started) {
+            if (!ph_residual(bb, rr, e, true)) return o;
+            op(OP_NORM, 2);
+            op(OP_MATVEC, 1);
+        }
         double bnrm2 = sqrt(bb);
         if (bnrm2 == 0.0) bnrm2 = 1.0;
         double err = sqrt(rr) / bnrm2;

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "mlb_engine.cuh"
+#include "mlb_refine.cuh"
 
 namespace mlb {
 
@@ -17,6 +18,39 @@ cudaError_t launch_solve(const SysView<T> &sys, const SolveCtl &ctl, int grid,
 // CTAs of the solve kernel that fit on one SM.
 template <typename T>
 int solve_blocks_per_sm();
+
+// FP32-inner / FP64-refined persistent solve kernel.
+template <typename T32, typename T64>
+cudaError_t launch_refine(const SysView<T32> &sys, const RefView<T64> &rv, const SolveCtl &ctl,
+                          const RefCtl &rc, int grid, cudaStream_t st);
+template <typename T32, typename T64>
+int refine_blocks_per_sm();
+// dst[i] = (float)src[i] for `count` doubles.
+cudaError_t launch_narrow(const double *src, float *dst, int64_t count, cudaStream_t st);
+
+// One system of a batch (device copy of its views and controls).
+template <typename T>
+struct BatchItem {
+    SysView<T> sys;
+    SolveCtl ctl;   // tol, maxit, kappa, max_outer; res -> this system's record
+};
+template <typename T32, typename T64>
+struct BatchItemR {
+    SysView<T32> sys;
+    RefView<T64> rv;
+    SolveCtl ctl;
+    RefCtl rc;
+};
+template <typename T>
+cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
+                         cudaStream_t st);
+template <typename T32, typename T64>
+cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
+                                int grid, cudaStream_t st);
+template <typename T>
+int batch_blocks_per_sm();
+template <typename T32, typename T64>
+int batch_refine_blocks_per_sm();
 
 // Q (ld x n, column-major) from the counter-based SplitMix64 + Box-Muller
 // generator; rows N..ld-1 are left untouched (zero).

@@ -1,30 +1,26 @@
 // Kernels of the ML(n)BiCGStab library (sm_103a).
 #include "mlb_internal.h"
+#include "mlb_refine.cuh"
 
 namespace mlb {
 
 // ===========================================================================
 // persistent solve kernel
 // ===========================================================================
+// One solve by the team described by `gs`: repeated calls of the method
+// from the current x while the recursive residual met tol but the true
+// residual did not (restart rule of this library), all iterations counted
+// against one maxit; then the true residual; the team's rank-0 CTA writes
+// the result record.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) solve_kernel(SysView<T> sys, SolveCtl ctl) {
+__device__ void run_fp64_solve(Engine<T> &E, GridSync &gs, const SolveCtl &ctl, Acct &acct, DevResult *res) {
     using S = typename coef_of<T>::type;
-    __shared__ double red[33 * kMaxSums + 1];
-    __shared__ S cbuf[kMaxN];
-    __shared__ S btbuf[kMaxN];
-    __shared__ int sflag;
-    __shared__ Acct acct;
-    Engine<T> E(sys, ctl, red, cbuf, btbuf, &sflag, &acct);
-
-    // Repeated calls of the method from the current x while the recursive
-    // residual met tol but the true residual did not (restart rule of this
-    // library), all iterations counted against one maxit.
     int64_t total = 0;
     int outer = 0;
     typename Engine<T>::Out o{1, 0, 0, 0, 0.0};
     for (;;) {
-        o = E.inner(ctl.maxit - total, outer == 0);
-        if (!E.ok) break;
+        o = E.inner(ctl.maxit - total, outer == 0, ctl.tol);
+        if (!gs.ok) break;
         total += o.iter;
         if (o.flag != 0 || o.iter == 0 || total >= ctl.maxit || outer >= ctl.max_outer) break;
         outer++;
@@ -32,7 +28,7 @@ __global__ void __launch_bounds__(kThreads, 2) solve_kernel(SysView<T> sys, Solv
     int64_t ops_last[5];
     for (int q = 0; q < 5; ++q) ops_last[q] = acct.ops[q];
     double true_rel = __longlong_as_double(0x7ff8000000000000LL);
-    if (E.ok) {
+    if (gs.ok) {
         double bb, rr;
         S qr;
         if (E.ph_residual(bb, rr, qr, false)) {
@@ -41,13 +37,12 @@ __global__ void __launch_bounds__(kThreads, 2) solve_kernel(SysView<T> sys, Solv
             true_rel = sqrt(rr) / bn;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        DevResult *res = ctl.res;
+    if (gs.bid == 0 && threadIdx.x == 0) {
         res->flag = o.flag;
         res->j = o.j;
         res->i = o.i;
-        res->status = E.ok ? 0 : ld_relaxed_i32(&ctl.bar->status);
-        if (!E.ok && res->status == 0) res->status = kStatusTimeout;
+        res->status = gs.ok ? 0 : (gs.bar ? ld_relaxed_i32(&gs.bar->status) : kStatusTimeout);
+        if (!gs.ok && res->status == 0) res->status = kStatusTimeout;
         res->iter = total;
         res->spmv = acct.spmv;
         res->outer = outer;
@@ -56,6 +51,129 @@ __global__ void __launch_bounds__(kThreads, 2) solve_kernel(SysView<T> sys, Solv
         res->bytes = acct.bytes;
         for (int q = 0; q < 5; ++q) res->ops[q] = ops_last[q];
     }
+}
+
+__device__ __forceinline__ void acct_reset(Acct &acct) {
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 5; ++q) acct.ops[q] = 0;
+        acct.spmv = 0;
+        acct.bytes = 0.0;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) solve_kernel(SysView<T> sys, SolveCtl ctl) {
+    using S = typename coef_of<T>::type;
+    __shared__ double red[2 * 32 * kMaxSums];
+    __shared__ S cbuf[kMaxN];
+    __shared__ S btbuf[kMaxN];
+    __shared__ int sflag;
+    __shared__ Acct acct;
+    acct_reset(acct);
+    GridSync gs(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns);
+    Engine<T> E(sys, ctl, gs, cbuf, btbuf, &acct);
+    run_fp64_solve(E, gs, ctl, acct, ctl.res);
+}
+
+// ===========================================================================
+// batch: many independent systems in one persistent launch
+// ===========================================================================
+// Each CTA takes the next system from a device queue (systems ordered
+// largest first by the host) and solves it alone: the same method with
+// CTA-wide barriers and reductions in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2)
+    batch_kernel(const BatchItem<T> *items, const int *order, int count, unsigned *queue) {
+    using S = typename coef_of<T>::type;
+    __shared__ double red[2 * 32 * kMaxSums];
+    __shared__ S cbuf[kMaxN];
+    __shared__ S btbuf[kMaxN];
+    __shared__ int sflag;
+    __shared__ Acct acct;
+    __shared__ int s_next;
+    __shared__ BatchItem<T> item;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int q = s_next;
+        if (q >= count) break;
+        if (threadIdx.x == 0) item = items[order[q]];
+        acct_reset(acct);   // includes the __syncthreads that publishes `item`
+        GridSync gs(red, &sflag);
+        Engine<T> E(item.sys, item.ctl, gs, cbuf, btbuf, &acct);
+        run_fp64_solve(E, gs, item.ctl, acct, item.ctl.res);
+        __syncthreads();
+    }
+}
+
+template <typename T32, typename T64>
+__global__ void __launch_bounds__(kThreads, 2)
+    batch_refine_kernel(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue) {
+    using S = typename coef_of<T32>::type;
+    __shared__ double red[2 * 32 * kMaxSums];
+    __shared__ S cbuf[kMaxN];
+    __shared__ S btbuf[kMaxN];
+    __shared__ int sflag;
+    __shared__ Acct acct;
+    __shared__ int s_next;
+    __shared__ BatchItemR<T32, T64> item;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int q = s_next;
+        if (q >= count) break;
+        if (threadIdx.x == 0) item = items[order[q]];
+        acct_reset(acct);
+        GridSync gs(red, &sflag);
+        Engine<T32> E(item.sys, item.ctl, gs, cbuf, btbuf, &acct);
+        Refiner<T64, T32> R(item.rv, gs, &acct, item.sys.x);
+        RefineOut o = refine_solve<T32, T64>(E, R, item.ctl, item.rc);
+        if (threadIdx.x == 0) {
+            DevResult *res = item.ctl.res;
+            res->flag = o.flag;
+            res->j = 0;
+            res->i = 0;
+            res->status = gs.ok ? 0 : kStatusTimeout;
+            res->iter = o.iter;
+            res->spmv = acct.spmv;
+            res->outer = o.outer;
+            res->err = o.err;
+            res->true_relres = o.err;
+            res->bytes = acct.bytes;
+            for (int k = 0; k < 5; ++k) res->ops[k] = acct.ops[k];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
+                         cudaStream_t st) {
+    batch_kernel<T><<<grid, kThreads, 0, st>>>(items, order, count, queue);
+    return cudaGetLastError();
+}
+
+template <typename T32, typename T64>
+cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
+                                int grid, cudaStream_t st) {
+    batch_refine_kernel<T32, T64><<<grid, kThreads, 0, st>>>(items, order, count, queue);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int batch_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T>, kThreads, 0) != cudaSuccess) return 0;
+    return nb;
+}
+template <typename T32, typename T64>
+int batch_refine_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_refine_kernel<T32, T64>, kThreads, 0) !=
+        cudaSuccess)
+        return 0;
+    return nb;
 }
 
 template <typename T>
@@ -75,6 +193,79 @@ int solve_blocks_per_sm() {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<T>, kThreads, 0) != cudaSuccess)
         return 0;
     return nb;
+}
+
+// ===========================================================================
+// FP32-inner / FP64-refined persistent solve kernel
+// ===========================================================================
+template <typename T32, typename T64>
+__global__ void __launch_bounds__(kThreads, 2)
+    refine_kernel(SysView<T32> sys, RefView<T64> rv, SolveCtl ctl, RefCtl rc) {
+    using S = typename coef_of<T32>::type;
+    __shared__ double red[2 * 32 * kMaxSums];
+    __shared__ S cbuf[kMaxN];
+    __shared__ S btbuf[kMaxN];
+    __shared__ int sflag;
+    __shared__ Acct acct;
+    acct_reset(acct);
+    GridSync gs(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns);
+    Engine<T32> E(sys, ctl, gs, cbuf, btbuf, &acct);
+    Refiner<T64, T32> R(rv, gs, &acct, sys.x);
+    RefineOut o = refine_solve<T32, T64>(E, R, ctl, rc);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        DevResult *res = ctl.res;
+        res->flag = o.flag;
+        res->j = 0;
+        res->i = 0;
+        res->status = gs.ok ? 0 : ld_relaxed_i32(&ctl.bar->status);
+        if (!gs.ok && res->status == 0) res->status = kStatusTimeout;
+        res->iter = o.iter;
+        res->spmv = acct.spmv;
+        res->outer = o.outer;
+        res->err = o.err;
+        res->true_relres = o.err;
+        res->bytes = acct.bytes;
+        for (int q = 0; q < 5; ++q) res->ops[q] = acct.ops[q];
+    }
+}
+
+template <typename T32, typename T64>
+cudaError_t launch_refine(const SysView<T32> &sys, const RefView<T64> &rv, const SolveCtl &ctl,
+                          const RefCtl &rc, int grid, cudaStream_t st) {
+    SysView<T32> s = sys;
+    RefView<T64> r = rv;
+    SolveCtl c = ctl;
+    RefCtl q = rc;
+    void *args[] = {(void *)&s, (void *)&r, (void *)&c, (void *)&q};
+    if (grid <= 1)
+        return cudaLaunchKernel((const void *)refine_kernel<T32, T64>, dim3(1), dim3(kThreads), args, 0, st);
+    return cudaLaunchCooperativeKernel((const void *)refine_kernel<T32, T64>, dim3(grid), dim3(kThreads),
+                                       args, 0, st);
+}
+
+template <typename T32, typename T64>
+int refine_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, refine_kernel<T32, T64>, kThreads, 0) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+// FP64 -> FP32 copies (matrix values, Q, F); interleaved complex data is a
+// sequence of doubles, so one kernel covers both.
+__global__ void narrow_kernel(const double *src, float *dst, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+cudaError_t launch_narrow(const double *src, float *dst, int64_t count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 1 << 20) blocks = 1 << 20;
+    narrow_kernel<<<(int)blocks, 256, 0, st>>>(src, dst, count);
+    return cudaGetLastError();
 }
 
 // ===========================================================================
@@ -277,7 +468,8 @@ cudaError_t launch_spmv_qdot(const SysView<T> &sys, const T *x, T *y, double *pa
 // ===========================================================================
 __global__ void barrier_selftest_kernel(BarrierState *bs, uint64_t timeout_ns) {
     __shared__ int flag;
-    grid_barrier(bs, gridDim.x + 1, timeout_ns, &flag);
+    unsigned epoch = 0;
+    grid_barrier(bs, epoch, gridDim.x + 1, timeout_ns, &flag);
 }
 
 cudaError_t launch_barrier_selftest(int grid, BarrierState *bs, uint64_t timeout_ns, cudaStream_t st) {
@@ -303,5 +495,23 @@ template cudaError_t launch_spmv_qdot<cdouble>(const SysView<cdouble> &, const c
                                                double *, int, double *, cudaStream_t);
 template int spmv_qdot_grid<double>();
 template int spmv_qdot_grid<cdouble>();
+template cudaError_t launch_refine<float, double>(const SysView<float> &, const RefView<double> &,
+                                                  const SolveCtl &, const RefCtl &, int, cudaStream_t);
+template cudaError_t launch_refine<cfloat, cdouble>(const SysView<cfloat> &, const RefView<cdouble> &,
+                                                    const SolveCtl &, const RefCtl &, int, cudaStream_t);
+template int refine_blocks_per_sm<float, double>();
+template int refine_blocks_per_sm<cfloat, cdouble>();
+template cudaError_t launch_batch<double>(const BatchItem<double> *, const int *, int, unsigned *, int,
+                                          cudaStream_t);
+template cudaError_t launch_batch<cdouble>(const BatchItem<cdouble> *, const int *, int, unsigned *, int,
+                                           cudaStream_t);
+template cudaError_t launch_batch_refine<float, double>(const BatchItemR<float, double> *, const int *, int,
+                                                        unsigned *, int, cudaStream_t);
+template cudaError_t launch_batch_refine<cfloat, cdouble>(const BatchItemR<cfloat, cdouble> *, const int *, int,
+                                                          unsigned *, int, cudaStream_t);
+template int batch_blocks_per_sm<double>();
+template int batch_blocks_per_sm<cdouble>();
+template int batch_refine_blocks_per_sm<float, double>();
+template int batch_refine_blocks_per_sm<cfloat, cdouble>();
 
 }  // namespace mlb

@@ -1,0 +1,79 @@
+"""Batched solves (one persistent launch, one CTA per system) through the C ABI.
+
+A batch runs, for every system, exactly the arithmetic of a single solve on
+one CTA (grid = 1): the same passes, the same reduction order.  So each
+batch result must equal the single-CTA solve bit for bit (solution and
+iteration count), and each solution must agree with the CPU oracle's to
+1e-8 relative with a true residual below tol.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1106_3678_gb300 import mlbicgstab as M
+from paper_1106_3678_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1106_3678_gb300 import build
+    build.build()
+    M.load()
+
+
+def _systems(count, seed, n_min=300, n_max=6000):
+    out = []
+    for A, meta in W.batch_cd(count, seed=seed, n_min=n_min, n_max=n_max):
+        out.append((A, W.row_sums(A)))
+    return out
+
+
+@pytest.mark.parametrize("precision", [M.MLB_PREC_FP64, M.MLB_PREC_FP32_REFINED])
+def test_batch_equals_single_cta_solves_and_oracle(precision):
+    n, tol, maxit = 4, 1e-10, 4000
+    systems = _systems(40, seed=21)
+    hs = [M.mlbicgstab_create(A, n=n, q_seed=0, precision=precision) for A, _ in systems]
+    bs = [b for _, b in systems]
+    xs = [np.zeros(A.n_rows) for A, _ in systems]
+    res = M.mlbicgstab_solve_batch(hs, bs, xs, [tol] * len(hs), [maxit] * len(hs))
+    for k, ((A, b), r, x) in enumerate(zip(systems, res, xs)):
+        assert r.status == 0 and r.flag == 0, (k, r.as_dict())
+        assert r.true_relres < tol
+        h1 = M.mlbicgstab_create(A, n=n, q_seed=0, precision=precision, grid=1)
+        x1 = np.zeros(A.n_rows)
+        r1, _ = M.mlbicgstab_solve(h1, b, x1, tol, maxit)
+        assert (r.iter, r.outer, r.flag) == (r1.iter, r1.outer, r1.flag), k
+        np.testing.assert_array_equal(x, x1)
+        ref = O.solve(A, b, np.zeros(A.n_rows), O.q_gauss(0, A.n_rows, n), maxit, tol)
+        assert ref.flag == 0
+        assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x), k
+
+
+def test_batch_more_systems_than_ctas_and_device_pointers():
+    import torch
+    systems = _systems(400, seed=22, n_min=200, n_max=1500)
+    hs = [M.mlbicgstab_create(A, n=2, q_seed=0) for A, _ in systems]
+    bs = [torch.tensor(b, device="cuda") for _, b in systems]
+    xs = [torch.zeros(A.n_rows, dtype=torch.float64, device="cuda") for A, _ in systems]
+    res = M.mlbicgstab_solve_batch(hs, bs, xs, [1e-10] * 400, [3000] * 400)
+    assert all(r.flag == 0 and r.true_relres < 1e-10 for r in res)
+    for (A, b), x in list(zip(systems, xs))[::37]:
+        assert O.true_relres(A, b, x.cpu().numpy()) < 1e-10
+
+
+def test_batch_rejects_mixed_precision():
+    A = W.cd2d(8)
+    h1 = M.mlbicgstab_create(A, n=2)
+    h2 = M.mlbicgstab_create(A, n=2, precision=M.MLB_PREC_FP32_REFINED)
+    b = W.row_sums(A)
+    with pytest.raises(M.MlbError) as e:
+        M.mlbicgstab_solve_batch([h1, h2], [b, b], [np.zeros(64), np.zeros(64)],
+                                 [1e-10, 1e-10], [100, 100])
+    assert e.value.code == M.MLB_ERR_ARG
