@@ -42,17 +42,21 @@ UNIT = "solves/s"
 # count of one full solve on the GPU path, used only to convert the
 # reference arm's per-iteration sample into solves/sec.
 WORKLOADS = {
-    "cd3d128_n4_fp64": dict(m=128, n=4, tol=1e-10, maxit=40000, iters=18468, precision=0),
-    "cd3d128_n4_refined": dict(m=128, n=4, tol=1e-10, maxit=80000, iters=None, precision=1,
+    "cd3d128_n4_fp64": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, iters=18705,
+                            precision=0),
+    "cd3d128_n4_refined": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=1,
                                inner_tol=1e-5),
+    "helmholtz_n8_c128": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=0),
+    "reservoir_n8_fp64": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0),
+    "batch512_n4_fp64": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0),
+    "batch512_n4_refined": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=1,
+                                inner_tol=1e-4),
 }
 for _n in (1, 8, 16):
-    WORKLOADS[f"cd3d128_n{_n}_fp64"] = dict(m=128, n=_n, tol=1e-10, maxit=60000, iters=None,
+    WORKLOADS[f"cd3d128_n{_n}_fp64"] = dict(kind="cd3d", m=128, n=_n, tol=1e-10, maxit=60000,
                                            precision=0)
-    WORKLOADS[f"cd3d128_n{_n}_refined"] = dict(m=128, n=_n, tol=1e-10, maxit=120000, iters=None,
-                                              precision=1, inner_tol=1e-5)
 DEFAULT = "cd3d128_n4_fp64"
-VARIANTS = ["cd3d128_n4_refined"]
+VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "cd3d128_n4_refined"]
 
 
 def _load_peaks():
@@ -70,6 +74,34 @@ def _make_inputs(wl):
     A = W.cd3d_lognormal(wl["m"])
     b = W.uniform_rhs(A.n_rows, seed=2)
     return A, b
+
+
+def _make_variant_inputs(wl):
+    """(list of (A, AH or None, b)) for a variant workload."""
+    from paper_1106_3678_gb300 import workloads as W
+    kind = wl["kind"]
+    if kind == "cd3d":
+        A, b = _make_inputs(wl)
+        return [(A, None, b)]
+    if kind == "helmholtz":
+        A = W.helmholtz3d_c()
+        return [(A, W.conj_transpose(A), W.row_sums(A))]
+    if kind == "reservoir":
+        A = W.bsr3_to_csr(W.reservoir_bsr3())
+        return [(A, None, W.row_sums(A))]
+    if kind == "batch":
+        return [(A, None, W.row_sums(A)) for A, _ in W.batch_cd(512, seed=5)]
+    raise ValueError(kind)
+
+
+def _variant_desc(name, wl, systems):
+    N = sum(A.n_rows for A, _, _ in systems)
+    nnz = sum(A.nnz for A, _, _ in systems)
+    what = {"cd3d": "3-D log-normal convection-diffusion 128^3",
+            "helmholtz": "complex damped shifted Laplacian 256x256x64, A^H as separate CSR",
+            "reservoir": "3x3-block reservoir system 64x64x32 cells",
+            "batch": "512 2-D/3-D convection-diffusion systems, N ~ logU[1e3,1e5], one launch"}[wl["kind"]]
+    return f"{what} (N={N:,}, nnz={nnz:,}), n={wl['n']}, {_prec_name(wl)}, tol {wl['tol']:g}"
 
 
 def _prec_name(wl):
@@ -228,6 +260,71 @@ def _create(M, A, wl, stream):
                                inner_tol=wl.get("inner_tol"))
 
 
+def _measure_variant(M, name, args, dev, stream, barrier, ws):
+    import torch
+    vwl = dict(WORKLOADS[name])
+    if args.maxit > 0:
+        vwl["maxit"] = args.maxit
+    systems = _make_variant_inputs(vwl)
+    dt = torch.complex128 if np.iscomplexobj(systems[0][2]) else torch.float64
+    hs = [M.mlbicgstab_create(A, AH=AH, n=vwl["n"], q_seed=0, max_outer=10, stream=stream,
+                              precision=vwl.get("precision", 0), inner_tol=vwl.get("inner_tol"))
+          for A, AH, _ in systems]
+    bs = [torch.tensor(b, dtype=dt, device=dev) for _, _, b in systems]
+    xs = [torch.zeros_like(b) for b in bs]
+    steps = max(1, args.variant_steps)
+    out = {"workload": name, "config": _variant_desc(name, vwl, systems),
+           "precision": _prec_name(vwl), "n": vwl["n"], "unit": UNIT}
+    if vwl["kind"] == "batch":
+        def once():
+            for x in xs:
+                x.zero_()
+            return M.mlbicgstab_solve_batch(hs, bs, xs, [vwl["tol"]] * len(hs),
+                                            [vwl["maxit"]] * len(hs))
+        once()   # warm-up
+        barrier()
+        t0 = time.perf_counter()
+        runs = [once() for _ in range(steps)]
+        barrier()
+        secs = (time.perf_counter() - t0) / steps
+        res = runs[-1]
+        out.update({
+            "value": ws * len(hs) / secs, "ms_per_step": secs * 1e3,
+            "systems_per_launch": len(hs),
+            "kernel_ms": res[0].kernel_ms,
+            "flags": sorted({r.flag for r in res}),
+            "iters_total": sum(r.iter for r in res), "iters_max": max(r.iter for r in res),
+            "true_relres_max": max(r.true_relres for r in res),
+        })
+        # the same systems solved one by one with the plain FP64 path
+        if vwl.get("precision", 0) == 0:
+            for x in xs:
+                x.zero_()
+            barrier()
+            t0 = time.perf_counter()
+            for h, b, x in zip(hs, bs, xs):
+                M.mlbicgstab_solve(h, b, x, vwl["tol"], vwl["maxit"])
+            barrier()
+            one = time.perf_counter() - t0
+            out["one_by_one_fp64"] = {"value": ws * len(hs) / one, "seconds": one}
+            out["speedup_vs_one_by_one_fp64"] = out["value"] / out["one_by_one_fp64"]["value"]
+    else:
+        h, b, x = hs[0], bs[0], xs[0]
+        long = True
+        vms, vres = _timed_solves(M, h, b, x, vwl, stream, steps, 0 if long else 1, barrier)
+        kb = sum(r["bytes"] for r in vres)
+        kms = sum(r["kernel_ms"] for r in vres)
+        out.update({
+            "value": ws * len(vres) / (vms * 1e-3), "ms_per_step": vms / len(vres),
+            "iters_per_solve": [r["iter"] for r in vres], "outer": [r["outer"] for r in vres],
+            "flags": [r["flag"] for r in vres], "true_relres": [r["true_relres"] for r in vres],
+            "achieved_gbs": kb / (kms * 1e-3) / 1e9 if kms > 0 else None,
+        })
+    for hh in hs:
+        hh.destroy()
+    return out
+
+
 def run_ours(args, wl):
     import torch
 
@@ -266,34 +363,18 @@ def run_ours(args, wl):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
 
-    # variants on the same matrix: other precisions / shadow counts
+    # variants: other workloads, precisions and the batched form
     variants = []
     for name in ([] if args.no_variants else (args.variant or VARIANTS)):
-        vwl = dict(WORKLOADS[name])
-        if args.maxit > 0:
-            vwl["maxit"] = args.maxit
-        hv = _create(M, A, vwl, stream)
-        vms, vres = _timed_solves(M, hv, b_d, x_d, vwl, stream, max(1, args.variant_steps),
-                                  1, barrier)
-        hv.destroy()
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([vms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            vms = float(t.item())
-        vsteps = len(vres)
-        kb = sum(r["bytes"] for r in vres)
-        kms = sum(r["kernel_ms"] for r in vres)
-        variants.append({
-            "workload": name, "precision": _prec_name(vwl), "n": vwl["n"],
-            "value": ws * vsteps / (vms * 1e-3), "unit": UNIT,
-            "ms_per_step": vms / vsteps,
-            "iters_per_solve": [r["iter"] for r in vres],
-            "outer": [r["outer"] for r in vres],
-            "flags": [r["flag"] for r in vres],
-            "true_relres": [r["true_relres"] for r in vres],
-            "achieved_gbs": kb / (kms * 1e-3) / 1e9 if kms > 0 else None,
-        })
+        variants.append(_measure_variant(M, name, args, dev, stream, barrier, ws))
+    head_value = ws * args.steps / (total_ms * 1e-3)
+    by_name = {v["workload"]: v for v in variants}
+    for v in variants:
+        wlv = WORKLOADS[v["workload"]]
+        if wlv["kind"] == "cd3d" and wlv.get("precision", 0) == 1 and wlv["n"] == wl["n"]:
+            v["speedup_vs_fp64"] = v["value"] / head_value
+        if v["workload"] == "batch512_n4_refined" and "batch512_n4_fp64" in by_name:
+            v["speedup_vs_batch_fp64"] = v["value"] / by_name["batch512_n4_fp64"]["value"]
 
     # end to end through the C ABI with pinned host buffers
     b_h = torch.tensor(b, dtype=torch.float64).pin_memory()
@@ -358,7 +439,7 @@ def run_ours(args, wl):
         "gpu_launches": args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
-        "variants": [dict(v, speedup_vs_fp64=v["value"] / value) for v in variants],
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     h.destroy()
@@ -383,7 +464,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variant", action="append", choices=sorted(WORKLOADS),
                     help="extra workloads measured on the same matrix (repeatable)")
-    ap.add_argument("--variant-steps", type=int, default=2)
+    ap.add_argument("--variant-steps", type=int, default=1)
     ap.add_argument("--maxit", type=int, default=0,
                     help="override the iteration cap (short runs for profiling)")
     args = ap.parse_args()
