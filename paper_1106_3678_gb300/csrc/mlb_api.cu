@@ -17,6 +17,7 @@ struct mlb_handle {
     int n = 4;
     int precision = MLB_PREC_FP64;
     int64_t N = 0, ld = 0, nnz = 0, nnz_pad = 0, nslices = 0;
+    int64_t maxw = 0;   // widest SELL-32 slice (entries per row)
     int device = 0;
     cudaStream_t stream = nullptr;
     int grid = 1;
@@ -107,10 +108,11 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 // CSR -> SELL-32 (slices of 32 consecutive rows, natural row order, entry k
 // of lane l at slice_ptr[s] + 32k + l; padding entries have value 0 and
 // column = the row itself, clamped to N-1).
-void csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp, std::vector<int32_t> &col,
-                   std::vector<char> &val, size_t es) {
+int64_t csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp, std::vector<int32_t> &col,
+                      std::vector<char> &val, size_t es) {
     const int64_t N = A->nrows, ns = ld / 32;
     sp.assign(ns + 1, 0);
+    int64_t maxw = 0;
     for (int64_t s = 0; s < ns; ++s) {
         int64_t w = 0;
         for (int64_t l = 0; l < 32; ++l) {
@@ -118,6 +120,7 @@ void csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp, st
             if (row < N) w = std::max(w, A->row_ptr[row + 1] - A->row_ptr[row]);
         }
         sp[s + 1] = sp[s] + 32 * w;
+        maxw = std::max(maxw, w);
     }
     const int64_t tot = sp[ns];
     col.assign(tot, 0);
@@ -140,6 +143,18 @@ void csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp, st
             }
         }
     }
+    return maxw;
+}
+
+// Slices per SpMV tile so that the widest tile (values of `vbytes` plus
+// 4-byte column indices) fits one shared-memory stage; 0 when one slice
+// alone does not fit (the SpMV then reads the matrix directly).
+int slices_per_tile(int64_t maxw, size_t vbytes) {
+    if (maxw <= 0) return kConsumerWarps;
+    const int64_t per_slice = maxw * 32 * (int64_t)(vbytes + 4);
+    int64_t spt = kStageBytes / per_slice;
+    if (spt > kConsumerWarps) spt = kConsumerWarps;
+    return (int)spt;
 }
 
 // A^H in CSR by a stable counting sort over columns (values conjugated for
@@ -177,6 +192,7 @@ SysView<T> make_view(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T *)h->sval;
+    v.spt = slices_per_tile(h->maxw, sizeof(T));
     v.Q = (const T *)h->Q;
     v.F = (const T *)h->F;
     v.G = (T *)h->G;
@@ -199,6 +215,7 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T32 *)h->sval32;
+    v.spt = slices_per_tile(h->maxw, sizeof(T32));
     v.Q = (const T32 *)h->Q32;
     v.F = (const T32 *)h->F32;
     v.G = (T32 *)h->G32;
@@ -221,6 +238,7 @@ RefView<T64> make_ref_view(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T64 *)h->sval;
+    v.spt = slices_per_tile(h->maxw, sizeof(T64));
     v.x = (T64 *)h->x;
     v.b = (const T64 *)h->b;
     v.r = (T64 *)h->r;
@@ -263,7 +281,7 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         std::vector<int64_t> sp;
         std::vector<int32_t> col;
         std::vector<char> val;
-        csr_to_sell32(A, ld, sp, col, val, es);
+        h->maxw = csr_to_sell32(A, ld, sp, col, val, es);
         h->nnz_pad = sp.back();
         int rc;
         if ((rc = dev_alloc_t(h, &h->slice_ptr, sp.size() * 8))) return rc;

@@ -11,6 +11,15 @@
 // and every CTA takes the same branches (convergence, breakdown, g_n/r_n
 // bookkeeping) without any host round trip.
 //
+// Work distribution: every CTA of the team owns a contiguous, balanced range
+// of 32-row slices (and the matching rows of every vector).  Every pass
+// reads its streamed operands through a TMA-fed shared-memory tile
+// pipeline (one producer warp, 15 consumer warps): vector chunks for the
+// streaming passes, SELL slices (values and columns) for the SpMV, whose
+// consumers gather x directly.
+// Every vector a CTA bulk-loads was last written by that same CTA (its own
+// rows) or is read-only.
+//
 // Storage ("ring"): g_k, w_k, c_k of iterate k = jn + s live in slot
 // s = k mod n of G, W, c.  During step jn+i, slots < i hold block j and
 // slots >= i still hold block j-1, as Algorithm 7.1 reads them.
@@ -30,10 +39,11 @@
 #pragma once
 
 #include "mlb_device.cuh"
+#include "mlb_tiles.cuh"
 
 namespace mlb {
 
-constexpr int kThreads = 512;   // threads per CTA of the solve kernels
+constexpr int kThreads = kTileThreads;   // 15 consumer warps + 1 producer warp
 constexpr int kMaxN = 64;       // largest number of shadow vectors
 constexpr int kMaxSums = 8;     // doubles reduced per pass (max)
 
@@ -52,6 +62,13 @@ struct Acct {
     int64_t ops[5];   // Table 4.3 categories of the current inner call
     int64_t spmv;     // all sparse products of the solve
     double bytes;     // algorithmic bytes of the solve
+    // Scalars evaluated by thread 0 and read by every thread after a
+    // __syncthreads: FP64 division and square root are costly on this GPU,
+    // so they are not repeated by all threads.  Calls rotate through the
+    // slots, so a slot is rewritten only after three more __syncthreads,
+    // which every reader of its previous value has already passed.
+    double d[4];
+    cdouble z[4];
 };
 
 // Device view of one linear system.  Vectors have leading dimension `ld`
@@ -63,6 +80,7 @@ struct SysView {
     const int64_t *slice_ptr;   // SELL-32: slice s spans [slice_ptr[s], slice_ptr[s+1])
     const int32_t *scol;        // column of entry (slice, k, lane) at off + 32k + lane
     const T *sval;
+    int spt;                    // slices per SpMV tile (the widest tile fits one stage)
     const T *Q;                 // ld x n
     const T *F;                 // ld x (n-1), F = A^H Q(:,0:n-2)
     T *G, *W;                   // ld x n rings
@@ -125,45 +143,122 @@ __device__ __forceinline__ cfloat narrow_scaled(cdouble v, double s) {
     return {(float)(v.re * s), (float)(v.im * s)};
 }
 
-// SELL-32 product over this thread's slices: for every row,
-// y = sum_k a_{row,k} xin[col_k], then epi(row, y, acc).  One warp per
-// 32-row slice, slices gwarp, gwarp + nwarps, ...
-template <typename T, typename Epi, typename AccArr>
-__device__ __forceinline__ void sell_spmv(int64_t nslices, const int64_t *slice_ptr, const int32_t *scol,
-                                          const T *sval, const T *xin, int64_t gwarp, int64_t nwarps,
-                                          int lane, Epi epi, AccArr &acc) {
-    for (int64_t s = gwarp; s < nslices; s += nwarps) {
-        const int64_t off = __ldg(slice_ptr + s);
-        const int w = (int)((__ldg(slice_ptr + s + 1) - off) >> 5);
-        const int32_t *cp = scol + off + lane;
-        const T *vp = sval + off + lane;
-        T sum{};
-        int k = 0;
-        for (; k + 4 <= w; k += 4) {
-            int32_t cc[4];
-            T vv[4];
+// Balanced contiguous share [lo, hi) of `total` items for member `bid` of
+// `nblocks`.
+__device__ __forceinline__ void own_range(int64_t total, unsigned nblocks, unsigned bid, int64_t &lo, int64_t &hi) {
+    lo = total * (int64_t)bid / nblocks;
+    hi = total * (int64_t)(bid + 1) / nblocks;
+}
+
+// One SELL-32 slice (32 rows, width w, entries at slice offset `off`):
+// the row sum of this lane, for slices of any width.
+template <typename T>
+__device__ __forceinline__ T sell_slice_sum(const int32_t *cp, const T *vp, int w, const T *xin) {
+    T sum{};
+    int k = 0;
+    for (; k + 4 <= w; k += 4) {
+        int32_t cc[4];
+        T vv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) cc[u] = __ldcs(cp + 32 * (k + u));
+        for (int u = 0; u < 4; ++u) cc[u] = __ldcs(cp + 32 * (k + u));
 #pragma unroll
-            for (int u = 0; u < 4; ++u) vv[u] = ldcs_val(vp + 32 * (k + u));
+        for (int u = 0; u < 4; ++u) vv[u] = ldcs_val(vp + 32 * (k + u));
 #pragma unroll
-            for (int u = 0; u < 4; ++u) sum = efma(vv[u], xin[cc[u]], sum);
-        }
-        if (k < w) {
-            int32_t cc[3];
-            T vv[3];
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-                if (k + u < w) cc[u] = __ldcs(cp + 32 * (k + u));
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-                if (k + u < w) vv[u] = ldcs_val(vp + 32 * (k + u));
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-                if (k + u < w) sum = efma(vv[u], xin[cc[u]], sum);
-        }
-        epi(s * 32 + lane, sum, acc);
+        for (int u = 0; u < 4; ++u) sum = efma(vv[u], xin[cc[u]], sum);
     }
+    if (k < w) {
+        int32_t cc[3];
+        T vv[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+            if (k + u < w) cc[u] = __ldcs(cp + 32 * (k + u));
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+            if (k + u < w) vv[u] = ldcs_val(vp + 32 * (k + u));
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+            if (k + u < w) sum = efma(vv[u], xin[cc[u]], sum);
+    }
+    return sum;
+}
+
+// SELL-32 product over the slices [s_lo, s_hi) owned by this CTA: for
+// every row, y = sum_k a_{row,k} xin[col_k], then epi(row, y, acc).  The
+// producer warp streams tiles of `spt` slices (values and column indices)
+// into the shared-memory ring; consumer warp w takes slice w of each tile
+// and gathers x directly.  The epilogue's stores are fenced for later bulk
+// (async-proxy) reads.  Returns false when a tile wait timed out.
+template <typename T, typename Epi, typename AccArr>
+__device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned &cseq, uint64_t timeout_ns,
+                                          int64_t s_lo, int64_t s_hi, int spt, const int64_t *slice_ptr,
+                                          const int32_t *scol, const T *sval, const T *xin, int lane, Epi epi,
+                                          AccArr &acc) {
+    const int cw = threadIdx.x >> 5;
+    bool ok = true;
+    if (spt <= 0) {
+        // slices too wide for one stage: direct loads, no pipeline
+        if (cw < kConsumerWarps) {
+            for (int64_t s = s_lo + cw; s < s_hi; s += kConsumerWarps) {
+                const int64_t off = __ldg(slice_ptr + s);
+                const int w = (int)((__ldg(slice_ptr + s + 1) - off) >> 5);
+                epi(s * 32 + lane, sell_slice_sum(scol + off + lane, sval + off + lane, w, xin), acc);
+            }
+        }
+        fence_proxy_async_global();
+        return true;
+    }
+    if (cw == kConsumerWarps) {
+        if (lane == 0)
+            ok = produce_sell(R, s_lo, s_hi, spt, slice_ptr, sval, (int)sizeof(T), scol, pseq, timeout_ns);
+    } else {
+        for (int64_t s0 = s_lo; s0 < s_hi; s0 += spt, ++cseq) {
+            const int st = (int)(cseq % kStages);
+            const unsigned use = cseq / kStages;
+            if (!mbar_wait(&R->full[st], use & 1u, timeout_ns)) { ok = false; break; }
+            const int64_t s1 = s0 + spt < s_hi ? s0 + spt : s_hi;
+            const unsigned char *stage = R->buf + (size_t)st * kStageBytes;
+            const int64_t s = s0 + cw;
+            if (s < s1) {
+                const int64_t e0 = __ldg(slice_ptr + s0);
+                const int64_t nv = __ldg(slice_ptr + s1) - e0;
+                const int64_t o = __ldg(slice_ptr + s) - e0;
+                const int w = (int)((__ldg(slice_ptr + s + 1) - e0 - o) >> 5);
+                const T *vp = reinterpret_cast<const T *>(stage) + o + lane;
+                const int32_t *cp = reinterpret_cast<const int32_t *>(stage + nv * sizeof(T)) + o + lane;
+                T sum{};
+                int k = 0;
+                for (; k + 8 <= w; k += 8) {
+                    T xv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) xv[u] = xin[cp[32 * (k + u)]];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) sum = efma(vp[32 * (k + u)], xv[u], sum);
+                }
+                if (k < w) {
+                    T xv[7];
+#pragma unroll
+                    for (int u = 0; u < 7; ++u)
+                        if (k + u < w) xv[u] = xin[cp[32 * (k + u)]];
+#pragma unroll
+                    for (int u = 0; u < 7; ++u)
+                        if (k + u < w) sum = efma(vp[32 * (k + u)], xv[u], sum);
+                }
+                epi(s * 32 + lane, sum, acc);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&R->empty[st]);
+        }
+        fence_proxy_async_global();
+    }
+    return ok;
+}
+
+// A 16-byte chunk of input i of a tile, from shared memory.
+template <typename T>
+__device__ __forceinline__ Pack<T> lds(const unsigned char *stage, int tc, int i, int k) {
+    Pack<T> p;
+    *reinterpret_cast<uint4 *>(&p) = *reinterpret_cast<const uint4 *>(stage + ((size_t)i * tc + k) * 16);
+    return p;
 }
 
 // Coefficient from reduced sums (re[, im]).
@@ -183,21 +278,24 @@ struct GridSync {
     unsigned bid;       // this CTA's rank in the team
     BarrierState *bar;
     double *partials;   // [2][kMaxSums][gridDim]
-    double *red;        // shared, 2 * 32 * kMaxSums
+    double *red;        // shared, kMaxSums * (kThreads + 1)
     int *sflag;         // shared
     uint64_t timeout_ns;
     unsigned epoch;
     int slot, rslot;
-    bool ok;            // false once a barrier failed
+    bool ok;            // false once a barrier or a tile wait failed
+    TileRing *ring;     // shared-memory tile pipeline of this CTA
+    unsigned pseq;      // tiles issued (producer lane)
+    unsigned cseq;      // tiles consumed (consumer threads)
 
     // Team = the whole grid.
-    __device__ GridSync(BarrierState *b, double *p, double *r, int *f, uint64_t to)
+    __device__ GridSync(BarrierState *b, double *p, double *r, int *f, uint64_t to, TileRing *rg)
         : nblocks(gridDim.x), bid(blockIdx.x), bar(b), partials(p), red(r), sflag(f), timeout_ns(to), epoch(0),
-          slot(0), rslot(0), ok(true) {}
+          slot(0), rslot(0), ok(true), ring(rg), pseq(0), cseq(0) {}
     // Team = this CTA alone.
-    __device__ GridSync(double *r, int *f)
-        : nblocks(1), bid(0), bar(nullptr), partials(nullptr), red(r), sflag(f), timeout_ns(0), epoch(0), slot(0),
-          rslot(0), ok(true) {}
+    __device__ GridSync(double *r, int *f, uint64_t to, TileRing *rg)
+        : nblocks(1), bid(0), bar(nullptr), partials(nullptr), red(r), sflag(f), timeout_ns(to), epoch(0), slot(0),
+          rslot(0), ok(true), ring(rg), pseq(0), cseq(0) {}
 
     // Thread 0 arrives/waits; all threads of the CTA then proceed.  Returns
     // false (uniformly) when the barrier failed.
@@ -208,53 +306,67 @@ struct GridSync {
         return true;
     }
 
-    // Sum K values over the grid; every thread of every CTA receives the
-    // same bits.  Order: warp xor-tree, warps in index order (one CTA) or a
-    // warp xor-tree over the warp totals, then over the CTAs: lane l adds
-    // CTAs l, l+32, ... in order, then an xor-tree over the lanes.
+    // Sum K values over the team; every thread of every CTA receives the
+    // same bits.  FP64 instructions are scarce on this GPU, so one warp does
+    // the arithmetic: threads stage their partials in shared memory; warp 0
+    // adds them (lane l: threads l, l+32, ... in order, then an xor-tree
+    // over the lanes); with several CTAs, warp 0 of every CTA then adds the
+    // CTA totals the same way (CTAs l, l+32, ...); the result is broadcast
+    // through shared memory.
     template <int K>
     __device__ __forceinline__ bool reduce(double (&v)[K]) {
         const int lane = threadIdx.x & 31;
         const int warp = threadIdx.x >> 5;
-        const int nw = blockDim.x >> 5;
-        warp_sum<K>(v);
-        double *sr = red + rslot * (32 * kMaxSums);
-        rslot ^= 1;
-        if (lane == 0) {
+        const int bd = blockDim.x;
+        double *sv = red;                       // K * blockDim partials
+        double *bc = red + kMaxSums * kThreads; // K broadcast totals
 #pragma unroll
-            for (int k = 0; k < K; ++k) sr[k * 32 + warp] = v[k];
-        }
+        for (int k = 0; k < K; ++k) sv[k * bd + threadIdx.x] = v[k];
         __syncthreads();
-        if (nblocks == 1) {
+        double t[K];
+        if (warp == 0) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                double t = 0.0;
-                for (int w = 0; w < nw; ++w) t += sr[k * 32 + w];
-                v[k] = t;
+                double a = 0.0;
+                for (int j = lane; j < bd; j += 32) a += sv[k * bd + j];
+                t[k] = a;
             }
+            warp_sum<K>(t);
+        }
+        if (nblocks == 1) {
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) bc[k] = t[k];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = bc[k];
             return true;
         }
         const unsigned G = nblocks;
         double *part = partials + (size_t)slot * kMaxSums * G;
-        if (warp == 0) {
-            double t[K];
+        slot ^= 1;
+        if (threadIdx.x == 0) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) t[k] = lane < nw ? sr[k * 32 + lane] : 0.0;
+            for (int k = 0; k < K; ++k) part[(size_t)k * G + bid] = t[k];
+        }
+        if (!gbar()) return false;
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                double a = 0.0;
+                for (unsigned b = lane; b < G; b += 32) a += part[(size_t)k * G + b];
+                t[k] = a;
+            }
             warp_sum<K>(t);
             if (lane == 0) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) part[(size_t)k * G + bid] = t[k];
+                for (int k = 0; k < K; ++k) bc[k] = t[k];
             }
         }
-        if (!gbar()) return false;
+        __syncthreads();
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double t = 0.0;
-            for (unsigned b = lane; b < G; b += 32) t += part[(size_t)k * G + b];
-            v[k] = t;
-        }
-        warp_sum<K>(v);
-        slot ^= 1;
+        for (int k = 0; k < K; ++k) v[k] = bc[k];
         return true;
     }
 
@@ -271,29 +383,51 @@ struct Engine {
     using ACC = typename real_of<T>::type;                    // thread accumulator
     static constexpr int DS = dslots<T>();
     static constexpr int PW = Pack<T>::W;
+    static constexpr int CPS = 32 * sizeof(T) / 16;           // 16-byte chunks per slice
 
     const SysView<T> &sys;
     const SolveCtl &ctl;
-    // CTA geometry
-    int64_t gtid, gstride, gwarp, nwarps, nchunk;
-    int lane;
     GridSync &gs;
     // shared memory
     S *c;            // kMaxN
     S *bt;           // kMaxN
     Acct *acct;      // accounting, kept by thread 0 (uniform in the grid)
+    // ownership: slices [s_lo, s_hi), chunks [c_lo, c_hi)
+    int64_t s_lo, s_hi, c_lo, c_hi;
+    int lane;
 
     __device__ Engine(const SysView<T> &s, const SolveCtl &k, GridSync &g, S *c_, S *bt_, Acct *acct_)
         : sys(s), ctl(k), gs(g), c(c_), bt(bt_), acct(acct_) {
-        gtid = (int64_t)g.bid * blockDim.x + threadIdx.x;
-        gstride = (int64_t)g.nblocks * blockDim.x;
-        gwarp = gtid >> 5;
-        nwarps = gstride >> 5;
+        own_range(s.nslices, g.nblocks, g.bid, s_lo, s_hi);
+        c_lo = s_lo * CPS;
+        c_hi = s_hi * CPS;
         lane = threadIdx.x & 31;
-        nchunk = s.ld / PW;
     }
     __device__ __forceinline__ void op(int which, int cnt = 1) {
         if (threadIdx.x == 0) acct->ops[which] += cnt;
+    }
+
+    // Evaluate fn() in thread 0 only and give the value to every thread.
+    unsigned bslot = 0;
+    template <typename Fn>
+    __device__ __forceinline__ S once_s(Fn fn) {
+        const int k = bslot++ & 3;
+        if constexpr (is_cx<T>::value) {
+            if (threadIdx.x == 0) acct->z[k] = fn();
+            __syncthreads();
+            return acct->z[k];
+        } else {
+            if (threadIdx.x == 0) acct->d[k] = fn();
+            __syncthreads();
+            return acct->d[k];
+        }
+    }
+    template <typename Fn>
+    __device__ __forceinline__ double once_d(Fn fn) {
+        const int k = bslot++ & 3;
+        if (threadIdx.x == 0) acct->d[k] = fn();
+        __syncthreads();
+        return acct->d[k];
     }
 
     __device__ __forceinline__ const T *Qc(int k) const { return sys.Q + (int64_t)k * sys.ld; }
@@ -318,29 +452,53 @@ struct Engine {
     __device__ __forceinline__ bool reduce(double (&v)[K]) { return gs.template reduce<K>(v); }
     __device__ __forceinline__ bool sync() { return gs.sync(); }
 
-    // Streaming pass: fn(chunk, acc) for every 16-byte chunk owned by this
-    // thread, then a grid reduction of K accumulators.
+    __device__ __forceinline__ void tile_pass(TilePass &P, const T *const *in, int ni) {
+        P.ni = ni;
+        for (int i = 0; i < ni; ++i) P.in[i] = in[i];
+        P.tc = tile_chunks_for(ni);
+        P.c_lo = c_lo;
+        P.c_hi = c_hi;
+    }
+
+    // Streaming pass through the tile pipeline: fn(chunk, stage, k, acc)
+    // for every chunk of this CTA, then a team reduction of K sums.
     template <int K, typename Fn>
-    __device__ __forceinline__ bool vsum(Fn fn, double (&out)[K]) {
+    __device__ __forceinline__ bool tsum(const TilePass &P, Fn fn, double (&out)[K]) {
         ACC acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = ACC(0);
-        for (int64_t ch = gtid; ch < nchunk; ch += gstride) fn(ch, acc);
+        bool okw = true;
+        if ((threadIdx.x >> 5) == kConsumerWarps) {
+            if (lane == 0) okw = produce(gs.ring, P, gs.pseq, gs.timeout_ns);
+        } else {
+            okw = consume(gs.ring, P, gs.cseq, gs.timeout_ns,
+                          [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k, acc); });
+        }
+        if (!okw) gs.ring->failed = 1;
 #pragma unroll
         for (int k = 0; k < K; ++k) out[k] = (double)acc[k];
-        return reduce<K>(out);
+        if (!reduce<K>(out)) return false;
+        if (gs.ring->failed) { gs.ok = false; return false; }
+        return true;
     }
     template <typename Fn>
-    __device__ __forceinline__ bool vpass(Fn fn) {
-        ACC dummy[1];
-        for (int64_t ch = gtid; ch < nchunk; ch += gstride) fn(ch, dummy);
-        return sync();
+    __device__ __forceinline__ bool tpass(const TilePass &P, Fn fn) {
+        double none[1];
+        return tsum<1>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *) { fn(ch, st, k); }, none);
     }
 
-    // SELL-32 SpMV pass over this thread's slices.
+    // SELL-32 SpMV pass over the owned slices (matrix tiles through the
+    // ring).  A failed tile wait marks the ring; the pass's reduction then
+    // reports it.
     template <int K, typename Epi>
     __device__ __forceinline__ void spmv_rows(const T *xin, Epi epi, ACC (&acc)[K]) {
-        sell_spmv(sys.nslices, sys.slice_ptr, sys.scol, sys.sval, xin, gwarp, nwarps, lane, epi, acc);
+        if (!sell_spmv(gs.ring, gs.pseq, gs.cseq, gs.timeout_ns, s_lo, s_hi, sys.spt, sys.slice_ptr, sys.scol,
+                       sys.sval, xin, lane, epi, acc))
+            gs.ring->failed = 1;
+    }
+    __device__ __forceinline__ bool ring_ok() {
+        if (gs.ring->failed) { gs.ok = false; return false; }
+        return true;
     }
 
     // ------------------------------------------------------------------
@@ -367,7 +525,7 @@ struct Engine {
         double v[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
-        if (!reduce<K>(v)) return false;
+        if (!reduce<K>(v) || !ring_ok()) return false;
         bb = v[0];
         rr = v[1];
         qr = mk_coef<T>(v + 2);
@@ -376,8 +534,9 @@ struct Engine {
     }
 
     // Refined mode, inner start with x_0 = 0: b = r = g_0 = src * scale
-    // (src is the FP64 residual of the outer iteration), x = 0; sums
-    // ||b||^2, ||r||^2, q_1^H r.
+    // (src is the FP64 residual of the outer iteration, rows of this CTA),
+    // x = 0; sums ||b||^2, ||r||^2, q_1^H r.  Direct loads (one pass per
+    // outer step).
     __device__ __noinline__ bool ph_init_narrow(const typename wide_of<T>::type *src, double scale, double &bb,
                                                 double &rr, S &qr) {
         using TW = typename wide_of<T>::type;
@@ -385,31 +544,39 @@ struct Engine {
         static_assert(PW * sizeof(TW) == 32, "a chunk of the FP32 vector is two 16-byte source loads");
         const T *q1 = Qc(0);
         T *g0 = Gc(0);
+        ACC acc[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = ACC(0);
+        if ((threadIdx.x >> 5) < kConsumerWarps) {
+            for (int64_t ch = c_lo + threadIdx.x; ch < c_hi; ch += kConsumers) {
+                const uint4 *sp = reinterpret_cast<const uint4 *>(src) + 2 * ch;
+                uint4 w2[2] = {sp[0], sp[1]};
+                TW tw[PW];
+                memcpy(tw, w2, sizeof(tw));
+                Pack<T> p, zero;
+                Pack<T> qq = ldp_ro(q1, ch);
+#pragma unroll
+                for (int e = 0; e < PW; ++e) {
+                    p.e[e] = narrow_scaled(tw[e], scale);
+                    zero.e[e] = T{};
+                }
+                stp(sys.b, ch, p);
+                stp(sys.r, ch, p);
+                stp(g0, ch, p);
+                stp(sys.x, ch, zero);
+#pragma unroll
+                for (int e = 0; e < PW; ++e) {
+                    acc_nrm(&acc[0], p.e[e]);
+                    acc_nrm(&acc[1], p.e[e]);
+                    acc_dot(&acc[2], qq.e[e], p.e[e]);
+                }
+            }
+        }
+        fence_proxy_async_global();
         double v[K];
-        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
-            const uint4 *sp = reinterpret_cast<const uint4 *>(src) + 2 * ch;
-            uint4 w2[2] = {sp[0], sp[1]};
-            TW tw[PW];
-            memcpy(tw, w2, sizeof(tw));
-            Pack<T> p, zero;
-            Pack<T> qq = ldp_ro(q1, ch);
 #pragma unroll
-            for (int e = 0; e < PW; ++e) {
-                p.e[e] = narrow_scaled(tw[e], scale);
-                zero.e[e] = T{};
-            }
-            stp(sys.b, ch, p);
-            stp(sys.r, ch, p);
-            stp(g0, ch, p);
-            stp(sys.x, ch, zero);
-#pragma unroll
-            for (int e = 0; e < PW; ++e) {
-                acc_nrm(&acc[0], p.e[e]);
-                acc_nrm(&acc[1], p.e[e]);
-                acc_dot(&acc[2], qq.e[e], p.e[e]);
-            }
-        }, v);
-        if (!okk) return false;
+        for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
+        if (!reduce<K>(v)) return false;
         bb = v[0];
         rr = v[1];
         qr = mk_coef<T>(v + 2);
@@ -432,7 +599,7 @@ struct Engine {
         double v[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
-        if (!reduce<K>(v)) return false;
+        if (!reduce<K>(v) || !ring_ok()) return false;
         cval = mk_coef<T>(v);
         sbytes(1);
         return true;
@@ -452,7 +619,7 @@ struct Engine {
         double v[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
-        if (!reduce<K>(v)) return false;
+        if (!reduce<K>(v) || !ring_ok()) return false;
         zz = v[0];
         zu = mk_coef<T>(v + 1);
         sbytes(1);
@@ -464,13 +631,19 @@ struct Engine {
     __device__ __noinline__ bool ph_alpha(S alpha, int sl, int qcol, bool f0, double &rr, S &qr, S &fr) {
         constexpr int K = 1 + 2 * DS;
         const T a = to_t<T>(alpha), na = to_t<T>(-alpha);
-        const T *gp = Gc(sl);
-        const T *wp = Wc(sl);
-        const T *qp = qcol >= 0 ? Qc(qcol) : nullptr;
-        const T *fp = f0 ? Fc(0) : nullptr;
+        const bool hq = qcol >= 0;
+        const T *in[6] = {sys.x, Gc(sl), sys.r, Wc(sl), hq ? Qc(qcol) : nullptr, f0 ? Fc(0) : nullptr};
+        int ni = 4;
+        if (hq) in[ni++] = Qc(qcol);
+        if (f0) in[ni++] = Fc(0);
+        const int iq = 4, iff = hq ? 5 : 4;
+        TilePass P;
+        tile_pass(P, in, ni);
+        const int tc = P.tc;
         double v[K];
-        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
-            Pack<T> xx = ldp(sys.x, ch), gg = ldp(gp, ch), rv = ldp(sys.r, ch), ww = ldp(wp, ch);
+        bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
+            Pack<T> xx = lds<T>(st, tc, 0, k), gg = lds<T>(st, tc, 1, k), rv = lds<T>(st, tc, 2, k),
+                    ww = lds<T>(st, tc, 3, k);
 #pragma unroll
             for (int e = 0; e < PW; ++e) {
                 xx.e[e] = efma(a, gg.e[e], xx.e[e]);
@@ -480,13 +653,13 @@ struct Engine {
             stp(sys.r, ch, rv);
 #pragma unroll
             for (int e = 0; e < PW; ++e) acc_nrm(&acc[0], rv.e[e]);
-            if (qp) {
-                Pack<T> qq = ldp_ro(qp, ch);
+            if (hq) {
+                Pack<T> qq = lds<T>(st, tc, iq, k);
 #pragma unroll
                 for (int e = 0; e < PW; ++e) acc_dot(&acc[1], qq.e[e], rv.e[e]);
             }
-            if (fp) {
-                Pack<T> ff = ldp_ro(fp, ch);
+            if (f0) {
+                Pack<T> ff = lds<T>(st, tc, iff, k);
 #pragma unroll
                 for (int e = 0; e < PW; ++e) acc_dot(&acc[1 + DS], ff.e[e], rv.e[e]);
             }
@@ -495,7 +668,7 @@ struct Engine {
         rr = v[0];
         qr = mk_coef<T>(v + 1);
         fr = mk_coef<T>(v + 1 + DS);
-        vbytes(6 + (qp ? 1 : 0) + (fp ? 1 : 0));
+        vbytes(6 + (hq ? 1 : 0) + (f0 ? 1 : 0));
         return true;
     }
 
@@ -503,11 +676,14 @@ struct Engine {
     __device__ __noinline__ bool ph_omega(S omega, double &rr, S &qr) {
         constexpr int K = 1 + DS;
         const T om = to_t<T>(omega), nom = to_t<T>(-omega);
-        const T *qp = Qc(0);
+        const T *in[4] = {sys.x, sys.r, sys.z, Qc(0)};
+        TilePass P;
+        tile_pass(P, in, 4);
+        const int tc = P.tc;
         double v[K];
-        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
-            Pack<T> xx = ldp(sys.x, ch), uu = ldp(sys.r, ch), zz = ldp(sys.z, ch);
-            Pack<T> qq = ldp_ro(qp, ch);
+        bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
+            Pack<T> xx = lds<T>(st, tc, 0, k), uu = lds<T>(st, tc, 1, k), zz = lds<T>(st, tc, 2, k),
+                    qq = lds<T>(st, tc, 3, k);
 #pragma unroll
             for (int e = 0; e < PW; ++e) {
                 xx.e[e] = efma(om, uu.e[e], xx.e[e]);
@@ -533,10 +709,13 @@ struct Engine {
         constexpr int K = DS;
         const T b0 = to_t<T>(bt0);
         T *wp = Wc(sl);
-        const T *qp = Qc(qcol);
+        const T *in[3] = {sys.r, wp, Qc(qcol)};
+        TilePass P;
+        tile_pass(P, in, 3);
+        const int tc = P.tc;
         double v[K];
-        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
-            Pack<T> rv = ldp(sys.r, ch), ww = ldp(wp, ch), qq = ldp_ro(qp, ch);
+        bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
+            Pack<T> rv = lds<T>(st, tc, 0, k), ww = lds<T>(st, tc, 1, k), qq = lds<T>(st, tc, 2, k);
 #pragma unroll
             for (int e = 0; e < PW; ++e) ww.e[e] = efma(b0, ww.e[e], rv.e[e]);
             stp(wp, ch, ww);
@@ -554,11 +733,13 @@ struct Engine {
         constexpr int K = DS;
         const T bb = to_t<T>(bts);
         T *wp = Wc(sl);
-        const T *ws = Wc(s);
-        const T *qp = Qc(qcol);
+        const T *in[3] = {wp, Wc(s), Qc(qcol)};
+        TilePass P;
+        tile_pass(P, in, 3);
+        const int tc = P.tc;
         double v[K];
-        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
-            Pack<T> zw = ldp(wp, ch), w2 = ldp(ws, ch), qq = ldp_ro(qp, ch);
+        bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
+            Pack<T> zw = lds<T>(st, tc, 0, k), w2 = lds<T>(st, tc, 1, k), qq = lds<T>(st, tc, 2, k);
 #pragma unroll
             for (int e = 0; e < PW; ++e) zw.e[e] = efma(bb, w2.e[e], zw.e[e]);
             stp(wp, ch, zw);
@@ -576,36 +757,47 @@ struct Engine {
     //   first=true : z_w = r + bt[sl] w_sl                (empty s-loop)
     //   first=false: z_w += bt[last] w_last
     //   g = bt[sl] g_sl;  g += bt[t] g_t for t = sl+1..n-1;  g = z_w - g/omega
-    // sums f_1^H g when with_f.
+    // sums f_1^H g when with_f.  The first kMaxInputs-4 columns g_t come
+    // through the tile pipeline, any further ones by direct loads.
     __device__ __noinline__ bool ph_w_last(bool first, int sl, S inv_omega, bool with_f, S &d) {
         constexpr int K = DS;
         const int n = sys.n;
         const int last = n - 1;
         T *wp = Wc(sl);
         T *gp = Gc(sl);
-        const T *wl = Wc(last);
         const T bl = to_t<T>(bt[first ? sl : last]);
         const T b0 = to_t<T>(bt[sl]);
         const T nio = to_t<T>(-inv_omega);
-        const T *fp = with_f ? Fc(0) : nullptr;
         const int t0 = sl + 1;
+        const int nt = n - t0;                                     // g_t columns
+        const int ntile = nt < kMaxInputs - 4 ? nt : kMaxInputs - 4;
+        const T *in[kMaxInputs];
+        int ni = 0;
+        in[ni++] = wp;
+        in[ni++] = gp;
+        in[ni++] = first ? sys.r : Wc(last);
+        const int i_f = ni;
+        if (with_f) in[ni++] = Fc(0);
+        const int i_t = ni;
+        for (int t = 0; t < ntile; ++t) in[ni++] = Gc(t0 + t);
+        TilePass P;
+        tile_pass(P, in, ni);
+        const int tc = P.tc;
         double v[K];
-        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
-            Pack<T> zw = ldp(wp, ch), g = ldp(gp, ch);
+        bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
+            Pack<T> zw = lds<T>(st, tc, 0, k), g = lds<T>(st, tc, 1, k), o = lds<T>(st, tc, 2, k);
             if (first) {
-                Pack<T> rv = ldp(sys.r, ch);
 #pragma unroll
-                for (int e = 0; e < PW; ++e) zw.e[e] = efma(bl, zw.e[e], rv.e[e]);
+                for (int e = 0; e < PW; ++e) zw.e[e] = efma(bl, zw.e[e], o.e[e]);
             } else {
-                Pack<T> w2 = ldp(wl, ch);
 #pragma unroll
-                for (int e = 0; e < PW; ++e) zw.e[e] = efma(bl, w2.e[e], zw.e[e]);
+                for (int e = 0; e < PW; ++e) zw.e[e] = efma(bl, o.e[e], zw.e[e]);
             }
 #pragma unroll
             for (int e = 0; e < PW; ++e) g.e[e] = emul(b0, g.e[e]);
-            for (int t = t0; t < n; ++t) {
-                const T bb = to_t<T>(bt[t]);
-                Pack<T> gt = ldp(sys.G + (int64_t)t * sys.ld, ch);
+            for (int t = 0; t < nt; ++t) {
+                const T bb = to_t<T>(bt[t0 + t]);
+                Pack<T> gt = t < ntile ? lds<T>(st, tc, i_t + t, k) : ldp(sys.G + (int64_t)(t0 + t) * sys.ld, ch);
 #pragma unroll
                 for (int e = 0; e < PW; ++e) g.e[e] = efma(bb, gt.e[e], g.e[e]);
             }
@@ -613,15 +805,15 @@ struct Engine {
             for (int e = 0; e < PW; ++e) g.e[e] = efma(nio, g.e[e], zw.e[e]);
             stp(wp, ch, zw);
             stp(gp, ch, g);
-            if (fp) {
-                Pack<T> ff = ldp_ro(fp, ch);
+            if (with_f) {
+                Pack<T> ff = lds<T>(st, tc, i_f, k);
 #pragma unroll
                 for (int e = 0; e < PW; ++e) acc_dot(&acc[0], ff.e[e], g.e[e]);
             }
         }, v);
         if (!okk) return false;
         d = mk_coef<T>(v);
-        vbytes(5 + (n - t0) + (fp ? 1 : 0));
+        vbytes(5 + nt + (with_f ? 1 : 0));
         return true;
     }
 
@@ -629,10 +821,13 @@ struct Engine {
     __device__ __noinline__ bool ph_f_round(S beta, int s, int sl, int fcol, S &d) {
         const T bb = to_t<T>(beta);
         T *gp = Gc(sl);
-        const T *gs = Gc(s);
+        const T *in[3] = {gp, Gc(s), fcol >= 0 ? Fc(fcol) : nullptr};
+        TilePass P;
+        tile_pass(P, in, fcol >= 0 ? 3 : 2);
+        const int tc = P.tc;
         if (fcol < 0) {
-            bool okk = vpass([&](int64_t ch, ACC *) {
-                Pack<T> g = ldp(gp, ch), g2 = ldp(gs, ch);
+            bool okk = tpass(P, [&](int64_t ch, const unsigned char *st, int k) {
+                Pack<T> g = lds<T>(st, tc, 0, k), g2 = lds<T>(st, tc, 1, k);
 #pragma unroll
                 for (int e = 0; e < PW; ++e) g.e[e] = efma(bb, g2.e[e], g.e[e]);
                 stp(gp, ch, g);
@@ -641,10 +836,9 @@ struct Engine {
             return okk;
         }
         constexpr int K = DS;
-        const T *fp = Fc(fcol);
         double v[K];
-        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
-            Pack<T> g = ldp(gp, ch), g2 = ldp(gs, ch), ff = ldp_ro(fp, ch);
+        bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
+            Pack<T> g = lds<T>(st, tc, 0, k), g2 = lds<T>(st, tc, 1, k), ff = lds<T>(st, tc, 2, k);
 #pragma unroll
             for (int e = 0; e < PW; ++e) g.e[e] = efma(bb, g2.e[e], g.e[e]);
             stp(gp, ch, g);
@@ -661,10 +855,13 @@ struct Engine {
     __device__ __noinline__ bool ph_g_j0(S beta, int sl, int fcol, S &d) {
         const T bb = to_t<T>(beta);
         T *gp = Gc(sl);
-        const T *g0 = Gc(0);
+        const T *in[3] = {sys.r, Gc(0), fcol >= 0 ? Fc(fcol) : nullptr};
+        TilePass P;
+        tile_pass(P, in, fcol >= 0 ? 3 : 2);
+        const int tc = P.tc;
         if (fcol < 0) {
-            bool okk = vpass([&](int64_t ch, ACC *) {
-                Pack<T> rv = ldp(sys.r, ch), g2 = ldp(g0, ch), g;
+            bool okk = tpass(P, [&](int64_t ch, const unsigned char *st, int k) {
+                Pack<T> rv = lds<T>(st, tc, 0, k), g2 = lds<T>(st, tc, 1, k), g;
 #pragma unroll
                 for (int e = 0; e < PW; ++e) g.e[e] = efma(bb, g2.e[e], rv.e[e]);
                 stp(gp, ch, g);
@@ -673,10 +870,9 @@ struct Engine {
             return okk;
         }
         constexpr int K = DS;
-        const T *fp = Fc(fcol);
         double v[K];
-        bool okk = vsum<K>([&](int64_t ch, ACC *acc) {
-            Pack<T> rv = ldp(sys.r, ch), g2 = ldp(g0, ch), ff = ldp_ro(fp, ch), g;
+        bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
+            Pack<T> rv = lds<T>(st, tc, 0, k), g2 = lds<T>(st, tc, 1, k), ff = lds<T>(st, tc, 2, k), g;
 #pragma unroll
             for (int e = 0; e < PW; ++e) g.e[e] = efma(bb, g2.e[e], rv.e[e]);
             stp(gp, ch, g);
@@ -692,7 +888,6 @@ struct Engine {
     // ------------------------------------------------------------------
     // helpers
     // ------------------------------------------------------------------
-
     __device__ __forceinline__ void record(bool rec, int64_t iter, double err) {
         if (rec && ctl.err_hist && iter < ctl.hist_cap && gs.bid == 0 && threadIdx.x == 0)
             ctl.err_hist[iter] = err;
@@ -733,9 +928,11 @@ struct Engine {
             op(OP_NORM, 2);
             op(OP_MATVEC, 1);
         }
-        double bnrm2 = sqrt(bb);
-        if (bnrm2 == 0.0) bnrm2 = 1.0;
-        double err = sqrt(rr) / bnrm2;
+        const double bnrm2 = once_d([&] {
+            double t = sqrt(bb);
+            return t == 0.0 ? 1.0 : t;
+        });
+        double err = once_d([&] { return sqrt(rr) / bnrm2; });
         o.err = err;
         record(rec, 0, err);
         if (err < tol) { o.flag = 0; return o; }
@@ -757,13 +954,13 @@ struct Engine {
             for (int i = 1; i <= n - 1; ++i) {
                 o.i = i;
                 // steps 5-8: alpha, x, r, e (and f_1^H r in block 0)
-                S alpha = e / c[i - 1];
+                S alpha = once_s([&] { return e / c[i - 1]; });
                 double r2;
                 S qr;
                 if (!ph_alpha(alpha, i - 1, i, j == 0, r2, qr, fr)) return o;
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
-                err = sqrt(r2) / bnrm2;
+                err = once_d([&] { return sqrt(r2) / bnrm2; });
                 o.err = err;
                 iter++;
                 o.iter = iter;
@@ -775,7 +972,7 @@ struct Engine {
 
                 if (j >= 1) {
                     // steps 10-18: sweep the rest of block j-1 with q's
-                    S b0 = -(e / c[i]);
+                    S b0 = once_s([&] { return -(e / c[i]); });
                     if (threadIdx.x == 0) bt[i] = b0;
                     __syncthreads();
                     op(OP_SAXPY);
@@ -785,7 +982,7 @@ struct Engine {
                     } else {
                         if (!ph_w_first(b0, i, i + 1, d)) return o;
                         for (int s = i + 1; s <= n - 1; ++s) {
-                            S bs = -(d / c[s]);
+                            S bs = once_s([&] { return -(d / c[s]); });
                             if (threadIdx.x == 0) bt[s] = bs;
                             __syncthreads();
                             op(OP_DOT);
@@ -800,19 +997,19 @@ struct Engine {
                     op(OP_SAXPY);   // omega-correction
                     // steps 19-22: sweep block j with f's
                     for (int s = 0; s <= i - 1; ++s) {
-                        S beta = -(d / c[s]);
+                        S beta = once_s([&] { return -(d / c[s]); });
                         op(OP_DOT);
                         op(OP_SAXPY);
                         if (!ph_f_round(beta, s, i, s + 1 <= i - 1 ? s + 1 : -1, d)) return o;
                     }
                 } else {
                     // steps 24-29 (block 0)
-                    S beta = -(fr / c[0]);
+                    S beta = once_s([&] { return -(fr / c[0]); });
                     op(OP_DOT);
                     op(OP_SAXPY);
                     if (!ph_g_j0(beta, i, i >= 2 ? 1 : -1, d)) return o;
                     for (int s = 1; s <= i - 1; ++s) {
-                        beta = -(d / c[s]);
+                        beta = once_s([&] { return -(d / c[s]); });
                         op(OP_DOT);
                         op(OP_SAXPY);
                         if (!ph_f_round(beta, s, i, s + 1 <= i - 1 ? s + 1 : -1, d)) return o;
@@ -830,13 +1027,13 @@ struct Engine {
             // steps 34-36: alpha, x, u (u kept in r)
             o.i = n;
             {
-                S alpha = e / c[n - 1];
+                S alpha = once_s([&] { return e / c[n - 1]; });
                 double u2;
                 S dummy;
                 if (!ph_alpha(alpha, n - 1, -1, false, u2, dummy, fr)) return o;
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
-                err = sqrt(u2) / bnrm2;
+                err = once_d([&] { return sqrt(u2) / bnrm2; });
                 o.err = err;
                 if (err < tol) {
                     iter++;
@@ -853,21 +1050,24 @@ struct Engine {
                 op(OP_DOT);
                 if (zz == 0.0 || !isfinite(zz)) { o.flag = -1; return o; }
                 op(OP_DOT);
-                omega = zu / zz;
-                if (ctl.kappa > 0.0) {
-                    op(OP_NORM, 2);
-                    double arho = abs_of(zu) / (sqrt(zz) * sqrt(u2));
-                    if (arho < ctl.kappa && arho != 0.0) omega = (ctl.kappa * omega) / arho;
-                }
+                if (ctl.kappa > 0.0) op(OP_NORM, 2);
+                omega = once_s([&] {
+                    S om = zu / zz;
+                    if (ctl.kappa > 0.0) {
+                        double arho = abs_of(zu) / (sqrt(zz) * sqrt(u2));
+                        if (arho < ctl.kappa && arho != 0.0) om = (ctl.kappa * om) / arho;
+                    }
+                    return om;
+                });
                 if (is_zero(omega) || !finite_of(omega)) { o.flag = -1; return o; }
-                inv_omega = recip(omega);
+                inv_omega = once_s([&] { return recip(omega); });
                 // steps 39-41: x += omega u, r = u - omega A u, e = q_1^H r
                 S q1r;
                 double r2;
                 if (!ph_omega(omega, r2, q1r)) return o;
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
-                err = sqrt(r2) / bnrm2;
+                err = once_d([&] { return sqrt(r2) / bnrm2; });
                 o.err = err;
                 iter++;
                 o.iter = iter;
@@ -879,7 +1079,7 @@ struct Engine {
             }
             // steps 42-50: sweep block j with q's into slot 0
             {
-                S b0 = -(e / c[0]);
+                S b0 = once_s([&] { return -(e / c[0]); });
                 if (threadIdx.x == 0) bt[0] = b0;
                 __syncthreads();
                 op(OP_SAXPY);
@@ -889,7 +1089,7 @@ struct Engine {
                 } else {
                     if (!ph_w_first(b0, 0, 1, d)) return o;
                     for (int s = 1; s <= n - 1; ++s) {
-                        S bs = -(d / c[s]);
+                        S bs = once_s([&] { return -(d / c[s]); });
                         if (threadIdx.x == 0) bt[s] = bs;
                         __syncthreads();
                         op(OP_DOT);

@@ -53,6 +53,11 @@ __device__ void run_fp64_solve(Engine<T> &E, GridSync &gs, const SolveCtl &ctl, 
     }
 }
 
+// Allow the ring's dynamic shared memory for a kernel (idempotent).
+static cudaError_t allow_ring(const void *fn) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+}
+
 __device__ __forceinline__ void acct_reset(Acct &acct) {
     if (threadIdx.x == 0) {
         for (int q = 0; q < 5; ++q) acct.ops[q] = 0;
@@ -63,17 +68,21 @@ __device__ __forceinline__ void acct_reset(Acct &acct) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) solve_kernel(SysView<T> sys, SolveCtl ctl) {
+__global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, SolveCtl ctl) {
     using S = typename coef_of<T>::type;
-    __shared__ double red[2 * 32 * kMaxSums];
+    extern __shared__ unsigned char dsm[];
+    __shared__ double red[kMaxSums * (kThreads + 1)];
     __shared__ S cbuf[kMaxN];
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;
     __shared__ Acct acct;
+    __shared__ TileRing ring;
+    ring_init(&ring, ring_buffer(dsm));
     acct_reset(acct);
-    GridSync gs(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns);
+    GridSync gs(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring);
     Engine<T> E(sys, ctl, gs, cbuf, btbuf, &acct);
     run_fp64_solve(E, gs, ctl, acct, ctl.res);
+    ring_drain(&ring, gs.pseq, gs.cseq, ctl.timeout_ns);
 }
 
 // ===========================================================================
@@ -83,16 +92,21 @@ __global__ void __launch_bounds__(kThreads, 2) solve_kernel(SysView<T> sys, Solv
 // largest first by the host) and solves it alone: the same method with
 // CTA-wide barriers and reductions in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     batch_kernel(const BatchItem<T> *items, const int *order, int count, unsigned *queue) {
     using S = typename coef_of<T>::type;
-    __shared__ double red[2 * 32 * kMaxSums];
+    extern __shared__ unsigned char dsm[];
+    __shared__ TileRing ring;
+    __shared__ double red[kMaxSums * (kThreads + 1)];
     __shared__ S cbuf[kMaxN];
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;
     __shared__ Acct acct;
     __shared__ int s_next;
     __shared__ BatchItem<T> item;
+    ring_init(&ring, ring_buffer(dsm));
+    unsigned pseq = 0, cseq = 0;
+    uint64_t timeout = 2000000000ull;
     for (;;) {
         if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
         __syncthreads();
@@ -100,24 +114,35 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (q >= count) break;
         if (threadIdx.x == 0) item = items[order[q]];
         acct_reset(acct);   // includes the __syncthreads that publishes `item`
-        GridSync gs(red, &sflag);
+        timeout = item.ctl.timeout_ns;
+        GridSync gs(red, &sflag, timeout, &ring);
+        gs.pseq = pseq;
+        gs.cseq = cseq;
         Engine<T> E(item.sys, item.ctl, gs, cbuf, btbuf, &acct);
         run_fp64_solve(E, gs, item.ctl, acct, item.ctl.res);
+        pseq = gs.pseq;
+        cseq = gs.cseq;
         __syncthreads();
     }
+    ring_drain(&ring, pseq, cseq, timeout);
 }
 
 template <typename T32, typename T64>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     batch_refine_kernel(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue) {
     using S = typename coef_of<T32>::type;
-    __shared__ double red[2 * 32 * kMaxSums];
+    extern __shared__ unsigned char dsm[];
+    __shared__ TileRing ring;
+    __shared__ double red[kMaxSums * (kThreads + 1)];
     __shared__ S cbuf[kMaxN];
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;
     __shared__ Acct acct;
     __shared__ int s_next;
     __shared__ BatchItemR<T32, T64> item;
+    ring_init(&ring, ring_buffer(dsm));
+    unsigned pseq = 0, cseq = 0;
+    uint64_t timeout = 2000000000ull;
     for (;;) {
         if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
         __syncthreads();
@@ -125,10 +150,15 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (q >= count) break;
         if (threadIdx.x == 0) item = items[order[q]];
         acct_reset(acct);
-        GridSync gs(red, &sflag);
+        timeout = item.ctl.timeout_ns;
+        GridSync gs(red, &sflag, timeout, &ring);
+        gs.pseq = pseq;
+        gs.cseq = cseq;
         Engine<T32> E(item.sys, item.ctl, gs, cbuf, btbuf, &acct);
         Refiner<T64, T32> R(item.rv, gs, &acct, item.sys.x);
         RefineOut o = refine_solve<T32, T64>(E, R, item.ctl, item.rc);
+        pseq = gs.pseq;
+        cseq = gs.cseq;
         if (threadIdx.x == 0) {
             DevResult *res = item.ctl.res;
             res->flag = o.flag;
@@ -145,33 +175,41 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         __syncthreads();
     }
+    ring_drain(&ring, pseq, cseq, timeout);
 }
 
 template <typename T>
 cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
                          cudaStream_t st) {
-    batch_kernel<T><<<grid, kThreads, 0, st>>>(items, order, count, queue);
+    cudaError_t e = allow_ring((const void *)batch_kernel<T>);
+    if (e != cudaSuccess) return e;
+    batch_kernel<T><<<grid, kThreads, kRingBytes, st>>>(items, order, count, queue);
     return cudaGetLastError();
 }
 
 template <typename T32, typename T64>
 cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
                                 int grid, cudaStream_t st) {
-    batch_refine_kernel<T32, T64><<<grid, kThreads, 0, st>>>(items, order, count, queue);
+    cudaError_t e = allow_ring((const void *)batch_refine_kernel<T32, T64>);
+    if (e != cudaSuccess) return e;
+    batch_refine_kernel<T32, T64><<<grid, kThreads, kRingBytes, st>>>(items, order, count, queue);
     return cudaGetLastError();
 }
 
 template <typename T>
 int batch_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T>, kThreads, 0) != cudaSuccess) return 0;
+    if (allow_ring((const void *)batch_kernel<T>) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T>, kThreads, kRingBytes) != cudaSuccess)
+        return 0;
     return nb;
 }
 template <typename T32, typename T64>
 int batch_refine_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_refine_kernel<T32, T64>, kThreads, 0) !=
-        cudaSuccess)
+    if (allow_ring((const void *)batch_refine_kernel<T32, T64>) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_refine_kernel<T32, T64>, kThreads, kRingBytes) !=
+            cudaSuccess)
         return 0;
     return nb;
 }
@@ -181,16 +219,19 @@ cudaError_t launch_solve(const SysView<T> &sys, const SolveCtl &ctl, int grid, c
     SysView<T> s = sys;
     SolveCtl c = ctl;
     void *args[] = {(void *)&s, (void *)&c};
+    cudaError_t e = allow_ring((const void *)solve_kernel<T>);
+    if (e != cudaSuccess) return e;
     if (grid <= 1)
-        return cudaLaunchKernel((const void *)solve_kernel<T>, dim3(1), dim3(kThreads), args, 0, st);
+        return cudaLaunchKernel((const void *)solve_kernel<T>, dim3(1), dim3(kThreads), args, kRingBytes, st);
     return cudaLaunchCooperativeKernel((const void *)solve_kernel<T>, dim3(grid), dim3(kThreads), args,
-                                       0, st);
+                                       kRingBytes, st);
 }
 
 template <typename T>
 int solve_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<T>, kThreads, 0) != cudaSuccess)
+    if (allow_ring((const void *)solve_kernel<T>) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<T>, kThreads, kRingBytes) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -199,19 +240,23 @@ int solve_blocks_per_sm() {
 // FP32-inner / FP64-refined persistent solve kernel
 // ===========================================================================
 template <typename T32, typename T64>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     refine_kernel(SysView<T32> sys, RefView<T64> rv, SolveCtl ctl, RefCtl rc) {
     using S = typename coef_of<T32>::type;
-    __shared__ double red[2 * 32 * kMaxSums];
+    extern __shared__ unsigned char dsm[];
+    __shared__ TileRing ring;
+    __shared__ double red[kMaxSums * (kThreads + 1)];
     __shared__ S cbuf[kMaxN];
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;
     __shared__ Acct acct;
+    ring_init(&ring, ring_buffer(dsm));
     acct_reset(acct);
-    GridSync gs(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns);
+    GridSync gs(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring);
     Engine<T32> E(sys, ctl, gs, cbuf, btbuf, &acct);
     Refiner<T64, T32> R(rv, gs, &acct, sys.x);
     RefineOut o = refine_solve<T32, T64>(E, R, ctl, rc);
+    ring_drain(&ring, gs.pseq, gs.cseq, ctl.timeout_ns);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevResult *res = ctl.res;
         res->flag = o.flag;
@@ -237,17 +282,21 @@ cudaError_t launch_refine(const SysView<T32> &sys, const RefView<T64> &rv, const
     SolveCtl c = ctl;
     RefCtl q = rc;
     void *args[] = {(void *)&s, (void *)&r, (void *)&c, (void *)&q};
+    cudaError_t e = allow_ring((const void *)refine_kernel<T32, T64>);
+    if (e != cudaSuccess) return e;
     if (grid <= 1)
-        return cudaLaunchKernel((const void *)refine_kernel<T32, T64>, dim3(1), dim3(kThreads), args, 0, st);
+        return cudaLaunchKernel((const void *)refine_kernel<T32, T64>, dim3(1), dim3(kThreads), args, kRingBytes,
+                                st);
     return cudaLaunchCooperativeKernel((const void *)refine_kernel<T32, T64>, dim3(grid), dim3(kThreads),
-                                       args, 0, st);
+                                       args, kRingBytes, st);
 }
 
 template <typename T32, typename T64>
 int refine_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, refine_kernel<T32, T64>, kThreads, 0) !=
-        cudaSuccess)
+    if (allow_ring((const void *)refine_kernel<T32, T64>) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, refine_kernel<T32, T64>, kThreads, kRingBytes) !=
+            cudaSuccess)
         return 0;
     return nb;
 }

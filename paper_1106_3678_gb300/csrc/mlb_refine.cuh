@@ -24,6 +24,7 @@ struct RefView {
     const int64_t *slice_ptr;
     const int32_t *scol;
     const T64 *sval;   // FP64 values, same SELL-32 layout as the FP32 copy
+    int spt;           // slices per SpMV tile for FP64 values
     T64 *x;            // solution
     const T64 *b;
     T64 *r;            // true residual
@@ -42,22 +43,20 @@ struct Refiner {
     GridSync &gs;
     Acct *acct;
     const T32 *x32;   // inner solution d
-    int64_t gtid, gstride, gwarp, nwarps;
+    int64_t s_lo, s_hi;   // owned slices (the same rows as the inner engine)
     int lane;
 
     __device__ Refiner(const RefView<T64> &v_, GridSync &g, Acct *a, const T32 *x32_)
         : v(v_), gs(g), acct(a), x32(x32_) {
-        gtid = (int64_t)g.bid * blockDim.x + threadIdx.x;
-        gstride = (int64_t)g.nblocks * blockDim.x;
-        gwarp = gtid >> 5;
-        nwarps = gstride >> 5;
+        own_range(v_.nslices, g.nblocks, g.bid, s_lo, s_hi);
         lane = threadIdx.x & 31;
     }
 
     // r = b - A x in FP64; sums ||b||^2, ||r||^2.
     __device__ __noinline__ bool residual(double &bb, double &rr) {
         double acc[2] = {0.0, 0.0};
-        sell_spmv(v.nslices, v.slice_ptr, v.scol, v.sval, v.x, gwarp, nwarps, lane,
+        bool okt = sell_spmv(gs.ring, gs.pseq, gs.cseq, gs.timeout_ns, s_lo, s_hi, v.spt, v.slice_ptr, v.scol,
+                             v.sval, v.x, lane,
                   [&](int64_t row, T64 y, double(&a)[2]) {
                       T64 bv = v.b[row];
                       T64 rv = subT(bv, y);
@@ -66,7 +65,9 @@ struct Refiner {
                       acc_nrm(&a[1], rv);
                   },
                   acc);
+        if (!okt) gs.ring->failed = 1;
         if (!gs.template reduce<2>(acc)) return false;
+        if (gs.ring->failed) { gs.ok = false; return false; }
         bb = acc[0];
         rr = acc[1];
         if (threadIdx.x == 0) {
@@ -82,8 +83,10 @@ struct Refiner {
     __device__ __noinline__ bool update(double scale) {
         constexpr int PW = Pack<T32>::W;
         static_assert(PW * sizeof(T64) == 32, "an FP32 chunk maps to two FP64 chunks");
-        const int64_t nchunk = v.ld / PW;
-        for (int64_t ch = gtid; ch < nchunk; ch += gstride) {
+        constexpr int CPS = 32 * sizeof(T32) / 16;   // FP32 chunks per slice
+        const int64_t c_hi = s_hi * CPS;
+        const int64_t c_start = s_lo * CPS + ((threadIdx.x >> 5) < kConsumerWarps ? threadIdx.x : c_hi);
+        for (int64_t ch = c_start; ch < c_hi; ch += kConsumers) {
             Pack<T32> d = ldp(x32, ch);
             uint4 *xp = reinterpret_cast<uint4 *>(v.x) + 2 * ch;
             uint4 w2[2] = {xp[0], xp[1]};
@@ -95,6 +98,7 @@ struct Refiner {
             xp[0] = w2[0];
             xp[1] = w2[1];
         }
+        fence_proxy_async_global();
         if (threadIdx.x == 0) acct->bytes += (double)v.N * (2.0 * sizeof(T64) + sizeof(T32));
         return gs.sync();
     }
