@@ -149,12 +149,15 @@ int64_t csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp,
 // Slices per SpMV tile so that the widest tile (values of `vbytes` plus
 // 4-byte column indices) fits one shared-memory stage; 0 when one slice
 // alone does not fit (the SpMV then reads the matrix directly).
-int slices_per_tile(int64_t maxw, size_t vbytes) {
-    if (maxw <= 0) return kConsumerWarps;
-    const int64_t per_slice = maxw * 32 * (int64_t)(vbytes + 4);
+int slices_per_tile(int64_t maxw, size_t vbytes, int nepi) {
+    const int64_t per_slice = maxw * 32 * (int64_t)(vbytes + 4) + (int64_t)nepi * 32 * (int64_t)vbytes;
+    if (per_slice <= 0) return kConsumerWarps;
     int64_t spt = kStageBytes / per_slice;
     if (spt > kConsumerWarps) spt = kConsumerWarps;
     return (int)spt;
+}
+void set_spt(int (&spt)[3], int64_t maxw, size_t vbytes) {
+    for (int e = 0; e < 3; ++e) spt[e] = slices_per_tile(maxw, vbytes, e);
 }
 
 // A^H in CSR by a stable counting sort over columns (values conjugated for
@@ -192,7 +195,7 @@ SysView<T> make_view(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T *)h->sval;
-    v.spt = slices_per_tile(h->maxw, sizeof(T));
+    set_spt(v.spt, h->maxw, sizeof(T));
     v.Q = (const T *)h->Q;
     v.F = (const T *)h->F;
     v.G = (T *)h->G;
@@ -215,7 +218,7 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T32 *)h->sval32;
-    v.spt = slices_per_tile(h->maxw, sizeof(T32));
+    set_spt(v.spt, h->maxw, sizeof(T32));
     v.Q = (const T32 *)h->Q32;
     v.F = (const T32 *)h->F32;
     v.G = (T32 *)h->G32;
@@ -238,7 +241,7 @@ RefView<T64> make_ref_view(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T64 *)h->sval;
-    v.spt = slices_per_tile(h->maxw, sizeof(T64));
+    set_spt(v.spt, h->maxw, sizeof(T64));
     v.x = (T64 *)h->x;
     v.b = (const T64 *)h->b;
     v.r = (T64 *)h->r;

@@ -46,6 +46,7 @@ namespace mlb {
 constexpr int kThreads = kTileThreads;   // 15 consumer warps + 1 producer warp
 constexpr int kMaxN = 64;       // largest number of shadow vectors
 constexpr int kMaxSums = 8;     // doubles reduced per pass (max)
+constexpr int kRedDoubles = kMaxSums * (kThreads / 2 + 1);   // shared reduction scratch
 
 // Result record written by CTA 0 at the end of a solve.
 struct DevResult {
@@ -80,7 +81,7 @@ struct SysView {
     const int64_t *slice_ptr;   // SELL-32: slice s spans [slice_ptr[s], slice_ptr[s+1])
     const int32_t *scol;        // column of entry (slice, k, lane) at off + 32k + lane
     const T *sval;
-    int spt;                    // slices per SpMV tile (the widest tile fits one stage)
+    int spt[3];                 // slices per SpMV tile with 0, 1, 2 epilogue vectors (<= 0: no tiles)
     const T *Q;                 // ld x n
     const T *F;                 // ld x (n-1), F = A^H Q(:,0:n-2)
     T *G, *W;                   // ld x n rings
@@ -182,74 +183,162 @@ __device__ __forceinline__ T sell_slice_sum(const int32_t *cp, const T *vp, int 
     return sum;
 }
 
+// Row sum of a slice wider than the pipelined path takes, from a stage
+// (values at vp, column indices at cp, lane-strided by 32).  Out of line
+// so that its registers do not weigh on the pipelined loop.
+template <typename T>
+__device__ __noinline__ T sell_slice_sum_wide(const int32_t *cp, const T *vp, int w, const T *xin) {
+    T sum{};
+    int k = 0;
+    for (; k + 8 <= w; k += 8) {
+        T xw[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xw[u] = xin[cp[32 * (k + u)]];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum = efma(vp[32 * (k + u)], xw[u], sum);
+    }
+    if (k < w) {
+        T xw[7];
+#pragma unroll
+        for (int u = 0; u < 7; ++u)
+            if (k + u < w) xw[u] = xin[cp[32 * (k + u)]];
+#pragma unroll
+        for (int u = 0; u < 7; ++u)
+            if (k + u < w) sum = efma(vp[32 * (k + u)], xw[u], sum);
+    }
+    return sum;
+}
+
 // SELL-32 product over the slices [s_lo, s_hi) owned by this CTA: for
-// every row, y = sum_k a_{row,k} xin[col_k], then epi(row, y, acc).  The
-// producer warp streams tiles of `spt` slices (values and column indices)
-// into the shared-memory ring; consumer warp w takes slice w of each tile
-// and gathers x directly.  The epilogue's stores are fenced for later bulk
-// (async-proxy) reads.  Returns false when a tile wait timed out.
-template <typename T, typename Epi, typename AccArr>
+// every row, y = sum_k a_{row,k} xin[col_k], then fin(row, y, e, acc) where
+// e[i] = epi[i][row] for the NE epilogue vectors (rows of this CTA).  The
+// producer warp streams tiles of `spt` slices (values, column indices and
+// the epilogue entries of the tile's rows) into the shared-memory ring;
+// consumer warp w takes slice w of each tile.  Each warp is
+// software-pipelined across tiles: the x gathers of tile t+1 are issued
+// between the FMAs of tile t (each gather reuses the register its FMA has
+// just read), so the FP64 pipe and the memory system work at the same time
+// and the only global loads on a warp's critical path are the gathers.
+// The epilogue's stores are fenced for later bulk (async-proxy) reads.
+// Returns false when a tile wait timed out.
+template <int NE, typename T, typename Fin, typename AccArr>
 __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned &cseq, uint64_t timeout_ns,
                                           int64_t s_lo, int64_t s_hi, int spt, const int64_t *slice_ptr,
-                                          const int32_t *scol, const T *sval, const T *xin, int lane, Epi epi,
+                                          const int32_t *scol, const T *sval, const T *xin,
+                                          const T *const (&epi)[NE > 0 ? NE : 1], int lane, Fin fin,
                                           AccArr &acc) {
+    constexpr int kPipeW = 8;   // slices up to this width take the pipelined path
+    constexpr int NEA = NE > 0 ? NE : 1;
     const int cw = threadIdx.x >> 5;
+    const SliceOffsets off(R, slice_ptr, s_lo, s_hi);
     bool ok = true;
     if (spt <= 0) {
         // slices too wide for one stage: direct loads, no pipeline
         if (cw < kConsumerWarps) {
             for (int64_t s = s_lo + cw; s < s_hi; s += kConsumerWarps) {
-                const int64_t off = __ldg(slice_ptr + s);
-                const int w = (int)((__ldg(slice_ptr + s + 1) - off) >> 5);
-                epi(s * 32 + lane, sell_slice_sum(scol + off + lane, sval + off + lane, w, xin), acc);
+                const int64_t o = off(s);
+                const int w = (int)((off(s + 1) - o) >> 5);
+                const int64_t row = s * 32 + lane;
+                T e[NEA];
+#pragma unroll
+                for (int i = 0; i < NE; ++i) e[i] = epi[i][row];
+                fin(row, sell_slice_sum(scol + o + lane, sval + o + lane, w, xin), e, acc);
             }
         }
         fence_proxy_async_global();
         return true;
     }
     if (cw == kConsumerWarps) {
-        if (lane == 0)
-            ok = produce_sell(R, s_lo, s_hi, spt, slice_ptr, sval, (int)sizeof(T), scol, pseq, timeout_ns);
-    } else {
-        for (int64_t s0 = s_lo; s0 < s_hi; s0 += spt, ++cseq) {
-            const int st = (int)(cseq % kStages);
-            const unsigned use = cseq / kStages;
-            if (!mbar_wait(&R->full[st], use & 1u, timeout_ns)) { ok = false; break; }
-            const int64_t s1 = s0 + spt < s_hi ? s0 + spt : s_hi;
-            const unsigned char *stage = R->buf + (size_t)st * kStageBytes;
-            const int64_t s = s0 + cw;
-            if (s < s1) {
-                const int64_t e0 = __ldg(slice_ptr + s0);
-                const int64_t nv = __ldg(slice_ptr + s1) - e0;
-                const int64_t o = __ldg(slice_ptr + s) - e0;
-                const int w = (int)((__ldg(slice_ptr + s + 1) - e0 - o) >> 5);
-                const T *vp = reinterpret_cast<const T *>(stage) + o + lane;
-                const int32_t *cp = reinterpret_cast<const int32_t *>(stage + nv * sizeof(T)) + o + lane;
-                T sum{};
-                int k = 0;
-                for (; k + 8 <= w; k += 8) {
-                    T xv[8];
+        if (lane == 0) {
+            const void *ep[NEA];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) xv[u] = xin[cp[32 * (k + u)]];
+            for (int i = 0; i < NE; ++i) ep[i] = epi[i];
+            ok = produce_sell(R, s_lo, s_hi, spt, off, sval, (int)sizeof(T), scol, ep, NE, pseq, timeout_ns);
+        }
+        return ok;
+    }
+    // one slice of one tile, as seen by this warp: stage, entry offset of
+    // the slice in the stage (o), entries of the tile (nv), slice width w
+    // (w < 0: no slice for this warp in this tile)
+    struct Job {
+        int st, o, nv, w;
+    };
+    const int nt = (int)((s_hi - s_lo + spt - 1) / spt);
+    // copies in registers (the epilogue's generic stores could alias them)
+    unsigned char *const rbuf = R->buf;
+    const unsigned cs0 = cseq;
+    auto stage_of = [&](const Job &j) { return rbuf + (size_t)j.st * kStageBytes; };
+    auto vals = [&](const Job &j) { return reinterpret_cast<const T *>(stage_of(j)) + j.o + lane; };
+    auto cols = [&](const Job &j) {
+        return reinterpret_cast<const int32_t *>(stage_of(j) + (size_t)j.nv * sizeof(T)) + j.o + lane;
+    };
+    // epilogue entry i of this warp's row in the tile
+    auto epv = [&](const Job &j, int i) {
+        return reinterpret_cast<const T *>(stage_of(j) + (size_t)j.nv * (sizeof(T) + 4))[(i * spt + cw) * 32 + lane];
+    };
+    // wait for tile t and locate this warp's slice in it
+    auto locate = [&](int t, Job &j) -> bool {
+        const unsigned q = cs0 + (unsigned)t;
+        j.st = (int)(q % kStages);
+        j.o = j.nv = 0;
+        j.w = -1;
+        if (!mbar_wait(&R->full[j.st], (q / kStages) & 1u, timeout_ns)) return false;
+        const int64_t s0 = s_lo + (int64_t)t * spt;
+        const int64_t s1 = s0 + spt < s_hi ? s0 + spt : s_hi;
+        const int64_t s = s0 + cw;
+        if (s < s1) {
+            const int64_t e0 = off(s0), es = off(s);
+            j.nv = (int)(off(s1) - e0);
+            j.o = (int)(es - e0);
+            j.w = (int)((off(s + 1) - es) >> 5);
+        }
+        return true;
+    };
+    auto row_of = [&](int t) { return (s_lo + (int64_t)t * spt + cw) * 32 + lane; };
+    int done = 0;
+    if (nt > 0) {
+        Job ja, jb;
+        T xv[kPipeW];
+        ok = locate(0, ja);
+        if (ok && ja.w >= 0 && ja.w <= kPipeW) {
+            const int32_t *cp = cols(ja);
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) sum = efma(vp[32 * (k + u)], xv[u], sum);
-                }
-                if (k < w) {
-                    T xv[7];
+            for (int u = 0; u < kPipeW; ++u)
+                if (u < ja.w) xv[u] = xin[cp[32 * u]];
+        }
+        for (int t = 0; ok && t < nt; ++t) {
+            const bool more = t + 1 < nt;
+            if (more && !locate(t + 1, jb)) {
+                ok = false;
+                break;
+            }
+            // FMAs of tile t, each followed by the gather of tile t+1 that
+            // reuses its register
+            const bool na = ja.w >= 0 && ja.w <= kPipeW;
+            const bool nb = more && jb.w >= 0 && jb.w <= kPipeW;
+            const T *va = vals(ja);
+            const int32_t *cb = cols(jb);
+            T sum{};
 #pragma unroll
-                    for (int u = 0; u < 7; ++u)
-                        if (k + u < w) xv[u] = xin[cp[32 * (k + u)]];
+            for (int u = 0; u < kPipeW; ++u) {
+                if (na && u < ja.w) sum = efma(va[32 * u], xv[u], sum);
+                if (nb && u < jb.w) xv[u] = xin[cb[32 * u]];
+            }
+            if (ja.w > kPipeW) sum = sell_slice_sum_wide(cols(ja), va, ja.w, xin);
+            if (ja.w >= 0) {
+                T e[NEA];
 #pragma unroll
-                    for (int u = 0; u < 7; ++u)
-                        if (k + u < w) sum = efma(vp[32 * (k + u)], xv[u], sum);
-                }
-                epi(s * 32 + lane, sum, acc);
+                for (int i = 0; i < NE; ++i) e[i] = epv(ja, i);
+                fin(row_of(t), sum, e, acc);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&R->empty[st]);
+            if (lane == 0) mbar_arrive(&R->empty[ja.st]);
+            ++done;
+            ja = jb;
         }
-        fence_proxy_async_global();
     }
+    cseq = cs0 + (unsigned)done;
+    fence_proxy_async_global();
     return ok;
 }
 
@@ -278,7 +367,7 @@ struct GridSync {
     unsigned bid;       // this CTA's rank in the team
     BarrierState *bar;
     double *partials;   // [2][kMaxSums][gridDim]
-    double *red;        // shared, kMaxSums * (kThreads + 1)
+    double *red;        // shared, kRedDoubles
     int *sflag;         // shared
     uint64_t timeout_ns;
     unsigned epoch;
@@ -307,38 +396,48 @@ struct GridSync {
     }
 
     // Sum K values over the team; every thread of every CTA receives the
-    // same bits.  FP64 instructions are scarce on this GPU, so one warp does
-    // the arithmetic: threads stage their partials in shared memory; warp 0
-    // adds them (lane l: threads l, l+32, ... in order, then an xor-tree
-    // over the lanes); with several CTAs, warp 0 of every CTA then adds the
-    // CTA totals the same way (CTAs l, l+32, ...); the result is broadcast
-    // through shared memory.
+    // same bits.  A dependent FP64 add costs about 60 cycles on this GPU and
+    // one warp issues at most one FP64 instruction per ~60 cycles, so the
+    // sums are short trees spread over many warps, independent sums
+    // interleaved:
+    //   CTA level 0: lanes l < 16 of every warp add their value to lane
+    //                l+16's (256 partials per sum);
+    //   CTA level 1: task (k, g), g < 64, on its own thread, adds partials
+    //                g, g+64, g+128, g+192 as a pair tree;
+    //   CTA level 2: warp k adds the 64 level-1 results of sum k (lane l:
+    //                l and l+32), then an xor tree over the lanes;
+    //   team:        with several CTAs, warp k of every CTA adds the CTA
+    //                totals of sum k the same way (lane l: CTAs l, l+32, ...
+    //                as a pair tree, then the xor tree).
+    // Fixed order for a given team size: deterministic.
     template <int K>
     __device__ __forceinline__ bool reduce(double (&v)[K]) {
-        const int lane = threadIdx.x & 31;
-        const int warp = threadIdx.x >> 5;
-        const int bd = blockDim.x;
-        double *sv = red;                       // K * blockDim partials
-        double *bc = red + kMaxSums * kThreads; // K broadcast totals
+        static_assert(K <= kMaxSums && kThreads == 512, "reduction layout");
+        constexpr int P0 = kThreads / 2, G1 = P0 / 4;
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        double *sv = red;                     // K * P0 partials
+        double *bc = red + kMaxSums * P0;     // K totals
 #pragma unroll
-        for (int k = 0; k < K; ++k) sv[k * bd + threadIdx.x] = v[k];
-        __syncthreads();
-        double t[K];
-        if (warp == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                double a = 0.0;
-                for (int j = lane; j < bd; j += 32) a += sv[k * bd + j];
-                t[k] = a;
-            }
-            warp_sum<K>(t);
+        for (int k = 0; k < K; ++k) {
+            const double h = v[k] + __shfl_down_sync(0xffffffffu, v[k], 16);
+            if (lane < 16) sv[k * P0 + warp * 16 + lane] = h;
         }
-        if (nblocks == 1) {
-            if (threadIdx.x == 0) {
+        __syncthreads();
+        for (int task = tid; task < K * G1; task += kThreads) {
+            double *p = sv + (task / G1) * P0 + task % G1;
+            const double a0 = p[0], a1 = p[G1], a2 = p[2 * G1], a3 = p[3 * G1];
+            p[0] = (a0 + a1) + (a2 + a3);      // only this task reads slot 0
+        }
+        __syncthreads();
+        if (warp < K) {
+            const double *p = sv + warp * P0 + lane;
+            double t = p[0] + p[32];
 #pragma unroll
-                for (int k = 0; k < K; ++k) bc[k] = t[k];
-            }
-            __syncthreads();
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) bc[warp] = t;
+        }
+        __syncthreads();
+        if (nblocks == 1) {
 #pragma unroll
             for (int k = 0; k < K; ++k) v[k] = bc[k];
             return true;
@@ -346,23 +445,27 @@ struct GridSync {
         const unsigned G = nblocks;
         double *part = partials + (size_t)slot * kMaxSums * G;
         slot ^= 1;
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) part[(size_t)k * G + bid] = t[k];
+            for (int k = 0; k < K; ++k) part[(size_t)k * G + bid] = bc[k];
         }
         if (!gbar()) return false;
-        if (warp == 0) {
+        if (warp < K) {
+            const double *p = part + (size_t)warp * G;
+            double t = 0.0;
+            for (unsigned b0 = 0; b0 < G; b0 += 256) {
+                double x[8];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                double a = 0.0;
-                for (unsigned b = lane; b < G; b += 32) a += part[(size_t)k * G + b];
-                t[k] = a;
+                for (int m = 0; m < 8; ++m) {
+                    const unsigned b = b0 + lane + 32 * m;
+                    x[m] = b < G ? p[b] : 0.0;
+                }
+                const double s8 = ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+                t = b0 == 0 ? s8 : t + s8;
             }
-            warp_sum<K>(t);
-            if (lane == 0) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) bc[k] = t[k];
-            }
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) bc[warp] = t;
         }
         __syncthreads();
 #pragma unroll
@@ -402,6 +505,7 @@ struct Engine {
         c_lo = s_lo * CPS;
         c_hi = s_hi * CPS;
         lane = threadIdx.x & 31;
+        soff_load(g.ring, s.slice_ptr, s_lo, s_hi);
     }
     __device__ __forceinline__ void op(int which, int cnt = 1) {
         if (threadIdx.x == 0) acct->ops[which] += cnt;
@@ -468,11 +572,18 @@ struct Engine {
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = ACC(0);
         bool okw = true;
+        TileRing *const ring = gs.ring;
+        const uint64_t to = gs.timeout_ns;
         if ((threadIdx.x >> 5) == kConsumerWarps) {
-            if (lane == 0) okw = produce(gs.ring, P, gs.pseq, gs.timeout_ns);
+            if (lane == 0) {
+                unsigned sq = gs.pseq;
+                okw = produce(ring, P, sq, to);
+                gs.pseq = sq;
+            }
         } else {
-            okw = consume(gs.ring, P, gs.cseq, gs.timeout_ns,
-                          [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k, acc); });
+            unsigned sq = gs.cseq;
+            okw = consume(ring, P, sq, to, [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k, acc); });
+            gs.cseq = sq;
         }
         if (!okw) gs.ring->failed = 1;
 #pragma unroll
@@ -490,11 +601,14 @@ struct Engine {
     // SELL-32 SpMV pass over the owned slices (matrix tiles through the
     // ring).  A failed tile wait marks the ring; the pass's reduction then
     // reports it.
-    template <int K, typename Epi>
-    __device__ __forceinline__ void spmv_rows(const T *xin, Epi epi, ACC (&acc)[K]) {
-        if (!sell_spmv(gs.ring, gs.pseq, gs.cseq, gs.timeout_ns, s_lo, s_hi, sys.spt, sys.slice_ptr, sys.scol,
-                       sys.sval, xin, lane, epi, acc))
-            gs.ring->failed = 1;
+    template <int K, int NE, typename Fin>
+    __device__ __forceinline__ void spmv_rows(const T *xin, const T *const (&epi)[NE], Fin fin, ACC (&acc)[K]) {
+        unsigned ps = gs.pseq, cs = gs.cseq;
+        const bool okw = sell_spmv<NE>(gs.ring, ps, cs, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
+                                       sys.scol, sys.sval, xin, epi, lane, fin, acc);
+        gs.pseq = ps;
+        gs.cseq = cs;
+        if (!okw) gs.ring->failed = 1;
     }
     __device__ __forceinline__ bool ring_ok() {
         if (gs.ring->failed) { gs.ok = false; return false; }
@@ -513,14 +627,15 @@ struct Engine {
         for (int k = 0; k < K; ++k) acc[k] = ACC(0);
         const T *q1 = Qc(0);
         T *g0 = Gc(0);
-        spmv_rows<K>(sys.x, [&](int64_t row, T y, ACC(&a)[K]) {
-            T bv = sys.b[row];
-            T rv = subT(bv, y);
-            sys.r[row] = rv;
+        const T *epi[2] = {sys.b, q1};
+        T *const r = sys.r;
+        spmv_rows<K>(sys.x, epi, [&](int64_t row, T y, const T (&e)[2], ACC(&a)[K]) {
+            T rv = subT(e[0], y);
+            r[row] = rv;
             if (write_g0) g0[row] = rv;
-            acc_nrm(&a[0], bv);
+            acc_nrm(&a[0], e[0]);
             acc_nrm(&a[1], rv);
-            acc_dot(&a[2], ldg_val(q1 + row), rv);
+            acc_dot(&a[2], e[1], rv);
         }, acc);
         double v[K];
 #pragma unroll
@@ -547,8 +662,12 @@ struct Engine {
         ACC acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = ACC(0);
+        T *const bq = sys.b;
+        T *const rq = sys.r;
+        T *const xq = sys.x;
+        const int64_t clo = c_lo, chi = c_hi;
         if ((threadIdx.x >> 5) < kConsumerWarps) {
-            for (int64_t ch = c_lo + threadIdx.x; ch < c_hi; ch += kConsumers) {
+            for (int64_t ch = clo + threadIdx.x; ch < chi; ch += kConsumers) {
                 const uint4 *sp = reinterpret_cast<const uint4 *>(src) + 2 * ch;
                 uint4 w2[2] = {sp[0], sp[1]};
                 TW tw[PW];
@@ -560,10 +679,10 @@ struct Engine {
                     p.e[e] = narrow_scaled(tw[e], scale);
                     zero.e[e] = T{};
                 }
-                stp(sys.b, ch, p);
-                stp(sys.r, ch, p);
+                stp(bq, ch, p);
+                stp(rq, ch, p);
                 stp(g0, ch, p);
-                stp(sys.x, ch, zero);
+                stp(xq, ch, zero);
 #pragma unroll
                 for (int e = 0; e < PW; ++e) {
                     acc_nrm(&acc[0], p.e[e]);
@@ -592,9 +711,10 @@ struct Engine {
         for (int k = 0; k < K; ++k) acc[k] = ACC(0);
         const T *q = Qc(qcol);
         T *w = Wc(sl);
-        spmv_rows<K>(Gc(sl), [&](int64_t row, T y, ACC(&a)[K]) {
+        const T *epi[1] = {q};
+        spmv_rows<K>(Gc(sl), epi, [&](int64_t row, T y, const T (&e)[1], ACC(&a)[K]) {
             w[row] = y;
-            acc_dot(&a[0], ldg_val(q + row), y);
+            acc_dot(&a[0], e[0], y);
         }, acc);
         double v[K];
 #pragma unroll
@@ -611,10 +731,12 @@ struct Engine {
         ACC acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = ACC(0);
-        spmv_rows<K>(sys.r, [&](int64_t row, T y, ACC(&a)[K]) {
-            sys.z[row] = y;
+        const T *epi[1] = {sys.r};
+        T *const z = sys.z;
+        spmv_rows<K>(sys.r, epi, [&](int64_t row, T y, const T (&e)[1], ACC(&a)[K]) {
+            z[row] = y;
             acc_nrm(&a[0], y);
-            acc_dot(&a[1], y, sys.r[row]);
+            acc_dot(&a[1], y, e[0]);
         }, acc);
         double v[K];
 #pragma unroll
@@ -637,6 +759,8 @@ struct Engine {
         if (hq) in[ni++] = Qc(qcol);
         if (f0) in[ni++] = Fc(0);
         const int iq = 4, iff = hq ? 5 : 4;
+        T *const xo = sys.x;
+        T *const ro = sys.r;
         TilePass P;
         tile_pass(P, in, ni);
         const int tc = P.tc;
@@ -649,8 +773,8 @@ struct Engine {
                 xx.e[e] = efma(a, gg.e[e], xx.e[e]);
                 rv.e[e] = efma(na, ww.e[e], rv.e[e]);
             }
-            stp(sys.x, ch, xx);
-            stp(sys.r, ch, rv);
+            stp(xo, ch, xx);
+            stp(ro, ch, rv);
 #pragma unroll
             for (int e = 0; e < PW; ++e) acc_nrm(&acc[0], rv.e[e]);
             if (hq) {
@@ -677,6 +801,8 @@ struct Engine {
         constexpr int K = 1 + DS;
         const T om = to_t<T>(omega), nom = to_t<T>(-omega);
         const T *in[4] = {sys.x, sys.r, sys.z, Qc(0)};
+        T *const xo = sys.x;
+        T *const ro = sys.r;
         TilePass P;
         tile_pass(P, in, 4);
         const int tc = P.tc;
@@ -689,8 +815,8 @@ struct Engine {
                 xx.e[e] = efma(om, uu.e[e], xx.e[e]);
                 uu.e[e] = efma(nom, zz.e[e], uu.e[e]);
             }
-            stp(sys.x, ch, xx);
-            stp(sys.r, ch, uu);
+            stp(xo, ch, xx);
+            stp(ro, ch, uu);
 #pragma unroll
             for (int e = 0; e < PW; ++e) {
                 acc_nrm(&acc[0], uu.e[e]);
@@ -780,6 +906,9 @@ struct Engine {
         if (with_f) in[ni++] = Fc(0);
         const int i_t = ni;
         for (int t = 0; t < ntile; ++t) in[ni++] = Gc(t0 + t);
+        const T *const Gb = sys.G;
+        const int64_t ldv = sys.ld;
+        const S *const btl = bt;
         TilePass P;
         tile_pass(P, in, ni);
         const int tc = P.tc;
@@ -796,8 +925,8 @@ struct Engine {
 #pragma unroll
             for (int e = 0; e < PW; ++e) g.e[e] = emul(b0, g.e[e]);
             for (int t = 0; t < nt; ++t) {
-                const T bb = to_t<T>(bt[t0 + t]);
-                Pack<T> gt = t < ntile ? lds<T>(st, tc, i_t + t, k) : ldp(sys.G + (int64_t)(t0 + t) * sys.ld, ch);
+                const T bb = to_t<T>(btl[t0 + t]);
+                Pack<T> gt = t < ntile ? lds<T>(st, tc, i_t + t, k) : ldp(Gb + (int64_t)(t0 + t) * ldv, ch);
 #pragma unroll
                 for (int e = 0; e < PW; ++e) g.e[e] = efma(bb, gt.e[e], g.e[e]);
             }

@@ -71,7 +71,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, SolveCtl ctl) {
     using S = typename coef_of<T>::type;
     extern __shared__ unsigned char dsm[];
-    __shared__ double red[kMaxSums * (kThreads + 1)];
+    __shared__ double red[kRedDoubles];
     __shared__ S cbuf[kMaxN];
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     using S = typename coef_of<T>::type;
     extern __shared__ unsigned char dsm[];
     __shared__ TileRing ring;
-    __shared__ double red[kMaxSums * (kThreads + 1)];
+    __shared__ double red[kRedDoubles];
     __shared__ S cbuf[kMaxN];
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     using S = typename coef_of<T32>::type;
     extern __shared__ unsigned char dsm[];
     __shared__ TileRing ring;
-    __shared__ double red[kMaxSums * (kThreads + 1)];
+    __shared__ double red[kRedDoubles];
     __shared__ S cbuf[kMaxN];
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     using S = typename coef_of<T32>::type;
     extern __shared__ unsigned char dsm[];
     __shared__ TileRing ring;
-    __shared__ double red[kMaxSums * (kThreads + 1)];
+    __shared__ double red[kRedDoubles];
     __shared__ S cbuf[kMaxN];
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;

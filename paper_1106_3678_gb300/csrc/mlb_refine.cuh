@@ -24,7 +24,7 @@ struct RefView {
     const int64_t *slice_ptr;
     const int32_t *scol;
     const T64 *sval;   // FP64 values, same SELL-32 layout as the FP32 copy
-    int spt;           // slices per SpMV tile for FP64 values
+    int spt[3];        // slices per SpMV tile for FP64 values, 0/1/2 epilogue vectors
     T64 *x;            // solution
     const T64 *b;
     T64 *r;            // true residual
@@ -55,16 +55,20 @@ struct Refiner {
     // r = b - A x in FP64; sums ||b||^2, ||r||^2.
     __device__ __noinline__ bool residual(double &bb, double &rr) {
         double acc[2] = {0.0, 0.0};
-        bool okt = sell_spmv(gs.ring, gs.pseq, gs.cseq, gs.timeout_ns, s_lo, s_hi, v.spt, v.slice_ptr, v.scol,
-                             v.sval, v.x, lane,
-                  [&](int64_t row, T64 y, double(&a)[2]) {
-                      T64 bv = v.b[row];
-                      T64 rv = subT(bv, y);
-                      v.r[row] = rv;
-                      acc_nrm(&a[0], bv);
-                      acc_nrm(&a[1], rv);
-                  },
-                  acc);
+        const T64 *epi[1] = {v.b};
+        T64 *const r = v.r;
+        unsigned ps = gs.pseq, cs = gs.cseq;
+        bool okt = sell_spmv<1>(gs.ring, ps, cs, gs.timeout_ns, s_lo, s_hi, v.spt[1], v.slice_ptr, v.scol, v.sval,
+                                v.x, epi, lane,
+                                [&](int64_t row, T64 y, const T64 (&e)[1], double(&a)[2]) {
+                                    T64 rv = subT(e[0], y);
+                                    r[row] = rv;
+                                    acc_nrm(&a[0], e[0]);
+                                    acc_nrm(&a[1], rv);
+                                },
+                                acc);
+        gs.pseq = ps;
+        gs.cseq = cs;
         if (!okt) gs.ring->failed = 1;
         if (!gs.template reduce<2>(acc)) return false;
         if (gs.ring->failed) { gs.ok = false; return false; }
@@ -86,9 +90,11 @@ struct Refiner {
         constexpr int CPS = 32 * sizeof(T32) / 16;   // FP32 chunks per slice
         const int64_t c_hi = s_hi * CPS;
         const int64_t c_start = s_lo * CPS + ((threadIdx.x >> 5) < kConsumerWarps ? threadIdx.x : c_hi);
+        const T32 *const d32 = x32;
+        T64 *const x64 = v.x;
         for (int64_t ch = c_start; ch < c_hi; ch += kConsumers) {
-            Pack<T32> d = ldp(x32, ch);
-            uint4 *xp = reinterpret_cast<uint4 *>(v.x) + 2 * ch;
+            Pack<T32> d = ldp(d32, ch);
+            uint4 *xp = reinterpret_cast<uint4 *>(x64) + 2 * ch;
             uint4 w2[2] = {xp[0], xp[1]};
             T64 xv[PW];
             memcpy(xv, w2, sizeof(xv));

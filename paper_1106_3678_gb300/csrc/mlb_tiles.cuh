@@ -28,7 +28,7 @@ constexpr int kConsumerWarps = 15;                  // 480 consumer threads
 constexpr int kConsumers = 32 * kConsumerWarps;
 constexpr int kTileThreads = kConsumers + 32;       // + one producer warp
 constexpr int kStages = 4;
-constexpr int kStageBytes = 40 * 1024;              // 160 KB of stages
+constexpr int kStageBytes = 44 * 1024;              // 176 KB of stages
 constexpr int kTileChunks = kConsumers;             // 16-byte chunks per input per tile (max)
 constexpr int kMaxInputs = 24;
 
@@ -71,6 +71,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+// Bulk copy with an L2 eviction-priority hint (for data streamed once).
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // Ring state of one CTA (in shared memory; producer and consumers advance
@@ -82,6 +96,12 @@ struct TileRing {
     unsigned issued;         // tiles issued (producer lane 0 only)
     unsigned consumed;       // tiles consumed (every consumer thread, uniform)
     int failed;              // set when a wait timed out
+    // Cache of the SELL-32 slice offsets of this CTA's slice range:
+    // soff[i] = slice_ptr[soff_lo + i] - soff_base for i = 0..soff_hi-soff_lo
+    // (kept in the dynamic shared memory after the stages).
+    int32_t *soff;
+    const int64_t *soff_src; // slice_ptr the cache was filled from (null: empty)
+    int64_t soff_lo, soff_hi, soff_base;
 };
 
 __device__ __forceinline__ void ring_init(TileRing *R, unsigned char *buf) {
@@ -92,13 +112,59 @@ __device__ __forceinline__ void ring_init(TileRing *R, unsigned char *buf) {
         }
         R->buf = buf;
         R->failed = 0;
+        R->soff = reinterpret_cast<int32_t *>(buf + (size_t)kStages * kStageBytes);
+        R->soff_src = nullptr;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 }
 
-// Dynamic shared memory a kernel needs for the ring (plus alignment slack).
-constexpr size_t kRingBytes = (size_t)kStages * kStageBytes + 128;
+// Slice offsets cached per CTA (slices of one CTA's share, plus one).
+constexpr int kSoffCap = 2048;
+
+// Dynamic shared memory a kernel needs for the ring and the offset cache
+// (plus alignment slack).
+constexpr size_t kRingBytes = (size_t)kStages * kStageBytes + (size_t)kSoffCap * 4 + 128;
+
+// Fill the slice-offset cache for slices [s_lo, s_hi] (all threads of the
+// CTA call this).  The cache stays empty when the range has more than
+// kSoffCap - 1 slices or spans 2^31 or more entries; SpMV passes then read
+// slice_ptr from global memory.
+__device__ __forceinline__ void soff_load(TileRing *R, const int64_t *slice_ptr, int64_t s_lo, int64_t s_hi) {
+    __syncthreads();   // no thread still reads an earlier cache
+    const int64_t n = s_hi - s_lo;
+    const int64_t base = __ldg(slice_ptr + s_lo);
+    const bool fits = n + 1 <= kSoffCap && __ldg(slice_ptr + s_hi) - base < ((int64_t)1 << 31);
+    if (fits)
+        for (int64_t i = threadIdx.x; i <= n; i += blockDim.x)
+            R->soff[i] = (int32_t)(__ldg(slice_ptr + s_lo + i) - base);
+    if (threadIdx.x == 0) {
+        R->soff_src = fits ? slice_ptr : nullptr;
+        R->soff_lo = s_lo;
+        R->soff_hi = s_hi;
+        R->soff_base = base;
+    }
+    __syncthreads();
+}
+
+// Offset source of one SpMV pass over slices [s_lo, s_hi): the cache when
+// it holds that range of that matrix, else global memory.
+struct SliceOffsets {
+    const int32_t *so;       // cache, or null
+    const int64_t *sp;       // slice_ptr
+    int64_t lo, base;
+    __device__ __forceinline__ SliceOffsets(const TileRing *R, const int64_t *slice_ptr, int64_t s_lo, int64_t s_hi)
+        : so(nullptr), sp(slice_ptr), lo(s_lo), base(0) {
+        if (R->soff_src == slice_ptr && R->soff_lo == s_lo && R->soff_hi == s_hi) {
+            so = R->soff;
+            base = R->soff_base;
+        }
+    }
+    // slice_ptr[s] for s in [lo, hi]
+    __device__ __forceinline__ int64_t operator()(int64_t s) const {
+        return so ? base + so[s - lo] : __ldg(sp + s);
+    }
+};
 
 __device__ __forceinline__ unsigned char *ring_buffer(unsigned char *dsm) {
     return (unsigned char *)(((uintptr_t)dsm + 127) & ~(uintptr_t)127);
@@ -145,43 +211,64 @@ __device__ __forceinline__ bool produce(TileRing *R, const TilePass &P, unsigned
 // stage + i*tc*16 + k*16 for input i), then release the stage.
 template <typename Fn>
 __device__ __forceinline__ bool consume(TileRing *R, const TilePass &P, unsigned &seq, uint64_t timeout_ns, Fn fn) {
+    // Everything the loop needs is copied into registers first: the
+    // consumers' generic stores could alias the pass descriptor, so reading
+    // it inside the loop would reload it from memory after every store.
     const int nt = P.ntiles();
+    const int tc = P.tc;
+    const int64_t c_lo = P.c_lo, c_hi = P.c_hi;
+    unsigned char *const buf = R->buf;
+    unsigned sq = seq;
     const int tid = threadIdx.x;   // < kConsumers
-    for (int t = 0; t < nt; ++t, ++seq) {
-        const int s = (int)(seq % kStages);
-        const unsigned use = seq / kStages;
-        if (!mbar_wait(&R->full[s], use & 1u, timeout_ns)) return false;
-        const int64_t c0 = P.c_lo + (int64_t)t * P.tc;
-        int64_t cn = P.c_hi - c0;
-        if (cn > P.tc) cn = P.tc;
-        const unsigned char *stage = R->buf + (size_t)s * kStageBytes;
+    for (int t = 0; t < nt; ++t, ++sq) {
+        const int s = (int)(sq % kStages);
+        const unsigned use = sq / kStages;
+        if (!mbar_wait(&R->full[s], use & 1u, timeout_ns)) {
+            seq = sq;
+            return false;
+        }
+        const int64_t c0 = c_lo + (int64_t)t * tc;
+        int64_t cn = c_hi - c0;
+        if (cn > tc) cn = tc;
+        const unsigned char *stage = buf + (size_t)s * kStageBytes;
         for (int k = tid; k < cn; k += kConsumers) fn(c0 + k, stage, k);
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&R->empty[s]);
     }
+    seq = sq;
     fence_proxy_async_global();
     return true;
 }
 
 // SELL-32 tiles: `spt` consecutive slices [s0, s0+spt) of this CTA's slice
-// range; the stage holds their values (first) and column indices.
+// range.  A stage holds their values, then their column indices, then for
+// each of the `ne` epilogue vectors the 32*spt entries of the tile's rows
+// (those rows belong to this CTA).  The matrix is streamed once per
+// product, so its copies carry an L2 evict-first hint.
 __device__ __forceinline__ bool produce_sell(TileRing *R, int64_t s_lo, int64_t s_hi, int spt,
-                                             const int64_t *slice_ptr, const void *sval, int vbytes,
-                                             const int32_t *scol, unsigned &seq, uint64_t timeout_ns) {
+                                             const SliceOffsets &off, const void *sval, int vbytes,
+                                             const int32_t *scol, const void *const *epi, int ne,
+                                             unsigned &seq, uint64_t timeout_ns) {
+    const uint64_t pol = l2_evict_first_policy();
     for (int64_t s0 = s_lo; s0 < s_hi; s0 += spt, ++seq) {
         const int s = (int)(seq % kStages);
         const unsigned use = seq / kStages;
         if (use > 0 && !mbar_wait(&R->empty[s], (use - 1) & 1u, timeout_ns)) return false;
         const int64_t s1 = s0 + spt < s_hi ? s0 + spt : s_hi;
-        const int64_t e0 = __ldg(slice_ptr + s0), e1 = __ldg(slice_ptr + s1);
+        const int64_t e0 = off(s0), e1 = off(s1);
         const unsigned nv = (unsigned)(e1 - e0);
         const unsigned bv = nv * (unsigned)vbytes, bc = nv * 4u;
-        mbar_arrive_expect_tx(&R->full[s], bv + bc);
+        const unsigned be = (unsigned)(s1 - s0) * 32u * (unsigned)vbytes;
+        mbar_arrive_expect_tx(&R->full[s], bv + bc + be * (unsigned)ne);
         unsigned char *dst = R->buf + (size_t)s * kStageBytes;
         if (nv > 0) {
-            bulk_g2s(dst, (const unsigned char *)sval + e0 * vbytes, bv, &R->full[s]);
-            bulk_g2s(dst + bv, scol + e0, bc, &R->full[s]);
+            bulk_g2s_hint(dst, (const unsigned char *)sval + e0 * vbytes, bv, &R->full[s], pol);
+            bulk_g2s_hint(dst + bv, scol + e0, bc, &R->full[s], pol);
         }
+        unsigned char *de = dst + bv + bc;
+        for (int i = 0; i < ne; ++i)
+            bulk_g2s(de + (size_t)i * spt * 32 * vbytes, (const unsigned char *)epi[i] + s0 * 32 * vbytes, be,
+                     &R->full[s]);
     }
     return true;
 }
