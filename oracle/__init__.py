@@ -63,7 +63,7 @@ def load(path: str | None = None):
         f = getattr(lib, f"orc_mlbicgstabt_{sfx}")
         f.restype = C.c_int
         f.argtypes = [C.c_int64, P, P, P, C.c_int32, P, P, P, C.c_int64,
-                      C.c_double, C.c_double, C.POINTER(_Result),
+                      C.c_double, C.c_double, P, C.POINTER(_Result),
                       P, C.c_int64, P, C.c_int64, P, C.c_int64, P, C.c_int64]
     if path is None:
         _LIB = lib
@@ -163,8 +163,9 @@ class Result:
 
 def mlbicgstabt(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
                 err_hist: bool = False, x_hist: int = 0, blk_ops: int = 0,
-                trace: bool = False, lib=None) -> Result:
-    """One call of ML(n)BiCGStabt (Algorithm 7.1, M = I) from x0."""
+                trace: bool = False, lib=None, mdiag=None) -> Result:
+    """One call of ML(n)BiCGStabt (Algorithm 7.1) from x0; ``mdiag`` is the
+    diagonal of the preconditioner M (None: M = I)."""
     lib = lib or load()
     cplx = (np.iscomplexobj(A.val) or np.iscomplexobj(b)
             or np.iscomplexobj(Q) or np.iscomplexobj(x0))
@@ -175,6 +176,9 @@ def mlbicgstabt(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
     Qf = np.asfortranarray(Q, dtype=dt)
     b = np.ascontiguousarray(b, dtype=dt)
     x = np.array(x0, dtype=dt, copy=True)
+    md = None if mdiag is None else np.ascontiguousarray(mdiag, dtype=dt)
+    if md is not None and md.shape != (N,):
+        raise ValueError("mdiag must hold N entries")
     cap = int(maxit) + 1
     eh = np.full(cap, np.nan) if err_hist else None
     xh = np.zeros((x_hist, N), dtype=dt) if x_hist else None
@@ -183,7 +187,7 @@ def mlbicgstabt(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
     res = _Result()
     fn = lib.orc_mlbicgstabt_z if cplx else lib.orc_mlbicgstabt_d
     rc = fn(N, _ptr(rp), _ptr(ci), _ptr(av), n, _ptr(Qf), _ptr(b), _ptr(x),
-            int(maxit), float(tol), float(kappa), C.byref(res),
+            int(maxit), float(tol), float(kappa), _ptr(md), C.byref(res),
             _ptr(eh), cap if eh is not None else 0,
             _ptr(xh), x_hist, _ptr(bo), blk_ops,
             _ptr(tr), cap if tr is not None else 0)
@@ -198,6 +202,17 @@ def mlbicgstabt(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
         blk_ops=bo, trace=None if tr is None else tr[:it])
 
 
+def jacobi_diag(A, lib=None):
+    """diag(A) as a vector: the Jacobi preconditioner M = diag(A)
+    (duplicate entries of a row are summed, as in the product A x)."""
+    d = np.zeros(A.n_rows, dtype=A.val.dtype)
+    for r in range(A.n_rows):
+        for k in range(A.row_ptr[r], A.row_ptr[r + 1]):
+            if A.col[k] == r:
+                d[r] += A.val[k]
+    return d
+
+
 def true_relres(A, b, x, lib=None) -> float:
     """||b - A x||_2 / ||b||_2 with ||b|| replaced by 1 when b = 0."""
     r = np.asarray(b) - spmv(A, x, lib=lib)
@@ -206,7 +221,7 @@ def true_relres(A, b, x, lib=None) -> float:
 
 
 def solve(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
-          max_outer: int = 10, lib=None) -> Result:
+          max_outer: int = 10, lib=None, mdiag=None) -> Result:
     """Call ``mlbicgstabt`` again from the current x while its recursive
     residual met ``tol`` but the true residual ||b - A x||/||b|| did not;
     each new call recomputes r = b - A x and returns at once (iter 0) when
@@ -218,7 +233,7 @@ def solve(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
     outer = 0
     res = None
     while True:
-        res = mlbicgstabt(A, b, x, Q, maxit - total, tol, kappa, lib=lib)
+        res = mlbicgstabt(A, b, x, Q, maxit - total, tol, kappa, lib=lib, mdiag=mdiag)
         x = res.x
         total += res.iter
         if res.flag != 0 or res.iter == 0 or total >= maxit:

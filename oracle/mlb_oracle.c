@@ -11,9 +11,10 @@
  *                            r_n(k) = k - n g_n(k)                  (§2, eq. 2.1)
  *   orc_spmv_{d,z}           y = A x, definition of the CSR product
  *   orc_ahq_{d,z}            F = A^H Q(:,1:n-1)            (Algorithm 4.1, step 2)
- *   orc_mlbicgstabt_{d,z}    ML(n)BiCGStabt = Algorithm 7.1 with M = I
- *                            (equivalently Algorithm 4.1), stopping rule and
- *                            flags of §5, omega guard of Eq. 5.1
+ *   orc_mlbicgstabt_{d,z}    ML(n)BiCGStabt = Algorithm 7.1 (M = I, which is
+ *                            Algorithm 4.1, or a diagonal M applied as
+ *                            written), stopping rule and flags of §5, omega
+ *                            guard of Eq. 5.1
  *   orc_qgauss               N(0,1) shadow vectors from the counter-based
  *                            generator the library documents: SplitMix64
  *                            (Steele, Lea & Flood, OOPSLA 2014) evaluated at

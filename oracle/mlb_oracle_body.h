@@ -111,6 +111,13 @@ void SFX(orc_ahq)(int64_t N, const int64_t *rp, const int32_t *ci,
     }
 }
 
+/* dst = M^{-1} src for a diagonal M (elementwise division by mdiag). */
+static void SFX(minv)(int64_t N, const S *mdiag, const S *src, S *dst)
+{
+    for (int64_t t = 0; t < N; ++t)
+        dst[t] = src[t] / mdiag[t];
+}
+
 /*
  * ML(n)BiCGStabt: Algorithm 7.1 of the paper with M = I, which is
  * Algorithm 4.1 with its k-loop split into k = jn + i, 1 <= i <= n, j >= 0
@@ -124,6 +131,15 @@ void SFX(orc_ahq)(int64_t N, const int64_t *rp, const int32_t *ci,
  * and slots i..n-1 still hold block j-1, which is exactly what steps 10-17
  * of Algorithm 7.1 read; slot i is then overwritten in place.
  *
+ * Preconditioning (Algorithm 7.1 with M != I): mdiag, when not NULL, is
+ * the diagonal of M (right preconditioning).  Then, as written in the
+ * algorithm: F = M^{-H} A^H Q (step 2), g^ = M^{-1} g is kept beside every
+ * g (steps 2, 31, 50) and is what x advances along (steps 6, 35) and what
+ * A multiplies (w = A g^); u^ = M^{-1} u (step 37) gives z = A u^ and
+ * x += omega u^ (steps 38-39); the guard of Eq. 5.1 is taken with A u^ in
+ * place of A u.  mdiag == NULL is M = I: no g^ is formed and the
+ * arithmetic is exactly that of Algorithm 4.1.
+ *
  * Inputs: CSR A (N rows), Q (N x n, column-major, ld N), b, x (in: x_0,
  * out: solution).  Optional histories (NULL to skip):
  *   err_hist[k]       relative residual after iteration k (k = 0: initial)
@@ -135,6 +151,7 @@ void SFX(orc_ahq)(int64_t N, const int64_t *rp, const int32_t *ci,
 int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
                          const S *av, int32_t n, const S *Q, const S *b,
                          S *x, int64_t maxit, double tol, double kappa,
+                         const S *mdiag,
                          orc_result *res,
                          double *err_hist, int64_t err_cap,
                          S *x_hist, int64_t x_cap,
@@ -151,8 +168,12 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
     S *r = (S *)calloc((size_t)N, sizeof(S));
     S *z = (S *)calloc((size_t)N, sizeof(S));
     S *c = (S *)calloc((size_t)n, sizeof(S));
-    if (!G || !W || (n > 1 && !F) || !r || !z || !c) {
+    /* g^ slots and u^ (M != I only; with M = I they are G and r) */
+    S *Gh = mdiag ? (S *)calloc((size_t)N * n, sizeof(S)) : G;
+    S *uh = mdiag ? (S *)calloc((size_t)N, sizeof(S)) : r;
+    if (!G || !W || (n > 1 && !F) || !r || !z || !c || !Gh || !uh) {
         free(G); free(W); free(F); free(r); free(z); free(c);
+        if (mdiag) { free(Gh); free(uh); }
         return -2;
     }
 
@@ -189,13 +210,21 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
         goto done;
     }
 
-    /* step 2: [f_1..f_{n-1}] = A^H [q_1..q_{n-1}] */
-    if (n > 1)
+    /* step 2: [f_1..f_{n-1}] = M^{-H} A^H [q_1..q_{n-1}] */
+    if (n > 1) {
         SFX(orc_ahq)(N, rp, ci, av, n - 1, Q, F);
+        if (mdiag)
+            for (int32_t s = 0; s < n - 1; ++s)
+                for (int64_t t = 0; t < N; ++t)
+                    F[(int64_t)s * N + t] = F[(int64_t)s * N + t] / CONJ(mdiag[t]);
+    }
 
-    /* step 2: g_0 = r_0, w_0 = A g_0, c_0 = q_1^H w_0, e_0 = q_1^H r_0 */
+    /* step 2: g_0 = r_0, g^_0 = M^{-1} r_0, w_0 = A g^_0, c_0 = q_1^H w_0,
+     * e_0 = q_1^H r_0 */
     memcpy(G, r, (size_t)N * sizeof(S));
-    SFX(matvec)(N, rp, ci, av, G, W, ops);
+    if (mdiag)
+        SFX(minv)(N, mdiag, G, Gh);
+    SFX(matvec)(N, rp, ci, av, Gh, W, ops);
     c[0] = SFX(dot)(N, Q, W, ops);
     if (c[0] == 0) {
         res->flag = -1;
@@ -211,9 +240,9 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
             S *gi = G + (int64_t)i * N;   /* slot of g_{jn+i} */
             S *wi = W + (int64_t)i * N;   /* slot of w_{jn+i} (z_w) */
 
-            /* steps 5-7 */
+            /* steps 5-7 (x advances along g^) */
             alpha = e / c[i - 1];
-            SFX(axpy)(N, alpha, G + (int64_t)(i - 1) * N, x, ops);
+            SFX(axpy)(N, alpha, Gh + (int64_t)(i - 1) * N, x, ops);
             SFX(axpy)(N, -alpha, W + (int64_t)(i - 1) * N, r, ops);
             err = SFX(nrm2)(N, r, ops) / bnrm2;
             iter++;
@@ -256,8 +285,10 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
                 }
             }
 
-            /* steps 31-32: w = A g, c = q_{i+1}^H w */
-            SFX(matvec)(N, rp, ci, av, gi, wi, ops);
+            /* steps 31-32: g^ = M^{-1} g, w = A g^, c = q_{i+1}^H w */
+            if (mdiag)
+                SFX(minv)(N, mdiag, gi, Gh + (int64_t)i * N);
+            SFX(matvec)(N, rp, ci, av, Gh + (int64_t)i * N, wi, ops);
             c[i] = SFX(dot)(N, Q + (int64_t)i * N, wi, ops);
             if (c[i] == 0) {
                 res->flag = -1;
@@ -268,7 +299,7 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
         /* steps 34-36: alpha, x, u (u is kept in r) */
         i = n;
         alpha = e / c[n - 1];
-        SFX(axpy)(N, alpha, G + (int64_t)(n - 1) * N, x, ops);
+        SFX(axpy)(N, alpha, Gh + (int64_t)(n - 1) * N, x, ops);
         SFX(axpy)(N, -alpha, W + (int64_t)(n - 1) * N, r, ops);
         err = SFX(nrm2)(N, r, ops) / bnrm2;
         if (err < tol) {
@@ -278,8 +309,10 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
             goto done;
         }
 
-        /* step 38: omega = (A u)^H u / ||A u||^2 */
-        SFX(matvec)(N, rp, ci, av, r, z, ops);
+        /* step 37: u^ = M^{-1} u; step 38: omega = (A u^)^H u / ||A u^||^2 */
+        if (mdiag)
+            SFX(minv)(N, mdiag, r, uh);
+        SFX(matvec)(N, rp, ci, av, uh, z, ops);
         S zz = SFX(dot)(N, z, z, ops);
         if (zz == 0) {
             res->flag = -1;
@@ -300,8 +333,8 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
             goto done;
         }
 
-        /* steps 39-40: x += omega u, r = u - omega A u */
-        SFX(axpy)(N, omega, r, x, ops);
+        /* steps 39-40: x += omega u^, r = u - omega A u^ */
+        SFX(axpy)(N, omega, uh, x, ops);
         SFX(axpy)(N, -omega, z, r, ops);
         err = SFX(nrm2)(N, r, ops) / bnrm2;
         iter++;
@@ -326,8 +359,10 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
         }
         /* step 50: g = z_w - g / omega_{j+1} */
         SFX(omega_corr)(N, W, omega, G, ops);
-        /* step 51: w = A g, c = q_1^H w */
-        SFX(matvec)(N, rp, ci, av, G, W, ops);
+        /* step 50 (end): g^ = M^{-1} g; step 51: w = A g^, c = q_1^H w */
+        if (mdiag)
+            SFX(minv)(N, mdiag, G, Gh);
+        SFX(matvec)(N, rp, ci, av, Gh, W, ops);
         c[0] = SFX(dot)(N, Q, W, ops);
         if (c[0] == 0) {
             res->flag = -1;
@@ -342,5 +377,6 @@ done:
     res->j = (int32_t)j;
     res->i = i;
     free(G); free(W); free(F); free(r); free(z); free(c);
+    if (mdiag) { free(Gh); free(uh); }
     return 0;
 }

@@ -50,6 +50,20 @@ MUTANTS = [
     ("gn_truncates", MAIN, "q -= 1;", "q -= 0;"),
     ("j0_branch_wrong_g", BODY, "SFX(xpay)(N, r, beta, G, gi, ops);",
      "SFX(xpay)(N, r, beta, gi, gi, ops);"),
+    # preconditioned path (Algorithm 7.1, M != I)
+    ("precond_x_along_g", BODY,
+     "SFX(axpy)(N, alpha, Gh + (int64_t)(i - 1) * N, x, ops);",
+     "SFX(axpy)(N, alpha, G + (int64_t)(i - 1) * N, x, ops);"),
+    ("precond_w_from_g", BODY,
+     "SFX(matvec)(N, rp, ci, av, Gh + (int64_t)i * N, wi, ops);",
+     "SFX(matvec)(N, rp, ci, av, gi, wi, ops);"),
+    ("precond_F_unscaled", BODY,
+     "F[(int64_t)s * N + t] = F[(int64_t)s * N + t] / CONJ(mdiag[t]);",
+     "F[(int64_t)s * N + t] = F[(int64_t)s * N + t];"),
+    ("precond_omega_step_u", BODY, "SFX(axpy)(N, omega, uh, x, ops);",
+     "SFX(axpy)(N, omega, r, x, ops);"),
+    ("precond_minv_multiplies", BODY, "dst[t] = src[t] / mdiag[t];",
+     "dst[t] = src[t] * mdiag[t];"),
 ]
 
 # fast pins, in the order they are tried
@@ -67,6 +81,8 @@ PINS = [
     lambda o: P.test_block0_biorthogonality(o, True),
     lambda o: P.test_table_4_3_operation_counts_per_block(o, 4),
     lambda o: P.test_cd2d_agrees_with_dense_lu(o, 4),
+    lambda o: P.test_precond_equals_method_on_right_scaled_system(o, False),
+    lambda o: P.test_precond_finite_termination(o, 8, 3),
 ]
 
 

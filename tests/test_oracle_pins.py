@@ -338,3 +338,96 @@ def test_restart_wrapper_reaches_true_residual(orc):
     Q = orc.q_gauss(0, A.n_rows, 4)
     res = orc.solve(A, b, np.zeros(A.n_rows), Q, 2000, 1e-10)
     assert res.flag == 0 and res.true_relres < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Preconditioning: Algorithm 7.1 with a diagonal M (Jacobi, M = diag(A))
+# ---------------------------------------------------------------------------
+
+def _col_scaled(A, s):
+    """A diag(s) (column j of A multiplied by s_j)."""
+    return W.CSR(row_ptr=A.row_ptr.copy(), col=A.col.copy(), val=A.val * s[A.col], n_rows=A.n_rows)
+
+
+def test_precond_identity_is_unpreconditioned(orc):
+    """M = I given explicitly is Algorithm 4.1: division by 1 is exact, so
+    every iterate is the same bits as the M = I path."""
+    A, _, b = W.random_dense_system(40, seed=41)
+    Q = np.random.default_rng(42).standard_normal((40, 4))
+    x0 = np.zeros(40)
+    r0 = orc.mlbicgstabt(A, b, x0, Q, maxit=25, tol=0.0, err_hist=True, x_hist=25)
+    r1 = orc.mlbicgstabt(A, b, x0, Q, maxit=25, tol=0.0, err_hist=True, x_hist=25, mdiag=np.ones(40))
+    np.testing.assert_array_equal(r0.err_hist, r1.err_hist)
+    np.testing.assert_array_equal(r0.x_hist, r1.x_hist)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_precond_equals_method_on_right_scaled_system(orc, cplx):
+    """Algorithm 7.1 with right preconditioner M solves A M^{-1} y = b with
+    x = M^{-1} y: its residuals r = b - A x are those of the M = I method on
+    A' = A M^{-1} (F = M^{-H} A^H Q = A'^H Q).  In exact arithmetic the two
+    residual sequences coincide; in FP64 they agree to rounding on a
+    well-conditioned system, and x_k = M^{-1} y_k."""
+    N, n = 36, 4
+    A, _, b = W.random_dense_system(N, seed=43, complex_=cplx)
+    rng = np.random.default_rng(44)
+    # a positive (or nearly real) M keeps A M^{-1} as well conditioned as A,
+    # so the two FP64 sequences stay within rounding of each other
+    d = rng.uniform(0.5, 2.0, N)
+    if cplx:
+        d = d * np.exp(1j * rng.uniform(-0.3, 0.3, N))
+    Q = rng.standard_normal((N, n)) + (1j * rng.standard_normal((N, n)) if cplx else 0)
+    x0 = np.zeros(N, dtype=b.dtype)
+    K = 20
+    rp = orc.mlbicgstabt(A, b, x0, Q, maxit=K, tol=0.0, err_hist=True, x_hist=K, mdiag=d)
+    Ap = _col_scaled(A, 1.0 / d)
+    ry = orc.mlbicgstabt(Ap, b, x0, Q, maxit=K, tol=0.0, err_hist=True, x_hist=K)
+    np.testing.assert_allclose(rp.err_hist, ry.err_hist, rtol=1e-7)
+    for k in range(K):
+        xk = ry.x_hist[k] / d
+        assert np.linalg.norm(rp.x_hist[k] - xk) <= 1e-7 * np.linalg.norm(xk), k
+
+
+def test_jacobi_undoes_column_scaling(orc):
+    """With M = diag(A), right preconditioning makes the method invariant to
+    a column scaling A -> A S (S diagonal): A S (diag(A) S)^{-1} =
+    A diag(A)^{-1}.  So the residual history on A S equals the one on A (to
+    rounding) and the solution is S^{-1} times A's, whatever S is; without
+    preconditioning the scaled system behaves differently."""
+    A = W.cd2d(16)
+    b = W.row_sums(A)
+    N = A.n_rows
+    s = 10.0 ** np.random.default_rng(45).uniform(-2, 2, N)
+    AS = _col_scaled(A, s)
+    Q = orc.q_gauss(0, N, 4)
+    x0 = np.zeros(N)
+    r1 = orc.mlbicgstabt(A, b, x0, Q, maxit=400, tol=1e-10, err_hist=True, mdiag=orc.jacobi_diag(A))
+    r2 = orc.mlbicgstabt(AS, b, x0, Q, maxit=400, tol=1e-10, err_hist=True, mdiag=orc.jacobi_diag(AS))
+    assert r1.flag == 0 and r2.flag == 0
+    assert abs(r1.iter - r2.iter) <= 2
+    k = min(r1.iter, r2.iter, 30)
+    np.testing.assert_allclose(r1.err_hist[:k], r2.err_hist[:k], rtol=1e-6)
+    np.testing.assert_allclose(r2.x * s, r1.x, rtol=1e-7, atol=1e-9)
+    r3 = orc.mlbicgstabt(AS, b, x0, Q, maxit=30, tol=0.0, err_hist=True)
+    assert np.max(np.abs(r3.err_hist[1:31] / r2.err_hist[1:31] - 1.0)) > 1e-3
+
+
+@pytest.mark.parametrize("N,n", [(8, 3), (9, 9)])
+def test_precond_finite_termination(orc, N, n):
+    """A M^{-1} is still an N x N system, so the preconditioned method also
+    stops by step N in exact arithmetic; it must converge by iteration N at
+    tol 1e-14 and agree with LAPACK on A x = b."""
+    A, M, b = W.random_dense_system(N, seed=200 + N + n)
+    d = np.random.default_rng(N).uniform(0.5, 3.0, N)
+    Q = np.random.default_rng(N + 1).standard_normal((N, n))
+    res = orc.mlbicgstabt(A, b, np.zeros(N), Q, maxit=4 * N, tol=1e-14, mdiag=d)
+    assert res.flag == 0 and res.iter <= N
+    xs = np.linalg.solve(M, b)
+    assert np.linalg.norm(res.x - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_jacobi_diag_definition(orc):
+    """jacobi_diag sums a row's diagonal entries (duplicates included)."""
+    A = W.CSR(row_ptr=np.array([0, 2, 4, 5], dtype=np.int64), col=np.array([0, 0, 0, 2, 2], dtype=np.int32),
+              val=np.array([1.0, 2.0, -3.0, 5.0, 7.0]), n_rows=3)
+    np.testing.assert_array_equal(orc.jacobi_diag(A), [3.0, 0.0, 7.0])
