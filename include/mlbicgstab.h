@@ -52,6 +52,10 @@ extern "C" {
 #define MLB_C128 2  /* complex double, interleaved (re, im) */
 
 /* ---- precision modes --------------------------------------------------- */
+/* Preconditioner M of Algorithm 7.1 (right preconditioning). */
+#define MLB_PRECOND_NONE 0   /* M = I: Algorithm 4.1 */
+#define MLB_PRECOND_JACOBI 1 /* M = diag(A) (every diagonal entry nonzero) */
+
 #define MLB_PREC_FP64 0     /* matrix, vectors and arithmetic in FP64 */
 #define MLB_PREC_FP32_REFINED 1 /* inner ML(n)BiCGStab in FP32 (values,
                                    vectors, accumulation) inside an FP64
@@ -99,6 +103,16 @@ typedef struct {
                              NULL = the legacy default stream */
     int64_t timeout_ns;   /* limit of every device-side wait (grid barrier
                              spin); default 2e9 (2 s) */
+    int32_t precond;      /* MLB_PRECOND_NONE (default) or MLB_PRECOND_JACOBI:
+                             Algorithm 7.1 with M = diag(A).  The handle
+                             stores A M^{-1} (columns divided by the
+                             diagonal), F = M^{-H} A^H Q (step 2), and each
+                             solve maps x_0 to y_0 = M x_0 and the result
+                             back to x = M^{-1} y, which is the algorithm's
+                             x-recurrence along g^ = M^{-1} g (steps 6, 35,
+                             39).  Stopping rule and residuals are those of
+                             A x = b. */
+    int32_t reserved0;    /* must be 0 */
 } mlb_options;
 
 /* Result of one solve.  flag/iter/err follow the paper's reference code
@@ -128,10 +142,20 @@ typedef struct {
 typedef struct {
     int64_t nrows, nnz;
     int32_t n, dtype, precision, grid, block;
-    int32_t reserved;
+    int32_t precond;      /* MLB_PRECOND_* of the handle */
     int64_t nnz_padded;   /* stored SELL-32 entries (>= nnz) */
     int64_t device_bytes; /* device memory held by the handle */
+    int32_t n_active;     /* shadow vectors the next solve uses (<= n) */
+    int32_t reserved1;
 } mlb_info;
+
+/* Parameters of mlbicgstab_solve_sequence (automatic choice of n, §5). */
+typedef struct {
+    int32_t n0;           /* n for the first two systems */
+    int32_t step;         /* search step of n (>= 0) */
+    int32_t n_min;        /* n stays in [n_min, n_max]; n_min >= 1 and */
+    int32_t n_max;        /* n_max <= the n every handle was created with */
+} mlb_sequence_options;
 
 typedef struct mlb_handle mlb_handle;
 
@@ -153,7 +177,7 @@ int mlbicgstab_create(mlb_handle **h, const mlb_matrix *A,
                       const mlb_matrix *AH, const mlb_options *opt);
 
 /*
- * Solve A x = b (Algorithm 7.1 with M = I, stopping rule of §5: stop when
+ * Solve A x = b (Algorithm 7.1, M as chosen at create; stopping rule of §5: stop when
  * ||r_k||/||b|| < tol after any update of r or u; at most `maxit` k-steps
  * in total).  The whole iteration runs in one persistent kernel: the
  * convergence and breakdown tests are taken on the device.
@@ -188,6 +212,41 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count,
                            const int64_t *maxit, mlb_result *res);
 
 /*
+ * Use the first n shadow vectors in the solves that follow
+ * (1 <= n <= the n the handle was created with; MLB_ERR_ARG otherwise).
+ * The handle's Q(:,1:n) and F(:,1:n-1) = A^H Q(:,1:n-1) are exactly the
+ * Q and F of a handle created with this n (entries of the drawn Q depend
+ * only on their row and column), so nothing is recomputed.
+ */
+int mlbicgstab_set_n(mlb_handle *h, int32_t n);
+
+/*
+ * The rule for choosing n in a sequence of systems (§5, "Choice of n":
+ * Code #4 of the author's earlier work): with t_prev and t_cur the times of
+ * the previous and the current solve, the next system uses n + step when
+ * t_prev > t_cur and n - step otherwise, clamped to [n_min, n_max].
+ * Returns the next n (or -1 when the arguments are invalid).
+ */
+int32_t mlbicgstab_next_n(int32_t n, double t_prev, double t_cur, int32_t step,
+                          int32_t n_min, int32_t n_max);
+
+/*
+ * Solve a sequence of `count` systems one after another (system s with
+ * handle hs[s]; a handle may repeat, e.g. one matrix with many right-hand
+ * sides), choosing n by mlbicgstab_next_n: systems 0 and 1 use so->n0,
+ * system s+1 (s >= 1) uses next_n(n_s, t_{s-1}, t_s), t being the device
+ * time of each solve (mlb_result.kernel_ms).  Arguments as in
+ * mlbicgstab_solve; n_used[s] receives the n of system s.  Every handle
+ * is returned to the n it had before the call.  Stops at the first error.
+ */
+int mlbicgstab_solve_sequence(mlb_handle *const *hs, int32_t count,
+                              const void *const *b, void *const *x,
+                              int32_t on_device, const double *tol,
+                              const int64_t *maxit,
+                              const mlb_sequence_options *so,
+                              mlb_result *res, int32_t *n_used);
+
+/*
  * Fused hot operation: y = A x and d = Q^H y (all n shadow inner products,
  * a tall-skinny block reduction) in one pass over A — the per-iteration
  * product w = A g with c = q^H w of Algorithm 4.1 (step 32) generalised to
@@ -195,6 +254,8 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count,
  * Reductions are deterministic (fixed order).  Blocks until d is ready.
  */
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d);
+/* (MLB_ERR_UNSUPPORTED for a handle with a preconditioner: it stores
+ * A M^{-1}, not A.) */
 
 /*
  * Allocation-free variant of mlbicgstab_spmv_qdot: y = A x and d = Q^H y

@@ -1,6 +1,9 @@
 // C ABI of the ML(n)BiCGStab library: argument validation, device state of
 // a handle, and the host side of every entry point.
 #include <algorithm>
+#include <cmath>
+#include <complex>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -14,7 +17,10 @@ using namespace mlb;
 
 struct mlb_handle {
     int dtype = MLB_F64;
-    int n = 4;
+    int n = 4;          // shadow vectors Q and F were built for
+    int n_active = 4;   // shadow vectors the next solve uses (<= n)
+    int precond = MLB_PRECOND_NONE;
+    void *mdiag = nullptr;   // diagonal of M (Jacobi), device, N values
     int precision = MLB_PREC_FP64;
     int64_t N = 0, ld = 0, nnz = 0, nnz_pad = 0, nslices = 0;
     int64_t maxw = 0;   // widest SELL-32 slice (entries per row)
@@ -204,7 +210,7 @@ SysView<T> make_view(const mlb_handle *h) {
     v.r = (T *)h->r;
     v.z = (T *)h->z;
     v.b = (T *)h->b;
-    v.n = h->n;
+    v.n = h->n_active;
     return v;
 }
 
@@ -227,7 +233,7 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.r = (T32 *)h->r32;
     v.z = (T32 *)h->z32;
     v.b = (T32 *)h->b32;
-    v.n = h->n;
+    v.n = h->n_active;
     return v;
 }
 
@@ -257,11 +263,77 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// With a preconditioner the kernels iterate on y = M x (A M^{-1} y = b):
+// before a solve the caller's x_0 becomes y_0 = M x_0, afterwards the
+// result y becomes x = M^{-1} y, on the handle's buffer h->x.
+int map_solution(mlb_handle *h, bool to_x, cudaStream_t st) {
+    if (h->precond == MLB_PRECOND_NONE) return MLB_OK;
+    cudaError_t e = h->dtype == MLB_C128
+                        ? launch_diag_apply<cdouble>((cdouble *)h->x, (const cdouble *)h->mdiag, h->N, to_x, st)
+                        : launch_diag_apply<double>((double *)h->x, (const double *)h->mdiag, h->N, to_x, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    return MLB_OK;
+}
+int map_solution(mlb_handle *h, bool to_x) { return map_solution(h, to_x, h->stream); }
+
+// Jacobi preconditioner M = diag(A) (Algorithm 7.1, right preconditioning):
+// d = diagonal of A (a row's diagonal entries summed), values of A M^{-1}
+// (column j divided by d_j) and, when A^H is supplied, of M^{-H} A^H (row i
+// divided by conj(d_i)).  MLB_ERR_ARG when some d_i is zero or not finite.
+template <typename V>
+int jacobi_scale_t(const mlb_matrix *A, const mlb_matrix *AH, std::vector<char> &dg, std::vector<char> &av,
+                   std::vector<char> &ahv) {
+    const int64_t N = A->nrows;
+    std::vector<V> d(N, V(0));
+    const V *a = (const V *)A->values;
+    for (int64_t r = 0; r < N; ++r)
+        for (int64_t k = A->row_ptr[r]; k < A->row_ptr[r + 1]; ++k)
+            if (A->col_idx[k] == r) d[r] += a[k];
+    for (int64_t r = 0; r < N; ++r)
+        if (!(std::abs(d[r]) > 0.0) || !std::isfinite(std::abs(d[r]))) return MLB_ERR_ARG;
+    dg.assign((const char *)d.data(), (const char *)(d.data() + N));
+    av.resize((size_t)A->nnz * sizeof(V));
+    V *o = (V *)av.data();
+    for (int64_t k = 0; k < A->nnz; ++k) o[k] = a[k] / d[A->col_idx[k]];
+    if (AH) {
+        ahv.resize((size_t)AH->nnz * sizeof(V));
+        const V *ah = (const V *)AH->values;
+        V *oh = (V *)ahv.data();
+        for (int64_t r = 0; r < N; ++r)
+            for (int64_t k = AH->row_ptr[r]; k < AH->row_ptr[r + 1]; ++k) {
+                if constexpr (std::is_same<V, double>::value) oh[k] = ah[k] / d[r];
+                else oh[k] = ah[k] / std::conj(d[r]);
+            }
+    }
+    return MLB_OK;
+}
+
 int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const mlb_options *o) {
     MLB_CUDA(cudaGetDevice(&h->device));
     h->dtype = A->dtype;
     h->esize = A->dtype == MLB_C128 ? 16 : 8;
     h->n = o->n;
+    h->n_active = o->n;
+    h->precond = o->precond;
+    // with a preconditioner the handle stores A M^{-1} (and M^{-H} A^H)
+    std::vector<char> jd, jav, jahv;
+    mlb_matrix As, AHs;
+    if (o->precond == MLB_PRECOND_JACOBI) {
+        const int rcj = A->dtype == MLB_C128 ? jacobi_scale_t<std::complex<double>>(A, AH, jd, jav, jahv)
+                                             : jacobi_scale_t<double>(A, AH, jd, jav, jahv);
+        if (rcj) return rcj;
+        As = *A;
+        As.values = jav.data();
+        A = &As;
+        if (AH) {
+            AHs = *AH;
+            AHs.values = jahv.data();
+            AH = &AHs;
+        }
+    }
     h->precision = o->precision;
     h->N = A->nrows;
     h->nnz = A->nnz;
@@ -316,6 +388,10 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     MLB_CUDA(cudaMemsetAsync(h->x, 0, vb, st));
     MLB_CUDA(cudaMemsetAsync(h->r, 0, vb, st));
     MLB_CUDA(cudaMemsetAsync(h->b, 0, vb, st));
+    if (h->precond == MLB_PRECOND_JACOBI) {
+        if ((rc = dev_alloc(h, &h->mdiag, vb))) return rc;
+        MLB_CUDA(cudaMemcpy(h->mdiag, jd.data(), (size_t)h->N * es, cudaMemcpyHostToDevice));
+    }
 
     // shadow vectors
     if (o->Q) {
@@ -483,6 +559,7 @@ int mlbicgstab_create(mlb_handle **out, const mlb_matrix *A, const mlb_matrix *A
     if (o.n < 1 || o.n > kMaxN) return MLB_ERR_ARG;
     if (o.precision != MLB_PREC_FP64 && o.precision != MLB_PREC_FP32_REFINED) return MLB_ERR_ARG;
     if (o.kappa < 0.0 || o.max_outer < 0 || o.timeout_ns <= 0) return MLB_ERR_ARG;
+    if ((o.precond != MLB_PRECOND_NONE && o.precond != MLB_PRECOND_JACOBI) || o.reserved0 != 0) return MLB_ERR_ARG;
     int rc = validate_csr(A);
     if (rc) return rc;
     if (AH) {
@@ -521,6 +598,8 @@ int mlbicgstab_info(const mlb_handle *h, mlb_info *info) {
     info->nrows = h->N;
     info->nnz = h->nnz;
     info->n = h->n;
+    info->n_active = h->n_active;
+    info->precond = h->precond;
     info->dtype = h->dtype;
     info->precision = h->precision;
     info->grid = h->grid;
@@ -562,6 +641,7 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     }
     MLB_CUDA(cudaMemcpyAsync(h->b, b, nb, in, st));
     MLB_CUDA(cudaMemcpyAsync(h->x, x, nb, in, st));
+    if (int rcm = map_solution(h, false)) return rcm;   // y_0 = M x_0
     MLB_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(BarrierState), st));
     SolveCtl ctl;
     ctl.tol = tol;
@@ -595,6 +675,7 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
         return MLB_ERR_CUDA;
     }
     MLB_CUDA(cudaEventRecord(h->ev1, st));
+    if (int rcm = map_solution(h, true)) return rcm;    // x = M^{-1} y
     MLB_CUDA(cudaMemcpyAsync(x, h->x, nb, outk, st));
     MLB_CUDA(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
     MLB_CUDA(cudaStreamSynchronize(st));
@@ -712,6 +793,7 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
         const size_t nb = (size_t)hs[s]->N * hs[s]->esize;
         MLB_CUDA(cudaMemcpyAsync(hs[s]->b, b[s], nb, in, st));
         MLB_CUDA(cudaMemcpyAsync(hs[s]->x, x[s], nb, in, st));
+        if (int rcm = map_solution(hs[s], false, st)) return rcm;
     }
     MLB_CUDA(cudaMemcpyAsync(dws, hws, off_res, cudaMemcpyHostToDevice, st));
     int sms = 0;
@@ -744,6 +826,7 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
     MLB_CUDA(cudaEventRecord(h0->ev1, st));
     for (int s = 0; s < count; ++s) {
         const size_t nb = (size_t)hs[s]->N * hs[s]->esize;
+        if (int rcm = map_solution(hs[s], true, st)) return rcm;
         MLB_CUDA(cudaMemcpyAsync(x[s], hs[s]->x, nb, outk, st));
     }
     DevResult *hres = (DevResult *)(hws + off_res);
@@ -771,8 +854,54 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
     return rc;
 }
 
+int mlbicgstab_set_n(mlb_handle *h, int32_t n) {
+    if (!h || n < 1 || n > h->n) return MLB_ERR_ARG;
+    h->n_active = n;
+    return MLB_OK;
+}
+
+int32_t mlbicgstab_next_n(int32_t n, double t_prev, double t_cur, int32_t step, int32_t n_min, int32_t n_max) {
+    if (step < 0 || n_min < 1 || n_max < n_min || n < n_min || n > n_max) return -1;
+    int64_t m = t_prev > t_cur ? (int64_t)n + step : (int64_t)n - step;
+    if (m < n_min) m = n_min;
+    if (m > n_max) m = n_max;
+    return (int32_t)m;
+}
+
+int mlbicgstab_solve_sequence(mlb_handle *const *hs, int32_t count, const void *const *b, void *const *x,
+                              int32_t on_device, const double *tol, const int64_t *maxit,
+                              const mlb_sequence_options *so, mlb_result *res, int32_t *n_used) {
+    if (!hs || count <= 0 || !b || !x || !tol || !maxit || !so || !res || !n_used) return MLB_ERR_ARG;
+    if (so->step < 0 || so->n_min < 1 || so->n_max < so->n_min || so->n0 < so->n_min || so->n0 > so->n_max)
+        return MLB_ERR_ARG;
+    for (int32_t s = 0; s < count; ++s)
+        if (!hs[s] || hs[s]->n < so->n_max) return MLB_ERR_ARG;
+    // every handle gets its n back at the end
+    std::vector<std::pair<mlb_handle *, int>> saved;
+    for (int32_t s = 0; s < count; ++s) {
+        bool seen = false;
+        for (auto &p : saved) seen = seen || p.first == hs[s];
+        if (!seen) saved.push_back({hs[s], hs[s]->n_active});
+    }
+    int rc = MLB_OK;
+    int32_t n = so->n0;
+    double t_prev = 0.0;
+    for (int32_t s = 0; s < count; ++s) {
+        hs[s]->n_active = n;
+        n_used[s] = n;
+        rc = mlbicgstab_solve(hs[s], b[s], x[s], on_device, tol[s], maxit[s], &res[s], nullptr, 0);
+        if (rc != MLB_OK) break;
+        const double t = res[s].kernel_ms;
+        if (s >= 1) n = mlbicgstab_next_n(n, t_prev, t, so->step, so->n_min, so->n_max);
+        t_prev = t;
+    }
+    for (auto &p : saved) p.first->n_active = p.second;
+    return rc;
+}
+
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
     if (!h || !x || !y || !d) return MLB_ERR_ARG;
+    if (h->precond != MLB_PRECOND_NONE) return MLB_ERR_UNSUPPORTED;
     MLB_CUDA(cudaSetDevice(h->device));
     if (!is_device_ptr(x) || !is_device_ptr(y)) return MLB_ERR_ARG;
     cudaStream_t st = h->stream;

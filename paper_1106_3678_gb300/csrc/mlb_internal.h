@@ -28,6 +28,11 @@ int refine_blocks_per_sm();
 // dst[i] = (float)src[i] for `count` doubles.
 cudaError_t launch_narrow(const double *src, float *dst, int64_t count, cudaStream_t st);
 
+// x[i] = x[i] * d[i] (divide = false) or x[i] / d[i] (divide = true), i < n:
+// the map between x and y = M x of a diagonal (Jacobi) preconditioner.
+template <typename T>
+cudaError_t launch_diag_apply(T *x, const T *d, int64_t n, bool divide, cudaStream_t st);
+
 // One system of a batch (device copy of its views and controls).
 template <typename T>
 struct BatchItem {

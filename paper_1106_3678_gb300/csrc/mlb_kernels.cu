@@ -530,6 +530,22 @@ cudaError_t launch_barrier_selftest(int grid, BarrierState *bs, uint64_t timeout
 // ===========================================================================
 // explicit instantiations
 // ===========================================================================
+// Elementwise map of a diagonal preconditioner (see launch_diag_apply).
+template <typename T>
+__global__ void diag_apply_kernel(T *x, const T *d, int64_t n, int divide) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = divide ? x[i] / d[i] : x[i] * d[i];
+}
+
+template <typename T>
+cudaError_t launch_diag_apply(T *x, const T *d, int64_t n, bool divide, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256;
+    const int grid = (int)std::min<int64_t>(want, 152 * 16);
+    diag_apply_kernel<T><<<grid, 256, 0, st>>>(x, d, n, divide ? 1 : 0);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_solve<double>(const SysView<double> &, const SolveCtl &, int, cudaStream_t);
 template cudaError_t launch_solve<cdouble>(const SysView<cdouble> &, const SolveCtl &, int, cudaStream_t);
 template int solve_blocks_per_sm<double>();
@@ -562,5 +578,8 @@ template int batch_blocks_per_sm<double>();
 template int batch_blocks_per_sm<cdouble>();
 template int batch_refine_blocks_per_sm<float, double>();
 template int batch_refine_blocks_per_sm<cfloat, cdouble>();
+
+template cudaError_t launch_diag_apply<double>(double *, const double *, int64_t, bool, cudaStream_t);
+template cudaError_t launch_diag_apply<cdouble>(cdouble *, const cdouble *, int64_t, bool, cudaStream_t);
 
 }  // namespace mlb

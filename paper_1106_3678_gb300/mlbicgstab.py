@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmlbicgstab.so")
 MLB_OK, MLB_ERR_ARG, MLB_ERR_CUDA, MLB_ERR_OOM, MLB_ERR_TIMEOUT, MLB_ERR_UNSUPPORTED = range(6)
 MLB_F64, MLB_C128 = 0, 2
 MLB_PREC_FP64, MLB_PREC_FP32_REFINED = 0, 1
+MLB_PRECOND_NONE, MLB_PRECOND_JACOBI = 0, 1
 
 # Every symbol the header declares (checked against the header by a test).
 EXPORTS = (
@@ -27,6 +28,7 @@ EXPORTS = (
     "mlbicgstab_solve_batch", "mlbicgstab_spmv_qdot", "mlbicgstab_get_Q",
     "mlbicgstab_info", "mlbicgstab_destroy", "mlbicgstab_strerror",
     "mlbicgstab_selftest_barrier_timeout", "mlbicgstab_spmv_qdot_noalloc",
+    "mlbicgstab_set_n", "mlbicgstab_next_n", "mlbicgstab_solve_sequence",
 )
 
 
@@ -43,7 +45,8 @@ class mlb_options(C.Structure):
                 ("kappa", C.c_double), ("max_outer", C.c_int32),
                 ("grid", C.c_int32), ("inner_tol", C.c_double),
                 ("inner_maxit", C.c_int64), ("stream", C.c_void_p),
-                ("timeout_ns", C.c_int64)]
+                ("timeout_ns", C.c_int64), ("precond", C.c_int32),
+                ("reserved0", C.c_int32)]
 
 
 class mlb_result(C.Structure):
@@ -65,8 +68,14 @@ class mlb_info(C.Structure):
     _fields_ = [("nrows", C.c_int64), ("nnz", C.c_int64), ("n", C.c_int32),
                 ("dtype", C.c_int32), ("precision", C.c_int32),
                 ("grid", C.c_int32), ("block", C.c_int32),
-                ("reserved", C.c_int32), ("nnz_padded", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("precond", C.c_int32), ("nnz_padded", C.c_int64),
+                ("device_bytes", C.c_int64), ("n_active", C.c_int32),
+                ("reserved1", C.c_int32)]
+
+
+class mlb_sequence_options(C.Structure):
+    _fields_ = [("n0", C.c_int32), ("step", C.c_int32), ("n_min", C.c_int32),
+                ("n_max", C.c_int32)]
 
 
 class MlbError(RuntimeError):
@@ -113,6 +122,15 @@ def load(path: str | None = None):
     lib.mlbicgstab_strerror.argtypes = [C.c_int]
     lib.mlbicgstab_selftest_barrier_timeout.restype = C.c_int
     lib.mlbicgstab_selftest_barrier_timeout.argtypes = [C.c_int32, C.c_int64]
+    lib.mlbicgstab_set_n.restype = C.c_int
+    lib.mlbicgstab_set_n.argtypes = [P, C.c_int32]
+    lib.mlbicgstab_next_n.restype = C.c_int32
+    lib.mlbicgstab_next_n.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int32,
+                                      C.c_int32, C.c_int32]
+    lib.mlbicgstab_solve_sequence.restype = C.c_int
+    lib.mlbicgstab_solve_sequence.argtypes = [P, C.c_int32, P, P, C.c_int32, P, P,
+                                              C.POINTER(mlb_sequence_options),
+                                              C.POINTER(mlb_result), P]
     lib.mlbicgstab_spmv_qdot_noalloc.restype = C.c_int
     lib.mlbicgstab_spmv_qdot_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, C.c_int32,
                                                  P, P, C.c_int64, C.c_int32, P, P, P]
@@ -204,7 +222,8 @@ def mlbicgstab_create(A, AH=None, n: int = 4, q_seed: int = 0, Q=None,
                       max_outer: int | None = None, grid: int = 0,
                       inner_tol: float | None = None,
                       inner_maxit: int | None = None, stream=None,
-                      timeout_ns: int | None = None) -> Handle:
+                      timeout_ns: int | None = None,
+                      precond: int = MLB_PRECOND_NONE) -> Handle:
     """Create a solver for CSR matrix ``A`` (see mlbicgstab_create in C).
     ``stream``: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
     lib = load()
@@ -216,6 +235,7 @@ def mlbicgstab_create(A, AH=None, n: int = 4, q_seed: int = 0, Q=None,
     o.q_seed = q_seed
     o.kappa = kappa
     o.grid = grid
+    o.precond = precond
     if max_outer is not None:
         o.max_outer = max_outer
     if inner_tol is not None:
@@ -278,6 +298,40 @@ def mlbicgstab_solve_batch(hs, bs, xs, tols, maxits):
                                        t.ctypes.data, m.ctypes.data, res)
     _check(rc, "mlbicgstab_solve_batch")
     return list(res)
+
+
+def mlbicgstab_set_n(h: Handle, n: int) -> None:
+    """Use the first n shadow vectors in later solves (n <= created n)."""
+    _check(load().mlbicgstab_set_n(h.ptr, int(n)), "mlbicgstab_set_n")
+
+
+def mlbicgstab_next_n(n: int, t_prev: float, t_cur: float, step: int, n_min: int, n_max: int) -> int:
+    """The paper's rule for the next n in a sequence of systems (§5)."""
+    return int(load().mlbicgstab_next_n(int(n), float(t_prev), float(t_cur), int(step),
+                                        int(n_min), int(n_max)))
+
+
+def mlbicgstab_solve_sequence(hs, bs, xs, tols, maxits, n0: int, step: int, n_min: int, n_max: int):
+    """Solve systems one after another with n chosen automatically;
+    returns (list of mlb_result, list of the n each system used)."""
+    count = len(hs)
+    ptrs = (C.c_void_p * count)(*[h.ptr.value for h in hs])
+    pb = [_ptr(b) for b in bs]
+    px = [_ptr(x) for x in xs]
+    on_dev = pb[0][1]
+    if any(p[1] != on_dev for p in pb + px):
+        raise ValueError("all b and x must be host arrays, or all device arrays")
+    bp = (C.c_void_p * count)(*[p[0].value for p in pb])
+    xp = (C.c_void_p * count)(*[p[0].value for p in px])
+    t = np.ascontiguousarray(tols, dtype=np.float64)
+    m = np.ascontiguousarray(maxits, dtype=np.int64)
+    so = mlb_sequence_options(int(n0), int(step), int(n_min), int(n_max))
+    res = (mlb_result * count)()
+    used = np.zeros(count, dtype=np.int32)
+    rc = load().mlbicgstab_solve_sequence(ptrs, count, bp, xp, on_dev, t.ctypes.data, m.ctypes.data,
+                                          C.byref(so), res, used.ctypes.data)
+    _check(rc, "mlbicgstab_solve_sequence")
+    return list(res), [int(v) for v in used]
 
 
 def mlbicgstab_spmv_qdot(h: Handle, x, y) -> np.ndarray:

@@ -50,10 +50,12 @@ def test_struct_layout_matches_c_compiler(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu\\n", sizeof(mlb_matrix), sizeof(mlb_options),
-         sizeof(mlb_result), sizeof(mlb_info));
-  printf("%zu %zu %zu\\n", offsetof(mlb_options, stream),
-         offsetof(mlb_options, timeout_ns), offsetof(mlb_result, ops));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(mlb_matrix), sizeof(mlb_options),
+         sizeof(mlb_result), sizeof(mlb_info), sizeof(mlb_sequence_options));
+  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(mlb_options, stream),
+         offsetof(mlb_options, timeout_ns), offsetof(mlb_result, ops),
+         offsetof(mlb_options, precond), offsetof(mlb_info, precond),
+         offsetof(mlb_info, n_active));
   return 0;
 }}''')
     exe = tmp_path / "layout"
@@ -62,10 +64,11 @@ int main(void) {{
                                  text=True).stdout.split("\n")[:2]
     assert [int(v) for v in sizes.split()] == [
         C.sizeof(M.mlb_matrix), C.sizeof(M.mlb_options),
-        C.sizeof(M.mlb_result), C.sizeof(M.mlb_info)]
+        C.sizeof(M.mlb_result), C.sizeof(M.mlb_info), C.sizeof(M.mlb_sequence_options)]
     assert [int(v) for v in offs.split()] == [
         M.mlb_options.stream.offset, M.mlb_options.timeout_ns.offset,
-        M.mlb_result.ops.offset]
+        M.mlb_result.ops.offset, M.mlb_options.precond.offset,
+        M.mlb_info.precond.offset, M.mlb_info.n_active.offset]
 
 
 def test_strerror_and_defaults(lib):
@@ -96,6 +99,8 @@ def test_invalid_arguments_are_rejected_before_gpu_work(lib):
     assert _raw_create(lib, A, n=65)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, kappa=-1.0)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, precision=7)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, precond=5)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, reserved0=1)[0] == M.MLB_ERR_ARG
     bad = W.CSR(A.row_ptr.copy(), A.col.copy(), A.val.copy(), A.n_rows)
     bad.col[3] = A.n_rows          # column out of range
     assert _raw_create(lib, bad)[0] == M.MLB_ERR_ARG
@@ -129,3 +134,42 @@ def test_binding_refuses_to_run_without_library(tmp_path):
         M.load(str(tmp_path / "missing.so"))
     x = np.zeros(3)
     assert M._ptr(x)[1] == 0
+
+
+def test_next_n_rule_of_section_5(lib):
+    """§5 ("Choice of n"): a faster current solve (t_prev > t_cur) moves n
+    up by `step`, otherwise down, clamped to [n_min, n_max]; invalid
+    arguments give -1.  A host function: no device involved."""
+    nn = M.mlbicgstab_next_n
+    assert nn(4, 2.0, 1.0, 2, 1, 16) == 6      # faster -> increase
+    assert nn(4, 1.0, 2.0, 2, 1, 16) == 2      # slower -> decrease
+    assert nn(4, 1.0, 1.0, 2, 1, 16) == 2      # equal counts as "otherwise"
+    assert nn(15, 2.0, 1.0, 4, 1, 16) == 16    # clamped above
+    assert nn(2, 1.0, 2.0, 4, 1, 16) == 1      # clamped below
+    assert nn(4, 2.0, 1.0, 0, 1, 16) == 4      # step 0 keeps n
+    assert nn(4, 2.0, 1.0, -1, 1, 16) == -1
+    assert nn(0, 2.0, 1.0, 1, 1, 16) == -1
+    assert nn(20, 2.0, 1.0, 1, 1, 16) == -1
+    assert nn(4, 2.0, 1.0, 1, 5, 3) == -1
+    # a sequence of times drives n as the rule says
+    n, seq = 4, []
+    times = [5.0, 4.0, 3.0, 3.5, 2.0, 2.5]
+    for k in range(1, len(times)):
+        n = nn(n, times[k - 1], times[k], 2, 2, 8)
+        seq.append(n)
+    assert seq == [6, 8, 6, 8, 6]
+
+
+def test_sequence_and_set_n_validate_before_gpu(lib):
+    """Invalid sequence arguments are rejected before any device work."""
+    so = M.mlb_sequence_options(4, 1, 1, 8)
+    res = (M.mlb_result * 1)()
+    used = (C.c_int32 * 1)()
+    assert lib.mlbicgstab_solve_sequence(None, 1, None, None, 0, None, None, C.byref(so), res, used) == M.MLB_ERR_ARG
+    bad = M.mlb_sequence_options(9, 1, 1, 8)   # n0 > n_max
+    hs = (C.c_void_p * 1)(1)
+    t = (C.c_double * 1)(1e-10)
+    m = (C.c_int64 * 1)(10)
+    p = (C.c_void_p * 1)(1)
+    assert lib.mlbicgstab_solve_sequence(hs, 1, p, p, 0, t, m, C.byref(bad), res, used) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_set_n(None, 2) == M.MLB_ERR_ARG
