@@ -47,6 +47,14 @@ WORKLOADS = {
     "cd3d128_n4_refined": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=1,
                                inner_tol=1e-5),
     "helmholtz_n8_c128": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=0),
+    # the omega guard of Eq. 5.1 (kappa = 0.7, the value suggested by
+    # Sleijpen & van der Vorst) on the same complex system
+    "helmholtz_n8_c128_kappa07": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=0,
+                                      kappa=0.7),
+    # Jacobi right preconditioning (Algorithm 7.1, M = diag(A)) on the
+    # headline system
+    "cd3d128_n4_fp64_jacobi": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=0,
+                                   precond=1),
     "reservoir_n8_fp64": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0),
     "batch512_n4_fp64": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0),
     "batch512_n4_refined": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=1,
@@ -56,7 +64,8 @@ for _n in (1, 8, 16):
     WORKLOADS[f"cd3d128_n{_n}_fp64"] = dict(kind="cd3d", m=128, n=_n, tol=1e-10, maxit=60000,
                                            precision=0)
 DEFAULT = "cd3d128_n4_fp64"
-VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "cd3d128_n4_refined"]
+VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07",
+            "cd3d128_n4_fp64_jacobi", "cd3d128_n4_refined"]
 
 
 def _load_peaks():
@@ -101,7 +110,12 @@ def _variant_desc(name, wl, systems):
             "helmholtz": "complex damped shifted Laplacian 256x256x64, A^H as separate CSR",
             "reservoir": "3x3-block reservoir system 64x64x32 cells",
             "batch": "512 2-D/3-D convection-diffusion systems, N ~ logU[1e3,1e5], one launch"}[wl["kind"]]
-    return f"{what} (N={N:,}, nnz={nnz:,}), n={wl['n']}, {_prec_name(wl)}, tol {wl['tol']:g}"
+    extra = ""
+    if wl.get("kappa", 0.0) > 0:
+        extra += f", omega guard kappa={wl['kappa']:g} (Eq. 5.1)"
+    if wl.get("precond", 0) == 1:
+        extra += ", Jacobi M=diag(A) (Algorithm 7.1)"
+    return f"{what} (N={N:,}, nnz={nnz:,}), n={wl['n']}, {_prec_name(wl)}{extra}, tol {wl['tol']:g}"
 
 
 def _prec_name(wl):
@@ -183,10 +197,8 @@ class ClockSampler:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1106_3678_gb300 import replicas
+    return replicas.world()
 
 
 def oracle_sample(A, b, n, iters):
@@ -268,13 +280,15 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
     systems = _make_variant_inputs(vwl)
     dt = torch.complex128 if np.iscomplexobj(systems[0][2]) else torch.float64
     hs = [M.mlbicgstab_create(A, AH=AH, n=vwl["n"], q_seed=0, max_outer=10, stream=stream,
-                              precision=vwl.get("precision", 0), inner_tol=vwl.get("inner_tol"))
+                              precision=vwl.get("precision", 0), inner_tol=vwl.get("inner_tol"),
+                              kappa=vwl.get("kappa", 0.0), precond=vwl.get("precond", 0))
           for A, AH, _ in systems]
     bs = [torch.tensor(b, dtype=dt, device=dev) for _, _, b in systems]
     xs = [torch.zeros_like(b) for b in bs]
     steps = max(1, args.variant_steps)
     out = {"workload": name, "config": _variant_desc(name, vwl, systems),
-           "precision": _prec_name(vwl), "n": vwl["n"], "unit": UNIT}
+           "precision": _prec_name(vwl), "n": vwl["n"], "unit": UNIT,
+           "kappa": vwl.get("kappa", 0.0), "precond": ["none", "jacobi"][vwl.get("precond", 0)]}
     if vwl["kind"] == "batch":
         def once():
             for x in xs:
@@ -357,11 +371,8 @@ def run_ours(args, wl):
     total_ms, results = _timed_solves(M, h, b_d, x_d, wl, stream, args.steps, args.warmup, barrier)
     clk = clocks.stop()
 
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_1106_3678_gb300 import replicas
+    total_ms = replicas.max_over_ranks(total_ms, dev)
 
     # variants: other workloads, precisions and the batched form
     variants = []
@@ -375,6 +386,13 @@ def run_ours(args, wl):
             v["speedup_vs_fp64"] = v["value"] / head_value
         if v["workload"] == "batch512_n4_refined" and "batch512_n4_fp64" in by_name:
             v["speedup_vs_batch_fp64"] = v["value"] / by_name["batch512_n4_fp64"]["value"]
+        if v["workload"] == "helmholtz_n8_c128_kappa07" and "helmholtz_n8_c128" in by_name:
+            base = by_name["helmholtz_n8_c128"]
+            v["vs_kappa0"] = {"speedup": v["value"] / base["value"],
+                              "iters": v["iters_per_solve"], "iters_kappa0": base["iters_per_solve"]}
+        if v["workload"] == "cd3d128_n4_fp64_jacobi":
+            v["vs_unpreconditioned"] = {"speedup": v["value"] / head_value,
+                                        "iters": v["iters_per_solve"]}
 
     # end to end through the C ABI with pinned host buffers
     b_h = torch.tensor(b, dtype=torch.float64).pin_memory()
@@ -387,12 +405,7 @@ def run_ours(args, wl):
         xn[:] = 0.0
         M.mlbicgstab_solve(h, bn, xn, wl["tol"], wl["maxit"])
     barrier()
-    e2e_s = max(time.perf_counter() - t0, 1e-9)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replicas.max_over_ranks(max(time.perf_counter() - t0, 1e-9), dev)
 
     if rank != 0:
         if ws > 1:
