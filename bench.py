@@ -64,6 +64,14 @@ for _n in (1, 8, 16):
     WORKLOADS[f"cd3d128_n{_n}_fp64"] = dict(kind="cd3d", m=128, n=_n, tol=1e-10, maxit=60000,
                                            precision=0)
 DEFAULT = "cd3d128_n4_fp64"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the solve
+# kernel on the headline workload, from one ncu capture of a 300-iteration
+# launch of the current kernel: 145.68 GB + 36.73 GB.  Traffic grows in
+# proportion to the iterations, so a full launch is scaled by its
+# iteration count.  Set to None whenever the kernel changes until it is
+# captured again.
+NCU_DRAM_BYTES_PER_ITER = (145.68e9 + 36.73e9) / 300
 VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07",
             "cd3d128_n4_fp64_jacobi", "cd3d128_n4_refined"]
 
@@ -443,7 +451,10 @@ def run_ours(args, wl):
         "restarts": [r["outer"] for r in results],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": None, "peak_kind": peak_kind,
+                     "traffic": (NCU_DRAM_BYTES_PER_ITER * statistics.median(iters)
+                                 if NCU_DRAM_BYTES_PER_ITER and args.workload == DEFAULT else None),
+                     "traffic_source": "ncu dram bytes of a 300-iteration launch, scaled by iterations",
+                     "peak_kind": peak_kind,
                      "kernel": "solve_kernel<double> (persistent, one launch per solve)",
                      "algorithmic_bytes_per_launch": kern_bytes / len(results),
                      "kernel_ms_per_launch": kern_ms / len(results)},
