@@ -52,7 +52,8 @@ WORKLOADS = {
     "helmholtz_n8_c128_kappa07": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=0,
                                       kappa=0.7),
     # Jacobi right preconditioning (Algorithm 7.1, M = diag(A)) on the
-    # headline system
+    # headline system (not in the default list: on this family it converges
+    # about 4x slower than M = I, in the oracle as well)
     "cd3d128_n4_fp64_jacobi": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=0,
                                    precond=1),
     "reservoir_n8_fp64": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0),
@@ -71,9 +72,9 @@ DEFAULT = "cd3d128_n4_fp64"
 # proportion to the iterations, so a full launch is scaled by its
 # iteration count.  Set to None whenever the kernel changes until it is
 # captured again.
-NCU_DRAM_BYTES_PER_ITER = (145.68e9 + 36.73e9) / 300
+NCU_DRAM_BYTES_PER_ITER = None   # kernel changed since the last capture
 VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07",
-            "cd3d128_n4_fp64_jacobi", "cd3d128_n4_refined"]
+            "cd3d128_n4_refined"]
 
 
 def _load_peaks():

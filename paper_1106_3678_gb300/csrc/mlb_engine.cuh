@@ -362,6 +362,12 @@ __device__ __forceinline__ typename coef_of<T>::type mk_coef(const double *v) {
 // system per CTA).  Every CTA of a team passes the same sequence of
 // barriers and reductions, so `epoch` and the slots advance in lock step.
 // Several engines in one kernel share one GridSync.
+//
+// The object lives in shared memory, one per CTA (thread-private copies
+// would sit in local memory, which the L1 left beside the tile ring cannot
+// hold for 512 threads, so every access would go to L2).  Writers: `epoch`
+// and `slot` thread 0; `pseq` the producer lane; `cseq` the consumer
+// threads (all the same value); `ok` any thread (only ever set to false).
 struct GridSync {
     unsigned nblocks;   // CTAs in the team
     unsigned bid;       // this CTA's rank in the team
@@ -371,7 +377,7 @@ struct GridSync {
     int *sflag;         // shared
     uint64_t timeout_ns;
     unsigned epoch;
-    int slot, rslot;
+    int slot;
     bool ok;            // false once a barrier or a tile wait failed
     TileRing *ring;     // shared-memory tile pipeline of this CTA
     unsigned pseq;      // tiles issued (producer lane)
@@ -380,11 +386,11 @@ struct GridSync {
     // Team = the whole grid.
     __device__ GridSync(BarrierState *b, double *p, double *r, int *f, uint64_t to, TileRing *rg)
         : nblocks(gridDim.x), bid(blockIdx.x), bar(b), partials(p), red(r), sflag(f), timeout_ns(to), epoch(0),
-          slot(0), rslot(0), ok(true), ring(rg), pseq(0), cseq(0) {}
+          slot(0), ok(true), ring(rg), pseq(0), cseq(0) {}
     // Team = this CTA alone.
     __device__ GridSync(double *r, int *f, uint64_t to, TileRing *rg)
         : nblocks(1), bid(0), bar(nullptr), partials(nullptr), red(r), sflag(f), timeout_ns(to), epoch(0), slot(0),
-          rslot(0), ok(true), ring(rg), pseq(0), cseq(0) {}
+          ok(true), ring(rg), pseq(0), cseq(0) {}
 
     // Thread 0 arrives/waits; all threads of the CTA then proceed.  Returns
     // false (uniformly) when the barrier failed.
@@ -444,12 +450,12 @@ struct GridSync {
         }
         const unsigned G = nblocks;
         double *part = partials + (size_t)slot * kMaxSums * G;
-        slot ^= 1;
         if (tid == 0) {
 #pragma unroll
             for (int k = 0; k < K; ++k) part[(size_t)k * G + bid] = bc[k];
         }
         if (!gbar()) return false;
+        if (tid == 0) slot ^= 1;   // every thread has read it (gbar synchronises)
         if (warp < K) {
             const double *p = part + (size_t)warp * G;
             double t = 0.0;
@@ -497,25 +503,26 @@ struct Engine {
     Acct *acct;      // accounting, kept by thread 0 (uniform in the grid)
     // ownership: slices [s_lo, s_hi), chunks [c_lo, c_hi)
     int64_t s_lo, s_hi, c_lo, c_hi;
-    int lane;
 
+    // Constructed by one thread in shared memory (one engine per CTA; see
+    // GridSync); every thread then calls attach().
     __device__ Engine(const SysView<T> &s, const SolveCtl &k, GridSync &g, S *c_, S *bt_, Acct *acct_)
         : sys(s), ctl(k), gs(g), c(c_), bt(bt_), acct(acct_) {
         own_range(s.nslices, g.nblocks, g.bid, s_lo, s_hi);
         c_lo = s_lo * CPS;
         c_hi = s_hi * CPS;
-        lane = threadIdx.x & 31;
-        soff_load(g.ring, s.slice_ptr, s_lo, s_hi);
     }
+    __device__ void attach() { soff_load(gs.ring, sys.slice_ptr, s_lo, s_hi); }
     __device__ __forceinline__ void op(int which, int cnt = 1) {
         if (threadIdx.x == 0) acct->ops[which] += cnt;
     }
 
     // Evaluate fn() in thread 0 only and give the value to every thread.
-    unsigned bslot = 0;
+    // Back-to-back calls use rotating slots; `bs` is the caller's counter
+    // (a register, the same sequence in every thread).
     template <typename Fn>
-    __device__ __forceinline__ S once_s(Fn fn) {
-        const int k = bslot++ & 3;
+    __device__ __forceinline__ S once_s(unsigned &bs, Fn fn) {
+        const int k = bs++ & 3;
         if constexpr (is_cx<T>::value) {
             if (threadIdx.x == 0) acct->z[k] = fn();
             __syncthreads();
@@ -527,8 +534,8 @@ struct Engine {
         }
     }
     template <typename Fn>
-    __device__ __forceinline__ double once_d(Fn fn) {
-        const int k = bslot++ & 3;
+    __device__ __forceinline__ double once_d(unsigned &bs, Fn fn) {
+        const int k = bs++ & 3;
         if (threadIdx.x == 0) acct->d[k] = fn();
         __syncthreads();
         return acct->d[k];
@@ -575,7 +582,7 @@ struct Engine {
         TileRing *const ring = gs.ring;
         const uint64_t to = gs.timeout_ns;
         if ((threadIdx.x >> 5) == kConsumerWarps) {
-            if (lane == 0) {
+            if ((threadIdx.x & 31) == 0) {
                 unsigned sq = gs.pseq;
                 okw = produce(ring, P, sq, to);
                 gs.pseq = sq;
@@ -605,9 +612,9 @@ struct Engine {
     __device__ __forceinline__ void spmv_rows(const T *xin, const T *const (&epi)[NE], Fin fin, ACC (&acc)[K]) {
         unsigned ps = gs.pseq, cs = gs.cseq;
         const bool okw = sell_spmv<NE>(gs.ring, ps, cs, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
-                                       sys.scol, sys.sval, xin, epi, lane, fin, acc);
-        gs.pseq = ps;
-        gs.cseq = cs;
+                                       sys.scol, sys.sval, xin, epi, threadIdx.x & 31, fin, acc);
+        if ((threadIdx.x >> 5) < kConsumerWarps) gs.cseq = cs;      // consumers
+        else if ((threadIdx.x & 31) == 0) gs.pseq = ps;             // producer lane
         if (!okw) gs.ring->failed = 1;
     }
     __device__ __forceinline__ bool ring_ok() {
@@ -1038,6 +1045,7 @@ struct Engine {
                          const typename wide_of<T>::type *init = nullptr, double scale = 1.0) {
         const int n = sys.n;
         Out o{1, 0, 0, 0, 0.0};
+        unsigned bsl = 0;   // rotating broadcast slot of once_s / once_d
         if (threadIdx.x == 0)
             for (int q = 0; q < 5; ++q) acct->ops[q] = 0;
 
@@ -1057,11 +1065,11 @@ struct Engine {
             op(OP_NORM, 2);
             op(OP_MATVEC, 1);
         }
-        const double bnrm2 = once_d([&] {
+        const double bnrm2 = once_d(bsl, [&] {
             double t = sqrt(bb);
             return t == 0.0 ? 1.0 : t;
         });
-        double err = once_d([&] { return sqrt(rr) / bnrm2; });
+        double err = once_d(bsl, [&] { return sqrt(rr) / bnrm2; });
         o.err = err;
         record(rec, 0, err);
         if (err < tol) { o.flag = 0; return o; }
@@ -1083,13 +1091,13 @@ struct Engine {
             for (int i = 1; i <= n - 1; ++i) {
                 o.i = i;
                 // steps 5-8: alpha, x, r, e (and f_1^H r in block 0)
-                S alpha = once_s([&] { return e / c[i - 1]; });
+                S alpha = once_s(bsl, [&] { return e / c[i - 1]; });
                 double r2;
                 S qr;
                 if (!ph_alpha(alpha, i - 1, i, j == 0, r2, qr, fr)) return o;
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
-                err = once_d([&] { return sqrt(r2) / bnrm2; });
+                err = once_d(bsl, [&] { return sqrt(r2) / bnrm2; });
                 o.err = err;
                 iter++;
                 o.iter = iter;
@@ -1101,7 +1109,7 @@ struct Engine {
 
                 if (j >= 1) {
                     // steps 10-18: sweep the rest of block j-1 with q's
-                    S b0 = once_s([&] { return -(e / c[i]); });
+                    S b0 = once_s(bsl, [&] { return -(e / c[i]); });
                     if (threadIdx.x == 0) bt[i] = b0;
                     __syncthreads();
                     op(OP_SAXPY);
@@ -1111,7 +1119,7 @@ struct Engine {
                     } else {
                         if (!ph_w_first(b0, i, i + 1, d)) return o;
                         for (int s = i + 1; s <= n - 1; ++s) {
-                            S bs = once_s([&] { return -(d / c[s]); });
+                            S bs = once_s(bsl, [&] { return -(d / c[s]); });
                             if (threadIdx.x == 0) bt[s] = bs;
                             __syncthreads();
                             op(OP_DOT);
@@ -1126,19 +1134,19 @@ struct Engine {
                     op(OP_SAXPY);   // omega-correction
                     // steps 19-22: sweep block j with f's
                     for (int s = 0; s <= i - 1; ++s) {
-                        S beta = once_s([&] { return -(d / c[s]); });
+                        S beta = once_s(bsl, [&] { return -(d / c[s]); });
                         op(OP_DOT);
                         op(OP_SAXPY);
                         if (!ph_f_round(beta, s, i, s + 1 <= i - 1 ? s + 1 : -1, d)) return o;
                     }
                 } else {
                     // steps 24-29 (block 0)
-                    S beta = once_s([&] { return -(fr / c[0]); });
+                    S beta = once_s(bsl, [&] { return -(fr / c[0]); });
                     op(OP_DOT);
                     op(OP_SAXPY);
                     if (!ph_g_j0(beta, i, i >= 2 ? 1 : -1, d)) return o;
                     for (int s = 1; s <= i - 1; ++s) {
-                        beta = once_s([&] { return -(d / c[s]); });
+                        beta = once_s(bsl, [&] { return -(d / c[s]); });
                         op(OP_DOT);
                         op(OP_SAXPY);
                         if (!ph_f_round(beta, s, i, s + 1 <= i - 1 ? s + 1 : -1, d)) return o;
@@ -1156,13 +1164,13 @@ struct Engine {
             // steps 34-36: alpha, x, u (u kept in r)
             o.i = n;
             {
-                S alpha = once_s([&] { return e / c[n - 1]; });
+                S alpha = once_s(bsl, [&] { return e / c[n - 1]; });
                 double u2;
                 S dummy;
                 if (!ph_alpha(alpha, n - 1, -1, false, u2, dummy, fr)) return o;
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
-                err = once_d([&] { return sqrt(u2) / bnrm2; });
+                err = once_d(bsl, [&] { return sqrt(u2) / bnrm2; });
                 o.err = err;
                 if (err < tol) {
                     iter++;
@@ -1180,7 +1188,7 @@ struct Engine {
                 if (zz == 0.0 || !isfinite(zz)) { o.flag = -1; return o; }
                 op(OP_DOT);
                 if (ctl.kappa > 0.0) op(OP_NORM, 2);
-                omega = once_s([&] {
+                omega = once_s(bsl, [&] {
                     S om = zu / zz;
                     if (ctl.kappa > 0.0) {
                         double arho = abs_of(zu) / (sqrt(zz) * sqrt(u2));
@@ -1189,14 +1197,14 @@ struct Engine {
                     return om;
                 });
                 if (is_zero(omega) || !finite_of(omega)) { o.flag = -1; return o; }
-                inv_omega = once_s([&] { return recip(omega); });
+                inv_omega = once_s(bsl, [&] { return recip(omega); });
                 // steps 39-41: x += omega u, r = u - omega A u, e = q_1^H r
                 S q1r;
                 double r2;
                 if (!ph_omega(omega, r2, q1r)) return o;
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
-                err = once_d([&] { return sqrt(r2) / bnrm2; });
+                err = once_d(bsl, [&] { return sqrt(r2) / bnrm2; });
                 o.err = err;
                 iter++;
                 o.iter = iter;
@@ -1208,7 +1216,7 @@ struct Engine {
             }
             // steps 42-50: sweep block j with q's into slot 0
             {
-                S b0 = once_s([&] { return -(e / c[0]); });
+                S b0 = once_s(bsl, [&] { return -(e / c[0]); });
                 if (threadIdx.x == 0) bt[0] = b0;
                 __syncthreads();
                 op(OP_SAXPY);
@@ -1218,7 +1226,7 @@ struct Engine {
                 } else {
                     if (!ph_w_first(b0, 0, 1, d)) return o;
                     for (int s = 1; s <= n - 1; ++s) {
-                        S bs = once_s([&] { return -(d / c[s]); });
+                        S bs = once_s(bsl, [&] { return -(d / c[s]); });
                         if (threadIdx.x == 0) bt[s] = bs;
                         __syncthreads();
                         op(OP_DOT);

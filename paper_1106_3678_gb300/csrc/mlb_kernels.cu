@@ -1,4 +1,6 @@
 // Kernels of the ML(n)BiCGStab library (sm_103a).
+#include <new>
+
 #include "mlb_internal.h"
 #include "mlb_refine.cuh"
 
@@ -53,6 +55,14 @@ __device__ void run_fp64_solve(Engine<T> &E, GridSync &gs, const SolveCtl &ctl, 
     }
 }
 
+// Raw shared storage for an object constructed in place by thread 0
+// (per-CTA state shared by all threads of the CTA).
+template <typename X>
+struct alignas(16) SharedSlot {
+    unsigned char raw[sizeof(X)];
+    __device__ X *get() { return reinterpret_cast<X *>(raw); }
+};
+
 // Allow the ring's dynamic shared memory for a kernel (idempotent).
 static cudaError_t allow_ring(const void *fn) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
@@ -77,12 +87,24 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, Solv
     __shared__ int sflag;
     __shared__ Acct acct;
     __shared__ TileRing ring;
+    __shared__ SysView<T> s_sys;
+    __shared__ SolveCtl s_ctl;
+    __shared__ SharedSlot<GridSync> gs_slot;
+    __shared__ SharedSlot<Engine<T>> e_slot;
     ring_init(&ring, ring_buffer(dsm));
-    acct_reset(acct);
-    GridSync gs(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring);
-    Engine<T> E(sys, ctl, gs, cbuf, btbuf, &acct);
-    run_fp64_solve(E, gs, ctl, acct, ctl.res);
-    ring_drain(&ring, gs.pseq, gs.cseq, ctl.timeout_ns);
+    if (threadIdx.x == 0) {
+        s_sys = sys;
+        s_ctl = ctl;
+        new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring);
+        new (e_slot.get()) Engine<T>(s_sys, s_ctl, *gs_slot.get(), cbuf, btbuf, &acct);
+    }
+    acct_reset(acct);   // includes the __syncthreads that publishes the objects
+    GridSync &gs = *gs_slot.get();
+    Engine<T> &E = *e_slot.get();
+    E.attach();
+    run_fp64_solve(E, gs, s_ctl, acct, s_ctl.res);
+    __syncthreads();
+    ring_drain(&ring, gs.pseq, gs.cseq, s_ctl.timeout_ns);
 }
 
 // ===========================================================================
@@ -104,6 +126,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ Acct acct;
     __shared__ int s_next;
     __shared__ BatchItem<T> item;
+    __shared__ SharedSlot<GridSync> gs_slot;
+    __shared__ SharedSlot<Engine<T>> e_slot;
     ring_init(&ring, ring_buffer(dsm));
     unsigned pseq = 0, cseq = 0;
     uint64_t timeout = 2000000000ull;
@@ -115,11 +139,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (threadIdx.x == 0) item = items[order[q]];
         acct_reset(acct);   // includes the __syncthreads that publishes `item`
         timeout = item.ctl.timeout_ns;
-        GridSync gs(red, &sflag, timeout, &ring);
-        gs.pseq = pseq;
-        gs.cseq = cseq;
-        Engine<T> E(item.sys, item.ctl, gs, cbuf, btbuf, &acct);
+        if (threadIdx.x == 0) {
+            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring);
+            g->pseq = pseq;
+            g->cseq = cseq;
+            new (e_slot.get()) Engine<T>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
+        }
+        __syncthreads();
+        GridSync &gs = *gs_slot.get();
+        Engine<T> &E = *e_slot.get();
+        E.attach();
         run_fp64_solve(E, gs, item.ctl, acct, item.ctl.res);
+        __syncthreads();
         pseq = gs.pseq;
         cseq = gs.cseq;
         __syncthreads();
@@ -140,6 +171,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ Acct acct;
     __shared__ int s_next;
     __shared__ BatchItemR<T32, T64> item;
+    __shared__ SharedSlot<GridSync> gs_slot;
+    __shared__ SharedSlot<Engine<T32>> e_slot;
+    __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
     ring_init(&ring, ring_buffer(dsm));
     unsigned pseq = 0, cseq = 0;
     uint64_t timeout = 2000000000ull;
@@ -151,12 +185,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (threadIdx.x == 0) item = items[order[q]];
         acct_reset(acct);
         timeout = item.ctl.timeout_ns;
-        GridSync gs(red, &sflag, timeout, &ring);
-        gs.pseq = pseq;
-        gs.cseq = cseq;
-        Engine<T32> E(item.sys, item.ctl, gs, cbuf, btbuf, &acct);
-        Refiner<T64, T32> R(item.rv, gs, &acct, item.sys.x);
+        if (threadIdx.x == 0) {
+            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring);
+            g->pseq = pseq;
+            g->cseq = cseq;
+            new (e_slot.get()) Engine<T32>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
+            new (r_slot.get()) Refiner<T64, T32>(item.rv, *g, &acct, item.sys.x);
+        }
+        __syncthreads();
+        GridSync &gs = *gs_slot.get();
+        Engine<T32> &E = *e_slot.get();
+        Refiner<T64, T32> &R = *r_slot.get();
+        E.attach();
         RefineOut o = refine_solve<T32, T64>(E, R, item.ctl, item.rc);
+        __syncthreads();
         pseq = gs.pseq;
         cseq = gs.cseq;
         if (threadIdx.x == 0) {
@@ -250,12 +292,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ S btbuf[kMaxN];
     __shared__ int sflag;
     __shared__ Acct acct;
+    __shared__ SysView<T32> s_sys;
+    __shared__ RefView<T64> s_rv;
+    __shared__ SolveCtl s_ctl;
+    __shared__ RefCtl s_rc;
+    __shared__ SharedSlot<GridSync> gs_slot;
+    __shared__ SharedSlot<Engine<T32>> e_slot;
+    __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
     ring_init(&ring, ring_buffer(dsm));
-    acct_reset(acct);
-    GridSync gs(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring);
-    Engine<T32> E(sys, ctl, gs, cbuf, btbuf, &acct);
-    Refiner<T64, T32> R(rv, gs, &acct, sys.x);
-    RefineOut o = refine_solve<T32, T64>(E, R, ctl, rc);
+    if (threadIdx.x == 0) {
+        s_sys = sys;
+        s_rv = rv;
+        s_ctl = ctl;
+        s_rc = rc;
+        GridSync *g = new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring);
+        new (e_slot.get()) Engine<T32>(s_sys, s_ctl, *g, cbuf, btbuf, &acct);
+        new (r_slot.get()) Refiner<T64, T32>(s_rv, *g, &acct, s_sys.x);
+    }
+    acct_reset(acct);   // includes the __syncthreads that publishes the objects
+    GridSync &gs = *gs_slot.get();
+    Engine<T32> &E = *e_slot.get();
+    Refiner<T64, T32> &R = *r_slot.get();
+    E.attach();
+    RefineOut o = refine_solve<T32, T64>(E, R, s_ctl, s_rc);
+    __syncthreads();
     ring_drain(&ring, gs.pseq, gs.cseq, ctl.timeout_ns);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevResult *res = ctl.res;

@@ -44,12 +44,11 @@ struct Refiner {
     Acct *acct;
     const T32 *x32;   // inner solution d
     int64_t s_lo, s_hi;   // owned slices (the same rows as the inner engine)
-    int lane;
 
+    // Constructed by one thread in shared memory, like the engine.
     __device__ Refiner(const RefView<T64> &v_, GridSync &g, Acct *a, const T32 *x32_)
         : v(v_), gs(g), acct(a), x32(x32_) {
         own_range(v_.nslices, g.nblocks, g.bid, s_lo, s_hi);
-        lane = threadIdx.x & 31;
     }
 
     // r = b - A x in FP64; sums ||b||^2, ||r||^2.
@@ -59,7 +58,7 @@ struct Refiner {
         T64 *const r = v.r;
         unsigned ps = gs.pseq, cs = gs.cseq;
         bool okt = sell_spmv<1>(gs.ring, ps, cs, gs.timeout_ns, s_lo, s_hi, v.spt[1], v.slice_ptr, v.scol, v.sval,
-                                v.x, epi, lane,
+                                v.x, epi, threadIdx.x & 31,
                                 [&](int64_t row, T64 y, const T64 (&e)[1], double(&a)[2]) {
                                     T64 rv = subT(e[0], y);
                                     r[row] = rv;
@@ -67,8 +66,8 @@ struct Refiner {
                                     acc_nrm(&a[1], rv);
                                 },
                                 acc);
-        gs.pseq = ps;
-        gs.cseq = cs;
+        if ((threadIdx.x >> 5) < kConsumerWarps) gs.cseq = cs;      // consumers
+        else if ((threadIdx.x & 31) == 0) gs.pseq = ps;             // producer lane
         if (!okt) gs.ring->failed = 1;
         if (!gs.template reduce<2>(acc)) return false;
         if (gs.ring->failed) { gs.ok = false; return false; }

@@ -189,19 +189,29 @@ __device__ __forceinline__ int tile_chunks_for(int ni) {
 // Producer side (lane 0 of the producer warp): issue every tile of pass P.
 // `seq` is this CTA's running tile sequence number.
 __device__ __forceinline__ bool produce(TileRing *R, const TilePass &P, unsigned &seq, uint64_t timeout_ns) {
-    const int nt = P.ntiles();
+    // The descriptor lives in memory (its input list is indexed at run
+    // time); copy it into registers once, so the issue loop does not wait
+    // on a load before every copy.
+    const unsigned char *src[kMaxInputs];
+#pragma unroll
+    for (int i = 0; i < kMaxInputs; ++i) src[i] = i < P.ni ? (const unsigned char *)P.in[i] : nullptr;
+    const int ni = P.ni, tc = P.tc;
+    const int64_t c_lo = P.c_lo, c_hi = P.c_hi;
+    unsigned char *const buf = R->buf;
+    const int nt = (int)((c_hi - c_lo + tc - 1) / tc);
     for (int t = 0; t < nt; ++t, ++seq) {
         const int s = (int)(seq % kStages);
         const unsigned use = seq / kStages;
         if (use > 0 && !mbar_wait(&R->empty[s], (use - 1) & 1u, timeout_ns)) return false;
-        const int64_t c0 = P.c_lo + (int64_t)t * P.tc;
-        int64_t cn = P.c_hi - c0;
-        if (cn > P.tc) cn = P.tc;
+        const int64_t c0 = c_lo + (int64_t)t * tc;
+        int64_t cn = c_hi - c0;
+        if (cn > tc) cn = tc;
         const unsigned bytes = (unsigned)(cn * 16);
-        mbar_arrive_expect_tx(&R->full[s], bytes * (unsigned)P.ni);
-        unsigned char *dst = R->buf + (size_t)s * kStageBytes;
-        for (int i = 0; i < P.ni; ++i)
-            bulk_g2s(dst + (size_t)i * P.tc * 16, (const unsigned char *)P.in[i] + c0 * 16, bytes, &R->full[s]);
+        mbar_arrive_expect_tx(&R->full[s], bytes * (unsigned)ni);
+        unsigned char *dst = buf + (size_t)s * kStageBytes;
+#pragma unroll
+        for (int i = 0; i < kMaxInputs; ++i)
+            if (i < ni) bulk_g2s(dst + (size_t)i * tc * 16, src[i] + c0 * 16, bytes, &R->full[s]);
     }
     return true;
 }
