@@ -47,6 +47,8 @@ WORKLOADS = {
     "cd3d128_n4_refined": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=1,
                                inner_tol=1e-5),
     "helmholtz_n8_c128": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=0),
+    "helmholtz_n8_c64_refined": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=1,
+                                     inner_tol=1e-5),
     # the omega guard of Eq. 5.1 (kappa = 0.7, the value suggested by
     # Sleijpen & van der Vorst) on the same complex system
     "helmholtz_n8_c128_kappa07": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=0,

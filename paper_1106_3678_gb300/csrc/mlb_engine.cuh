@@ -366,8 +366,11 @@ __device__ __forceinline__ typename coef_of<T>::type mk_coef(const double *v) {
 // The object lives in shared memory, one per CTA (thread-private copies
 // would sit in local memory, which the L1 left beside the tile ring cannot
 // hold for 512 threads, so every access would go to L2).  Writers: `epoch`
-// and `slot` thread 0; `pseq` the producer lane; `cseq` the consumer
-// threads (all the same value); `ok` any thread (only ever set to false).
+// and `slot` thread 0; `ok` any thread (only ever set to false).  The tile
+// sequence counters are per thread, in `seqs[threadIdx.x]` (the producer
+// lane counts issued tiles, a consumer thread consumed ones): one shared
+// counter would race, since in a pass of at most kStages tiles a fast warp
+// can finish the pass before a slow one has read where it starts.
 struct GridSync {
     unsigned nblocks;   // CTAs in the team
     unsigned bid;       // this CTA's rank in the team
@@ -380,17 +383,18 @@ struct GridSync {
     int slot;
     bool ok;            // false once a barrier or a tile wait failed
     TileRing *ring;     // shared-memory tile pipeline of this CTA
-    unsigned pseq;      // tiles issued (producer lane)
-    unsigned cseq;      // tiles consumed (consumer threads)
+    unsigned *seqs;     // shared, kThreads per-thread tile counters
+
+    __device__ __forceinline__ unsigned &seq() const { return seqs[threadIdx.x]; }
 
     // Team = the whole grid.
-    __device__ GridSync(BarrierState *b, double *p, double *r, int *f, uint64_t to, TileRing *rg)
+    __device__ GridSync(BarrierState *b, double *p, double *r, int *f, uint64_t to, TileRing *rg, unsigned *sq)
         : nblocks(gridDim.x), bid(blockIdx.x), bar(b), partials(p), red(r), sflag(f), timeout_ns(to), epoch(0),
-          slot(0), ok(true), ring(rg), pseq(0), cseq(0) {}
+          slot(0), ok(true), ring(rg), seqs(sq) {}
     // Team = this CTA alone.
-    __device__ GridSync(double *r, int *f, uint64_t to, TileRing *rg)
+    __device__ GridSync(double *r, int *f, uint64_t to, TileRing *rg, unsigned *sq)
         : nblocks(1), bid(0), bar(nullptr), partials(nullptr), red(r), sflag(f), timeout_ns(to), epoch(0), slot(0),
-          ok(true), ring(rg), pseq(0), cseq(0) {}
+          ok(true), ring(rg), seqs(sq) {}
 
     // Thread 0 arrives/waits; all threads of the CTA then proceed.  Returns
     // false (uniformly) when the barrier failed.
@@ -583,14 +587,14 @@ struct Engine {
         const uint64_t to = gs.timeout_ns;
         if ((threadIdx.x >> 5) == kConsumerWarps) {
             if ((threadIdx.x & 31) == 0) {
-                unsigned sq = gs.pseq;
+                unsigned sq = gs.seq();
                 okw = produce(ring, P, sq, to);
-                gs.pseq = sq;
+                gs.seq() = sq;
             }
         } else {
-            unsigned sq = gs.cseq;
+            unsigned sq = gs.seq();
             okw = consume(ring, P, sq, to, [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k, acc); });
-            gs.cseq = sq;
+            gs.seq() = sq;
         }
         if (!okw) gs.ring->failed = 1;
 #pragma unroll
@@ -610,11 +614,10 @@ struct Engine {
     // reports it.
     template <int K, int NE, typename Fin>
     __device__ __forceinline__ void spmv_rows(const T *xin, const T *const (&epi)[NE], Fin fin, ACC (&acc)[K]) {
-        unsigned ps = gs.pseq, cs = gs.cseq;
-        const bool okw = sell_spmv<NE>(gs.ring, ps, cs, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
+        unsigned sq = gs.seq();   // issued (producer lane) or consumed (consumers) tiles
+        const bool okw = sell_spmv<NE>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
                                        sys.scol, sys.sval, xin, epi, threadIdx.x & 31, fin, acc);
-        if ((threadIdx.x >> 5) < kConsumerWarps) gs.cseq = cs;      // consumers
-        else if ((threadIdx.x & 31) == 0) gs.pseq = ps;             // producer lane
+        gs.seq() = sq;
         if (!okw) gs.ring->failed = 1;
     }
     __device__ __forceinline__ bool ring_ok() {

@@ -91,11 +91,13 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, Solv
     __shared__ SolveCtl s_ctl;
     __shared__ SharedSlot<GridSync> gs_slot;
     __shared__ SharedSlot<Engine<T>> e_slot;
+    __shared__ unsigned seqs[kThreads];
     ring_init(&ring, ring_buffer(dsm));
+    seqs[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         s_sys = sys;
         s_ctl = ctl;
-        new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring);
+        new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring, seqs);
         new (e_slot.get()) Engine<T>(s_sys, s_ctl, *gs_slot.get(), cbuf, btbuf, &acct);
     }
     acct_reset(acct);   // includes the __syncthreads that publishes the objects
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, Solv
     E.attach();
     run_fp64_solve(E, gs, s_ctl, acct, s_ctl.res);
     __syncthreads();
-    ring_drain(&ring, gs.pseq, gs.cseq, s_ctl.timeout_ns);
+    ring_drain(&ring, seqs[kConsumers], seqs[0], s_ctl.timeout_ns);
 }
 
 // ===========================================================================
@@ -128,8 +130,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ BatchItem<T> item;
     __shared__ SharedSlot<GridSync> gs_slot;
     __shared__ SharedSlot<Engine<T>> e_slot;
+    __shared__ unsigned seqs[kThreads];   // tile counters, kept across systems
     ring_init(&ring, ring_buffer(dsm));
-    unsigned pseq = 0, cseq = 0;
+    seqs[threadIdx.x] = 0;
     uint64_t timeout = 2000000000ull;
     for (;;) {
         if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
@@ -140,9 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         acct_reset(acct);   // includes the __syncthreads that publishes `item`
         timeout = item.ctl.timeout_ns;
         if (threadIdx.x == 0) {
-            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring);
-            g->pseq = pseq;
-            g->cseq = cseq;
+            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
             new (e_slot.get()) Engine<T>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
         }
         __syncthreads();
@@ -151,11 +152,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         E.attach();
         run_fp64_solve(E, gs, item.ctl, acct, item.ctl.res);
         __syncthreads();
-        pseq = gs.pseq;
-        cseq = gs.cseq;
-        __syncthreads();
     }
-    ring_drain(&ring, pseq, cseq, timeout);
+    ring_drain(&ring, seqs[kConsumers], seqs[0], timeout);
 }
 
 template <typename T32, typename T64>
@@ -174,8 +172,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ SharedSlot<GridSync> gs_slot;
     __shared__ SharedSlot<Engine<T32>> e_slot;
     __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
+    __shared__ unsigned seqs[kThreads];   // tile counters, kept across systems
     ring_init(&ring, ring_buffer(dsm));
-    unsigned pseq = 0, cseq = 0;
+    seqs[threadIdx.x] = 0;
     uint64_t timeout = 2000000000ull;
     for (;;) {
         if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
@@ -186,9 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         acct_reset(acct);
         timeout = item.ctl.timeout_ns;
         if (threadIdx.x == 0) {
-            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring);
-            g->pseq = pseq;
-            g->cseq = cseq;
+            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
             new (e_slot.get()) Engine<T32>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
             new (r_slot.get()) Refiner<T64, T32>(item.rv, *g, &acct, item.sys.x);
         }
@@ -199,8 +196,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         E.attach();
         RefineOut o = refine_solve<T32, T64>(E, R, item.ctl, item.rc);
         __syncthreads();
-        pseq = gs.pseq;
-        cseq = gs.cseq;
         if (threadIdx.x == 0) {
             DevResult *res = item.ctl.res;
             res->flag = o.flag;
@@ -217,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncthreads();
     }
-    ring_drain(&ring, pseq, cseq, timeout);
+    ring_drain(&ring, seqs[kConsumers], seqs[0], timeout);
 }
 
 template <typename T>
@@ -299,13 +294,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ SharedSlot<GridSync> gs_slot;
     __shared__ SharedSlot<Engine<T32>> e_slot;
     __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
+    __shared__ unsigned seqs[kThreads];
     ring_init(&ring, ring_buffer(dsm));
+    seqs[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         s_sys = sys;
         s_rv = rv;
         s_ctl = ctl;
         s_rc = rc;
-        GridSync *g = new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring);
+        GridSync *g = new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring, seqs);
         new (e_slot.get()) Engine<T32>(s_sys, s_ctl, *g, cbuf, btbuf, &acct);
         new (r_slot.get()) Refiner<T64, T32>(s_rv, *g, &acct, s_sys.x);
     }
@@ -316,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     E.attach();
     RefineOut o = refine_solve<T32, T64>(E, R, s_ctl, s_rc);
     __syncthreads();
-    ring_drain(&ring, gs.pseq, gs.cseq, ctl.timeout_ns);
+    ring_drain(&ring, seqs[kConsumers], seqs[0], ctl.timeout_ns);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevResult *res = ctl.res;
         res->flag = o.flag;

@@ -56,8 +56,8 @@ struct Refiner {
         double acc[2] = {0.0, 0.0};
         const T64 *epi[1] = {v.b};
         T64 *const r = v.r;
-        unsigned ps = gs.pseq, cs = gs.cseq;
-        bool okt = sell_spmv<1>(gs.ring, ps, cs, gs.timeout_ns, s_lo, s_hi, v.spt[1], v.slice_ptr, v.scol, v.sval,
+        unsigned sq = gs.seq();   // issued (producer lane) or consumed (consumers) tiles
+        bool okt = sell_spmv<1>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, v.spt[1], v.slice_ptr, v.scol, v.sval,
                                 v.x, epi, threadIdx.x & 31,
                                 [&](int64_t row, T64 y, const T64 (&e)[1], double(&a)[2]) {
                                     T64 rv = subT(e[0], y);
@@ -66,8 +66,7 @@ struct Refiner {
                                     acc_nrm(&a[1], rv);
                                 },
                                 acc);
-        if ((threadIdx.x >> 5) < kConsumerWarps) gs.cseq = cs;      // consumers
-        else if ((threadIdx.x & 31) == 0) gs.pseq = ps;             // producer lane
+        gs.seq() = sq;
         if (!okt) gs.ring->failed = 1;
         if (!gs.template reduce<2>(acc)) return false;
         if (gs.ring->failed) { gs.ok = false; return false; }

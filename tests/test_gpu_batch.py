@@ -77,3 +77,25 @@ def test_batch_rejects_mixed_precision():
         M.mlbicgstab_solve_batch([h1, h2], [b, b], [np.zeros(64), np.zeros(64)],
                                  [1e-10, 1e-10], [100, 100])
     assert e.value.code == M.MLB_ERR_ARG
+
+
+def test_batch_of_small_passes_is_race_free_and_deterministic():
+    """Many refinement steps on small systems make many passes of a single
+    tile, where the warps of a CTA can be a whole pass apart.  Each thread
+    keeps its own tile counter, so every wait must complete (no status
+    MLB_ERR_TIMEOUT) and repeated launches must give the same bits."""
+    import torch
+    systems = [A for A, _ in W.batch_cd(256, seed=23, n_min=300, n_max=3000)]
+    bs = [torch.tensor(W.row_sums(A), device="cuda") for A in systems]
+    runs = []
+    for _ in range(3):
+        hs = [M.mlbicgstab_create(A, n=4, q_seed=0, precision=M.MLB_PREC_FP32_REFINED, max_outer=40,
+                                  inner_tol=1e-2, inner_maxit=50, timeout_ns=500_000_000) for A in systems]
+        xs = [torch.zeros(A.n_rows, dtype=torch.float64, device="cuda") for A in systems]
+        res = M.mlbicgstab_solve_batch(hs, bs, xs, [1e-10] * len(hs), [20000] * len(hs))
+        assert all(r.status == 0 for r in res)
+        runs.append(([x.cpu().numpy() for x in xs], [(r.iter, r.outer, r.flag) for r in res]))
+    for xs_k, meta_k in runs[1:]:
+        assert meta_k == runs[0][1]
+        for a, b in zip(xs_k, runs[0][0]):
+            np.testing.assert_array_equal(a, b)
