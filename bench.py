@@ -70,11 +70,11 @@ DEFAULT = "cd3d128_n4_fp64"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the solve
 # kernel on the headline workload, from one ncu capture of a 300-iteration
-# launch of the current kernel: 145.68 GB + 36.73 GB.  Traffic grows in
+# launch of the current kernel: 136.79 GB + 34.50 GB.  Traffic grows in
 # proportion to the iterations, so a full launch is scaled by its
 # iteration count.  Set to None whenever the kernel changes until it is
 # captured again.
-NCU_DRAM_BYTES_PER_ITER = None   # kernel changed since the last capture
+NCU_DRAM_BYTES_PER_ITER = (136.79e9 + 34.50e9) / 300
 VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07",
             "cd3d128_n4_refined"]
 
