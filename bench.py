@@ -60,6 +60,10 @@ WORKLOADS = {
                                    precond=1),
     "reservoir_n8_fp64": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0),
     "batch512_n4_fp64": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0),
+    # a sequence of right-hand sides with n chosen by the rule of §5
+    # (n0 = 4, step 2, n in [1, 16]) against the same sequence at fixed n = 4
+    "sequence8_cd3d64": dict(kind="sequence", m=64, n=16, count=8, n0=4, step=2, n_min=1, n_max=16,
+                             tol=1e-10, maxit=40000, precision=0),
     "batch512_n4_refined": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=1,
                                 inner_tol=1e-4),
 }
@@ -76,7 +80,7 @@ DEFAULT = "cd3d128_n4_fp64"
 # captured again.
 NCU_DRAM_BYTES_PER_ITER = (136.79e9 + 34.50e9) / 300
 VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07",
-            "cd3d128_n4_refined"]
+            "sequence8_cd3d64", "cd3d128_n4_refined"]
 
 
 def _load_peaks():
@@ -111,6 +115,9 @@ def _make_variant_inputs(wl):
         return [(A, None, W.row_sums(A))]
     if kind == "batch":
         return [(A, None, W.row_sums(A)) for A, _ in W.batch_cd(512, seed=5)]
+    if kind == "sequence":
+        A = W.cd3d_lognormal(wl["m"])
+        return [(A, None, W.uniform_rhs(A.n_rows, seed=10 + k)) for k in range(wl["count"])]
     raise ValueError(kind)
 
 
@@ -120,7 +127,10 @@ def _variant_desc(name, wl, systems):
     what = {"cd3d": "3-D log-normal convection-diffusion 128^3",
             "helmholtz": "complex damped shifted Laplacian 256x256x64, A^H as separate CSR",
             "reservoir": "3x3-block reservoir system 64x64x32 cells",
-            "batch": "512 2-D/3-D convection-diffusion systems, N ~ logU[1e3,1e5], one launch"}[wl["kind"]]
+            "batch": "512 2-D/3-D convection-diffusion systems, N ~ logU[1e3,1e5], one launch",
+            "sequence": (f"sequence of {wl.get('count', 0)} right-hand sides U[-1,1] (seeds 10..) on the 3-D "
+                         f"log-normal convection-diffusion {wl.get('m', 0)}^3 system, n by the rule of §5 "
+                         f"(n0={wl.get('n0')}, step {wl.get('step')}, n in [{wl.get('n_min')}, {wl.get('n_max')}])")}[wl["kind"]]
     extra = ""
     if wl.get("kappa", 0.0) > 0:
         extra += f", omega guard kappa={wl['kappa']:g} (Eq. 5.1)"
@@ -289,6 +299,8 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
     if args.maxit > 0:
         vwl["maxit"] = args.maxit
     systems = _make_variant_inputs(vwl)
+    if vwl["kind"] == "sequence":
+        return _measure_sequence(M, name, vwl, systems, dev, stream, barrier, ws)
     dt = torch.complex128 if np.iscomplexobj(systems[0][2]) else torch.float64
     hs = [M.mlbicgstab_create(A, AH=AH, n=vwl["n"], q_seed=0, max_outer=10, stream=stream,
                               precision=vwl.get("precision", 0), inner_tol=vwl.get("inner_tol"),
@@ -347,6 +359,34 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
         })
     for hh in hs:
         hh.destroy()
+    return out
+
+
+def _measure_sequence(M, name, vwl, systems, dev, stream, barrier, ws):
+    """One handle (built for n_max) solves the right-hand sides in order,
+    first with n chosen by mlbicgstab_solve_sequence, then at fixed n0."""
+    import torch
+    A = systems[0][0]
+    h = M.mlbicgstab_create(A, n=vwl["n"], q_seed=0, max_outer=10, stream=stream)
+    bs = [torch.tensor(b, dtype=torch.float64, device=dev) for _, _, b in systems]
+    count = len(bs)
+    out = {"workload": name, "config": _variant_desc(name, vwl, systems), "precision": "fp64",
+           "n": vwl["n0"], "unit": UNIT}
+    for label, step in (("adaptive", vwl["step"]), ("fixed_n0", 0)):
+        xs = [torch.zeros_like(b) for b in bs]
+        barrier()
+        t0 = time.perf_counter()
+        res, used = M.mlbicgstab_solve_sequence([h] * count, bs, xs, [vwl["tol"]] * count, [vwl["maxit"]] * count,
+                                                n0=vwl["n0"], step=step, n_min=vwl["n_min"], n_max=vwl["n_max"])
+        barrier()
+        secs = time.perf_counter() - t0
+        out[label] = {"value": ws * count / secs, "seconds": secs, "n_used": used,
+                      "iters": [r.iter for r in res], "flags": sorted({r.flag for r in res}),
+                      "true_relres_max": max(r.true_relres for r in res)}
+    out["value"] = out["adaptive"]["value"]
+    out["ms_per_step"] = 1e3 * out["adaptive"]["seconds"] / count
+    out["speedup_vs_fixed_n0"] = out["adaptive"]["value"] / out["fixed_n0"]["value"]
+    h.destroy()
     return out
 
 

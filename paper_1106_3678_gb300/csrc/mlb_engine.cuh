@@ -639,7 +639,9 @@ struct Engine {
         T *g0 = Gc(0);
         const T *epi[2] = {sys.b, q1};
         T *const r = sys.r;
-        spmv_rows<K>(sys.x, epi, [&](int64_t row, T y, const T (&e)[2], ACC(&a)[K]) {
+        // epilogues capture by value: a captured reference would keep the
+        // pointer in memory, reloaded after every store of the loop
+        spmv_rows<K>(sys.x, epi, [=](int64_t row, T y, const T (&e)[2], ACC(&a)[K]) {
             T rv = subT(e[0], y);
             r[row] = rv;
             if (write_g0) g0[row] = rv;
@@ -722,7 +724,7 @@ struct Engine {
         const T *q = Qc(qcol);
         T *w = Wc(sl);
         const T *epi[1] = {q};
-        spmv_rows<K>(Gc(sl), epi, [&](int64_t row, T y, const T (&e)[1], ACC(&a)[K]) {
+        spmv_rows<K>(Gc(sl), epi, [=](int64_t row, T y, const T (&e)[1], ACC(&a)[K]) {
             w[row] = y;
             acc_dot(&a[0], e[0], y);
         }, acc);
@@ -743,7 +745,7 @@ struct Engine {
         for (int k = 0; k < K; ++k) acc[k] = ACC(0);
         const T *epi[1] = {sys.r};
         T *const z = sys.z;
-        spmv_rows<K>(sys.r, epi, [&](int64_t row, T y, const T (&e)[1], ACC(&a)[K]) {
+        spmv_rows<K>(sys.r, epi, [=](int64_t row, T y, const T (&e)[1], ACC(&a)[K]) {
             z[row] = y;
             acc_nrm(&a[0], y);
             acc_dot(&a[1], y, e[0]);

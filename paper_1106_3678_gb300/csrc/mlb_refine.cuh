@@ -59,7 +59,7 @@ struct Refiner {
         unsigned sq = gs.seq();   // issued (producer lane) or consumed (consumers) tiles
         bool okt = sell_spmv<1>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, v.spt[1], v.slice_ptr, v.scol, v.sval,
                                 v.x, epi, threadIdx.x & 31,
-                                [&](int64_t row, T64 y, const T64 (&e)[1], double(&a)[2]) {
+                                [=](int64_t row, T64 y, const T64 (&e)[1], double(&a)[2]) {
                                     T64 rv = subT(e[0], y);
                                     r[row] = rv;
                                     acc_nrm(&a[0], e[0]);
