@@ -60,6 +60,8 @@ WORKLOADS = {
                                    precond=1),
     "reservoir_n8_fp64": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0),
     "batch512_n4_fp64": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0),
+    # the autotuner on a mid-size system (default configuration vs tuned)
+    "tune_cd2d256": dict(kind="tune", m=256, n=4, tol=1e-10, maxit=40000, precision=0),
     # a sequence of right-hand sides with n chosen by the rule of §5
     # (n0 = 4, step 2, n in [1, 16]) against the same sequence at fixed n = 4
     "sequence8_cd3d64": dict(kind="sequence", m=64, n=16, count=8, n0=4, step=2, n_min=1, n_max=16,
@@ -80,7 +82,7 @@ DEFAULT = "cd3d128_n4_fp64"
 # captured again.
 NCU_DRAM_BYTES_PER_ITER = (136.79e9 + 34.50e9) / 300
 VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07",
-            "sequence8_cd3d64", "cd3d128_n4_refined"]
+            "sequence8_cd3d64", "tune_cd2d256", "cd3d128_n4_refined"]
 
 
 def _load_peaks():
@@ -115,6 +117,9 @@ def _make_variant_inputs(wl):
         return [(A, None, W.row_sums(A))]
     if kind == "batch":
         return [(A, None, W.row_sums(A)) for A, _ in W.batch_cd(512, seed=5)]
+    if kind == "tune":
+        A = W.cd2d(wl["m"])
+        return [(A, None, W.row_sums(A))]
     if kind == "sequence":
         A = W.cd3d_lognormal(wl["m"])
         return [(A, None, W.uniform_rhs(A.n_rows, seed=10 + k)) for k in range(wl["count"])]
@@ -128,6 +133,7 @@ def _variant_desc(name, wl, systems):
             "helmholtz": "complex damped shifted Laplacian 256x256x64, A^H as separate CSR",
             "reservoir": "3x3-block reservoir system 64x64x32 cells",
             "batch": "512 2-D/3-D convection-diffusion systems, N ~ logU[1e3,1e5], one launch",
+            "tune": f"2-D 5-point convection-diffusion {wl.get('m', 0)}^2, default launch configuration vs autotuned",
             "sequence": (f"sequence of {wl.get('count', 0)} right-hand sides U[-1,1] (seeds 10..) on the 3-D "
                          f"log-normal convection-diffusion {wl.get('m', 0)}^3 system, n by the rule of §5 "
                          f"(n0={wl.get('n0')}, step {wl.get('step')}, n in [{wl.get('n_min')}, {wl.get('n_max')}])")}[wl["kind"]]
@@ -301,6 +307,8 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
     systems = _make_variant_inputs(vwl)
     if vwl["kind"] == "sequence":
         return _measure_sequence(M, name, vwl, systems, dev, stream, barrier, ws)
+    if vwl["kind"] == "tune":
+        return _measure_tune(M, name, vwl, systems, dev, stream, barrier, ws, args)
     dt = torch.complex128 if np.iscomplexobj(systems[0][2]) else torch.float64
     hs = [M.mlbicgstab_create(A, AH=AH, n=vwl["n"], q_seed=0, max_outer=10, stream=stream,
                               precision=vwl.get("precision", 0), inner_tol=vwl.get("inner_tol"),
@@ -362,6 +370,33 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
     return out
 
 
+def _measure_tune(M, name, vwl, systems, dev, stream, barrier, ws, args):
+    """The same solve with the default launch configuration, then after
+    mlbicgstab_autotune (tuning itself is setup and not timed)."""
+    import torch
+    A, _, b = systems[0]
+    h = M.mlbicgstab_create(A, n=vwl["n"], q_seed=0, max_outer=10, stream=stream)
+    bd = torch.tensor(b, dtype=torch.float64, device=dev)
+    xd = torch.zeros_like(bd)
+    steps = max(1, args.variant_steps)
+    out = {"workload": name, "config": _variant_desc(name, vwl, systems), "precision": "fp64",
+           "n": vwl["n"], "unit": UNIT}
+    ms0, r0 = _timed_solves(M, h, bd, xd, vwl, stream, steps, 1, barrier)
+    grid0 = M.mlbicgstab_info(h)["grid"]
+    tune = M.mlbicgstab_autotune(h, iters=30, use_cache=False)
+    ms1, r1 = _timed_solves(M, h, bd, xd, vwl, stream, steps, 1, barrier)
+    out["default"] = {"value": ws * steps / (ms0 * 1e-3), "grid": grid0, "spt_cap": 15,
+                      "iters": [r["iter"] for r in r0]}
+    out["tuned"] = {"value": ws * steps / (ms1 * 1e-3), "grid": tune["grid"], "spt_cap": tune["spt_cap"],
+                    "iters": [r["iter"] for r in r1], "trials": tune["trials"]}
+    out["value"] = out["tuned"]["value"]
+    out["ms_per_step"] = ms1 / steps
+    out["flags"] = sorted({r["flag"] for r in r0 + r1})
+    out["speedup_vs_default"] = out["tuned"]["value"] / out["default"]["value"]
+    h.destroy()
+    return out
+
+
 def _measure_sequence(M, name, vwl, systems, dev, stream, barrier, ws):
     """One handle (built for n_max) solves the right-hand sides in order,
     first with n chosen by mlbicgstab_solve_sequence, then at fixed n0."""
@@ -407,6 +442,7 @@ def run_ours(args, wl):
     N = A.n_rows
     stream = torch.cuda.Stream()
     h = _create(M, A, wl, stream)
+    tune = M.mlbicgstab_autotune(h, iters=20, use_cache=False)   # setup, like create: not timed
     info = M.mlbicgstab_info(h)
     b_d = torch.tensor(b, dtype=torch.float64, device=dev)
     x_d = torch.zeros(N, dtype=torch.float64, device=dev)
@@ -488,7 +524,9 @@ def run_ours(args, wl):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": _config(wl, A, {"grid": info["grid"], "block": info["block"],
-                                  "nnz_sell32": info["nnz_padded"]}),
+                                  "nnz_sell32": info["nnz_padded"],
+                                  "autotune": {k: tune[k] for k in ("grid", "spt_cap", "us_per_iter",
+                                                                    "default_us_per_iter", "trials")}}),
         "iters_per_solve": iters, "flags": [r["flag"] for r in results],
         "true_relres": [r["true_relres"] for r in results],
         "restarts": [r["outer"] for r in results],

@@ -149,6 +149,16 @@ typedef struct {
     int32_t reserved1;
 } mlb_info;
 
+/* Result of mlbicgstab_autotune. */
+typedef struct {
+    int32_t grid;         /* CTAs of the persistent solve kernel chosen */
+    int32_t spt_cap;      /* cap on 32-row slices per SpMV tile chosen */
+    double us_per_iter;   /* device time per iteration with the choice */
+    double default_us_per_iter; /* the same before tuning */
+    int32_t trials;       /* configurations timed (0 when from the cache) */
+    int32_t from_cache;   /* 1: taken from the process-wide cache */
+} mlb_tune_result;
+
 /* Parameters of mlbicgstab_solve_sequence (automatic choice of n, §5). */
 typedef struct {
     int32_t n0;           /* n for the first two systems */
@@ -245,6 +255,23 @@ int mlbicgstab_solve_sequence(mlb_handle *const *hs, int32_t count,
                               const int64_t *maxit,
                               const mlb_sequence_options *so,
                               mlb_result *res, int32_t *n_used);
+
+/*
+ * Autotuner (performance only; the paper has no counterpart).  Times
+ * `iters` iterations of A x = 1 from x = 0 (host buffers, tol 0) for each
+ * candidate configuration: CTA counts want, want/2, want/4, want/8 (want =
+ * the CTAs that give each at least 512 16-byte chunks, at most all SMs)
+ * and the current one, times slice caps 15, 12, 8, 4 per SpMV tile (rows
+ * per tile = 32 x slices); keeps the fastest in the handle (later solves
+ * and batches use it) and caches it for the process per (dtype,
+ * precision, preconditioner, floor(log2 N), round(nnz/N)).  use_cache = 1
+ * takes a cached choice without timing.  Later results change only in
+ * rounding (reduction trees follow the CTA count).  Overwrites the
+ * handle's device work buffers; blocks until done; MLB_ERR_ARG for iters
+ * outside [1, 100000].
+ */
+int mlbicgstab_autotune(mlb_handle *h, int32_t iters, int32_t use_cache,
+                        mlb_tune_result *out);
 
 /*
  * Fused hot operation: y = A x and d = Q^H y (all n shadow inner products,

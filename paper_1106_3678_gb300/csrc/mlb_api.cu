@@ -3,11 +3,14 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
-#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mlbicgstab.h"
@@ -27,6 +30,9 @@ struct mlb_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     int grid = 1;
+    int grid_max = 1;       // largest co-resident grid of the solve kernel
+    int grid_want = 1;      // CTAs that give every CTA at least 512 chunks
+    int spt_cap = kConsumerWarps;   // cap on slices per SpMV tile (autotuner)
     uint64_t timeout_ns = 2000000000ull;
     double kappa = 0.0;
     int max_outer = 10;
@@ -162,8 +168,8 @@ int slices_per_tile(int64_t maxw, size_t vbytes, int nepi) {
     if (spt > kConsumerWarps) spt = kConsumerWarps;
     return (int)spt;
 }
-void set_spt(int (&spt)[3], int64_t maxw, size_t vbytes) {
-    for (int e = 0; e < 3; ++e) spt[e] = slices_per_tile(maxw, vbytes, e);
+void set_spt(int (&spt)[3], int64_t maxw, size_t vbytes, int cap) {
+    for (int e = 0; e < 3; ++e) spt[e] = std::min(slices_per_tile(maxw, vbytes, e), cap);
 }
 
 // A^H in CSR by a stable counting sort over columns (values conjugated for
@@ -201,7 +207,7 @@ SysView<T> make_view(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T *)h->sval;
-    set_spt(v.spt, h->maxw, sizeof(T));
+    set_spt(v.spt, h->maxw, sizeof(T), h->spt_cap);
     v.Q = (const T *)h->Q;
     v.F = (const T *)h->F;
     v.G = (T *)h->G;
@@ -224,7 +230,7 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T32 *)h->sval32;
-    set_spt(v.spt, h->maxw, sizeof(T32));
+    set_spt(v.spt, h->maxw, sizeof(T32), h->spt_cap);
     v.Q = (const T32 *)h->Q32;
     v.F = (const T32 *)h->F32;
     v.G = (T32 *)h->G32;
@@ -247,7 +253,7 @@ RefView<T64> make_ref_view(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T64 *)h->sval;
-    set_spt(v.spt, h->maxw, sizeof(T64));
+    set_spt(v.spt, h->maxw, sizeof(T64), h->spt_cap);
     v.x = (T64 *)h->x;
     v.b = (const T64 *)h->b;
     v.r = (T64 *)h->r;
@@ -488,6 +494,8 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     int grid = (int)std::min<int64_t>(want, maxg);
     if (o->grid > 0) grid = std::min(o->grid, maxg);
     h->grid = std::max(grid, 1);
+    h->grid_max = std::max(maxg, 1);
+    h->grid_want = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxg));
     if ((rc = dev_alloc_t(h, &h->partials, (size_t)2 * maxg * kMaxSums * 8))) return rc;
     if ((rc = dev_alloc_t(h, &h->bar, sizeof(BarrierState)))) return rc;
     if ((rc = dev_alloc_t(h, &h->dres, sizeof(DevResult)))) return rc;
@@ -852,6 +860,100 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
         if (d.status != 0) rc = MLB_ERR_TIMEOUT;
     }
     return rc;
+}
+
+// Autotuner: CTA count and slices per SpMV tile, chosen by timing short
+// fixed-length solves on the handle's own matrix; the choice is cached per
+// (dtype, precision, preconditioner, floor(log2 N), round(nnz/N)).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int64_t>, std::pair<int, int>> g_tune_cache;
+
+// Device time per iteration of `iters` iterations of A x = 1 from x = 0
+// (tol 0, so exactly `iters` steps unless a breakdown ends it earlier);
+// the better of two runs.
+static int time_config(mlb_handle *h, int32_t iters, std::vector<char> &bh, std::vector<char> &xh, double &us) {
+    mlb_result r;
+    double best = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+        std::fill(xh.begin(), xh.end(), 0);
+        const int rc = mlbicgstab_solve(h, bh.data(), xh.data(), 0, 0.0, iters, &r, nullptr, 0);
+        if (rc != MLB_OK) return rc;
+        if (r.iter > 0) best = std::min(best, 1e3 * r.kernel_ms / (double)r.iter);
+    }
+    us = best;
+    return MLB_OK;
+}
+
+int mlbicgstab_autotune(mlb_handle *h, int32_t iters, int32_t use_cache, mlb_tune_result *out) {
+    if (!h || !out || iters < 1 || iters > 100000 || (use_cache != 0 && use_cache != 1)) return MLB_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    int lg = 0;
+    for (int64_t v = h->N; v > 1; v >>= 1) ++lg;
+    const auto key = std::make_tuple(h->dtype, h->precision, h->precond, lg,
+                                     (int64_t)((double)h->nnz / (double)std::max<int64_t>(h->N, 1) + 0.5));
+    if (use_cache) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->grid = std::max(1, std::min(it->second.first, h->grid_max));
+            h->spt_cap = std::max(1, std::min(it->second.second, (int)kConsumerWarps));
+            out->grid = h->grid;
+            out->spt_cap = h->spt_cap;
+            out->from_cache = 1;
+            return MLB_OK;
+        }
+    }
+    // right-hand side of ones and a zero start, in host memory
+    std::vector<char> bh((size_t)h->N * h->esize, 0), xh((size_t)h->N * h->esize, 0);
+    const double one = 1.0;
+    for (int64_t i = 0; i < h->N; ++i) memcpy(&bh[(size_t)i * h->esize], &one, sizeof(one));
+    const int g0 = h->grid, s0 = h->spt_cap;
+    std::vector<int> grids, spts;
+    grids.push_back(g0);
+    for (int d = 1; d <= 8; d *= 2) {
+        const int g = std::max(1, h->grid_want / d);
+        if (std::find(grids.begin(), grids.end(), g) == grids.end()) grids.push_back(g);
+    }
+    spts.push_back(s0);
+    for (int c : {(int)kConsumerWarps, 12, 8, 4})
+        if (std::find(spts.begin(), spts.end(), c) == spts.end()) spts.push_back(c);
+    double def_us = 0.0;
+    int rc = time_config(h, iters, bh, xh, def_us);
+    if (rc) return rc;
+    int best_g = g0, best_s = s0;
+    double best_us = def_us;
+    int trials = 1;
+    for (int g : grids)
+        for (int sc : spts) {
+            if (g == g0 && sc == s0) continue;
+            h->grid = g;
+            h->spt_cap = sc;
+            double us = 0.0;
+            rc = time_config(h, iters, bh, xh, us);
+            ++trials;
+            if (rc) {
+                h->grid = g0;
+                h->spt_cap = s0;
+                return rc;
+            }
+            if (us < best_us) {
+                best_us = us;
+                best_g = g;
+                best_s = sc;
+            }
+        }
+    h->grid = best_g;
+    h->spt_cap = best_s;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {best_g, best_s};
+    }
+    out->grid = best_g;
+    out->spt_cap = best_s;
+    out->us_per_iter = best_us;
+    out->default_us_per_iter = def_us;
+    out->trials = trials;
+    return MLB_OK;
 }
 
 int mlbicgstab_set_n(mlb_handle *h, int32_t n) {

@@ -29,6 +29,7 @@ EXPORTS = (
     "mlbicgstab_info", "mlbicgstab_destroy", "mlbicgstab_strerror",
     "mlbicgstab_selftest_barrier_timeout", "mlbicgstab_spmv_qdot_noalloc",
     "mlbicgstab_set_n", "mlbicgstab_next_n", "mlbicgstab_solve_sequence",
+    "mlbicgstab_autotune",
 )
 
 
@@ -71,6 +72,11 @@ class mlb_info(C.Structure):
                 ("precond", C.c_int32), ("nnz_padded", C.c_int64),
                 ("device_bytes", C.c_int64), ("n_active", C.c_int32),
                 ("reserved1", C.c_int32)]
+
+
+class mlb_tune_result(C.Structure):
+    _fields_ = [("grid", C.c_int32), ("spt_cap", C.c_int32), ("us_per_iter", C.c_double),
+                ("default_us_per_iter", C.c_double), ("trials", C.c_int32), ("from_cache", C.c_int32)]
 
 
 class mlb_sequence_options(C.Structure):
@@ -131,6 +137,8 @@ def load(path: str | None = None):
     lib.mlbicgstab_solve_sequence.argtypes = [P, C.c_int32, P, P, C.c_int32, P, P,
                                               C.POINTER(mlb_sequence_options),
                                               C.POINTER(mlb_result), P]
+    lib.mlbicgstab_autotune.restype = C.c_int
+    lib.mlbicgstab_autotune.argtypes = [P, C.c_int32, C.c_int32, C.POINTER(mlb_tune_result)]
     lib.mlbicgstab_spmv_qdot_noalloc.restype = C.c_int
     lib.mlbicgstab_spmv_qdot_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, C.c_int32,
                                                  P, P, C.c_int64, C.c_int32, P, P, P]
@@ -332,6 +340,14 @@ def mlbicgstab_solve_sequence(hs, bs, xs, tols, maxits, n0: int, step: int, n_mi
                                           C.byref(so), res, used.ctypes.data)
     _check(rc, "mlbicgstab_solve_sequence")
     return list(res), [int(v) for v in used]
+
+
+def mlbicgstab_autotune(h: Handle, iters: int = 20, use_cache: bool = True) -> dict:
+    """Choose the CTA count and SpMV tile size of a handle by timing."""
+    r = mlb_tune_result()
+    _check(load().mlbicgstab_autotune(h.ptr, int(iters), 1 if use_cache else 0, C.byref(r)),
+           "mlbicgstab_autotune")
+    return {f: getattr(r, f) for f, _ in r._fields_}
 
 
 def mlbicgstab_spmv_qdot(h: Handle, x, y) -> np.ndarray:

@@ -50,8 +50,8 @@ def test_struct_layout_matches_c_compiler(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(mlb_matrix), sizeof(mlb_options),
-         sizeof(mlb_result), sizeof(mlb_info), sizeof(mlb_sequence_options));
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mlb_matrix), sizeof(mlb_options),
+         sizeof(mlb_result), sizeof(mlb_info), sizeof(mlb_sequence_options), sizeof(mlb_tune_result));
   printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(mlb_options, stream),
          offsetof(mlb_options, timeout_ns), offsetof(mlb_result, ops),
          offsetof(mlb_options, precond), offsetof(mlb_info, precond),
@@ -64,7 +64,8 @@ int main(void) {{
                                  text=True).stdout.split("\n")[:2]
     assert [int(v) for v in sizes.split()] == [
         C.sizeof(M.mlb_matrix), C.sizeof(M.mlb_options),
-        C.sizeof(M.mlb_result), C.sizeof(M.mlb_info), C.sizeof(M.mlb_sequence_options)]
+        C.sizeof(M.mlb_result), C.sizeof(M.mlb_info), C.sizeof(M.mlb_sequence_options),
+        C.sizeof(M.mlb_tune_result)]
     assert [int(v) for v in offs.split()] == [
         M.mlb_options.stream.offset, M.mlb_options.timeout_ns.offset,
         M.mlb_result.ops.offset, M.mlb_options.precond.offset,
@@ -173,3 +174,10 @@ def test_sequence_and_set_n_validate_before_gpu(lib):
     p = (C.c_void_p * 1)(1)
     assert lib.mlbicgstab_solve_sequence(hs, 1, p, p, 0, t, m, C.byref(bad), res, used) == M.MLB_ERR_ARG
     assert lib.mlbicgstab_set_n(None, 2) == M.MLB_ERR_ARG
+
+
+def test_autotune_validates_before_gpu(lib):
+    r = M.mlb_tune_result()
+    assert lib.mlbicgstab_autotune(None, 20, 1, C.byref(r)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune(C.c_void_p(1), 0, 1, C.byref(r)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune(C.c_void_p(1), 20, 2, C.byref(r)) == M.MLB_ERR_ARG
