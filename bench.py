@@ -68,6 +68,9 @@ WORKLOADS = {
                              tol=1e-10, maxit=40000, precision=0),
     "batch512_n4_refined": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=1,
                                 inner_tol=1e-4),
+    # the fused product y = A x, d = Q^H y alone (mlbicgstab_spmv_qdot) on
+    # the headline matrix, for n = 1, 4, 16 shadow vectors
+    "spmv_qdot_cd3d128": dict(kind="spmv_qdot", m=128, n=4, ns=(1, 4, 16), calls=50),
 }
 for _n in (1, 8, 16):
     WORKLOADS[f"cd3d128_n{_n}_fp64"] = dict(kind="cd3d", m=128, n=_n, tol=1e-10, maxit=60000,
@@ -81,8 +84,8 @@ DEFAULT = "cd3d128_n4_fp64"
 # iteration count.  Set to None whenever the kernel changes until it is
 # captured again.
 NCU_DRAM_BYTES_PER_ITER = (136.79e9 + 34.50e9) / 300
-VARIANTS = ["batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07",
-            "sequence8_cd3d64", "tune_cd2d256", "cd3d128_n4_refined"]
+VARIANTS = ["spmv_qdot_cd3d128", "batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128",
+            "helmholtz_n8_c128_kappa07", "sequence8_cd3d64", "tune_cd2d256", "cd3d128_n4_refined"]
 
 
 def _load_peaks():
@@ -123,12 +126,18 @@ def _make_variant_inputs(wl):
     if kind == "sequence":
         A = W.cd3d_lognormal(wl["m"])
         return [(A, None, W.uniform_rhs(A.n_rows, seed=10 + k)) for k in range(wl["count"])]
+    if kind == "spmv_qdot":
+        A = W.cd3d_lognormal(wl["m"])
+        return [(A, None, W.uniform_rhs(A.n_rows, seed=3))]
     raise ValueError(kind)
 
 
 def _variant_desc(name, wl, systems):
     N = sum(A.n_rows for A, _, _ in systems)
     nnz = sum(A.nnz for A, _, _ in systems)
+    if wl["kind"] == "spmv_qdot":
+        return (f"fused y = A x, d = Q^H y on the 3-D log-normal convection-diffusion {wl['m']}^3 matrix "
+                f"(N={N:,}, nnz={nnz:,}), n in {list(wl['ns'])}, x U[-1,1], fp64, {wl['calls']} calls each")
     what = {"cd3d": "3-D log-normal convection-diffusion 128^3",
             "helmholtz": "complex damped shifted Laplacian 256x256x64, A^H as separate CSR",
             "reservoir": "3x3-block reservoir system 64x64x32 cells",
@@ -309,6 +318,8 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
         return _measure_sequence(M, name, vwl, systems, dev, stream, barrier, ws)
     if vwl["kind"] == "tune":
         return _measure_tune(M, name, vwl, systems, dev, stream, barrier, ws, args)
+    if vwl["kind"] == "spmv_qdot":
+        return _measure_spmv_qdot(M, name, vwl, systems, dev, stream, barrier, ws)
     dt = torch.complex128 if np.iscomplexobj(systems[0][2]) else torch.float64
     hs = [M.mlbicgstab_create(A, AH=AH, n=vwl["n"], q_seed=0, max_outer=10, stream=stream,
                               precision=vwl.get("precision", 0), inner_tol=vwl.get("inner_tol"),
@@ -367,6 +378,49 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
         })
     for hh in hs:
         hh.destroy()
+    return out
+
+
+def _measure_spmv_qdot(M, name, vwl, systems, dev, stream, barrier, ws):
+    """The fused product alone: device time of each launch (events inside
+    the library around the kernel), and the whole call (launch, copy of d
+    to the host, synchronisation).  The inputs (about 230-500 MB) exceed
+    L2, so no flush between calls.  Algorithmic bytes: A's SELL values and
+    columns and slice offsets once, x once, y written once, the n columns
+    of Q once."""
+    import torch
+    A, _, b = systems[0]
+    N = A.n_rows
+    peak, peak_kind = _load_peaks()
+    x = torch.tensor(b, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    out = {"workload": name, "config": _variant_desc(name, vwl, systems), "precision": "fp64",
+           "n": vwl["n"], "unit": "products/s", "by_n": {}}
+    for n in vwl["ns"]:
+        h = M.mlbicgstab_create(A, n=n, q_seed=0, stream=stream)
+        info = M.mlbicgstab_info(h)
+        byts = info["nnz_padded"] * 12 + 8 * (N // 32 + 2) + 8 * N * (2 + n)
+        for _ in range(3):
+            M.mlbicgstab_spmv_qdot(h, x, y)
+        barrier()
+        kms = []
+        t0 = time.perf_counter()
+        for _ in range(vwl["calls"]):
+            M.mlbicgstab_spmv_qdot(h, x, y)
+            kms.append(M.mlbicgstab_info(h)["qd_kernel_ms"])
+        call = (time.perf_counter() - t0) / vwl["calls"]
+        barrier()
+        k = float(np.mean(kms)) * 1e-3
+        gbs = byts / k / 1e9
+        out["by_n"][str(n)] = {"kernel_us": k * 1e6, "kernel_us_min": min(kms) * 1e3,
+                               "call_us": call * 1e6, "algorithmic_bytes": byts,
+                               "achieved_gbs": gbs, "frac_of_" + peak_kind + "_hbm": gbs / peak}
+        h.destroy()
+    main = out["by_n"][str(vwl["n"])]
+    out["value"] = ws * 1e6 / main["kernel_us"]
+    out["ms_per_step"] = main["kernel_us"] * 1e-3
+    out["roofline"] = {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                       "frac": main["achieved_gbs"] / peak, "peak_kind": peak_kind}
     return out
 
 

@@ -147,6 +147,9 @@ typedef struct {
     int64_t device_bytes; /* device memory held by the handle */
     int32_t n_active;     /* shadow vectors the next solve uses (<= n) */
     int32_t reserved1;
+    double qd_kernel_ms;  /* device time of the last mlbicgstab_spmv_qdot
+                             (CUDA events around its launch on the handle's
+                             stream); 0 before the first call */
 } mlb_info;
 
 /* Result of mlbicgstab_autotune. */
@@ -277,8 +280,10 @@ int mlbicgstab_autotune(mlb_handle *h, int32_t iters, int32_t use_cache,
  * Fused hot operation: y = A x and d = Q^H y (all n shadow inner products,
  * a tall-skinny block reduction) in one pass over A — the per-iteration
  * product w = A g with c = q^H w of Algorithm 4.1 (step 32) generalised to
- * every q.  x, y: device arrays of N values; d: host array of n values.
+ * every q.  x, y: device arrays of N values; d: host array of n_active
+ * values (the handle's n unless mlbicgstab_set_n chose fewer columns).
  * Reductions are deterministic (fixed order).  Blocks until d is ready.
+ * MLB_ERR_TIMEOUT if a wait inside the kernel gave up (y and d invalid).
  */
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d);
 /* (MLB_ERR_UNSUPPORTED for a handle with a preconditioner: it stores

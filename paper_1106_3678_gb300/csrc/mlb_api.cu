@@ -57,6 +57,10 @@ struct mlb_handle {
     int64_t err_cap = 0;
     double *qd_partials = nullptr;
     double *qd_out = nullptr;
+    int *qd_status = nullptr;     // one slot per CTA of the fused product
+    unsigned *qd_ticket = nullptr;  // last-CTA counter, 0 between launches
+    double qd_ms = 0.0;           // device time of the last fused product
+    double *qd_host = nullptr;    // pinned copy of qd_out
     int qd_grid = 0;
     DevResult *hres = nullptr;  // pinned
     // batch workspace (owned by the first handle of a batch call)
@@ -500,8 +504,16 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     if ((rc = dev_alloc_t(h, &h->bar, sizeof(BarrierState)))) return rc;
     if ((rc = dev_alloc_t(h, &h->dres, sizeof(DevResult)))) return rc;
     h->qd_grid = cplx ? spmv_qdot_grid<cdouble>() : spmv_qdot_grid<double>();
-    if ((rc = dev_alloc_t(h, &h->qd_partials, (size_t)h->qd_grid * kQdMaxN * 2 * 8))) return rc;
-    if ((rc = dev_alloc_t(h, &h->qd_out, (size_t)kQdMaxN * 2 * 8))) return rc;
+    if ((rc = dev_alloc_t(h, &h->qd_partials, (size_t)std::max(h->qd_grid, maxg) * kQdMaxN * 2 * 8))) return rc;
+    if ((rc = dev_alloc_t(h, &h->qd_out, (size_t)(kQdMaxN * 2 + 1) * 8))) return rc;
+    if ((rc = dev_alloc_t(h, &h->qd_status, (size_t)std::max(h->qd_grid, maxg) * sizeof(int)))) return rc;
+    if ((rc = dev_alloc_t(h, &h->qd_ticket, sizeof(unsigned)))) return rc;
+    MLB_CUDA(cudaMemsetAsync(h->qd_ticket, 0, sizeof(unsigned), st));
+    if (cudaMallocHost(&h->qd_host, (size_t)(kQdMaxN * 2 + 1) * 8) != cudaSuccess) {
+        cudaGetLastError();
+        h->qd_host = nullptr;
+        return MLB_ERR_OOM;
+    }
     if (cudaMallocHost(&h->hres, sizeof(DevResult)) != cudaSuccess) {
         cudaGetLastError();
         h->hres = nullptr;
@@ -519,6 +531,7 @@ void release(mlb_handle *h) {
     h->allocs.clear();
     if (h->err_hist) cudaFree(h->err_hist);
     if (h->hres) cudaFreeHost(h->hres);
+    if (h->qd_host) cudaFreeHost(h->qd_host);
     if (h->bws) cudaFree(h->bws);
     if (h->bhost) cudaFreeHost(h->bhost);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -614,6 +627,7 @@ int mlbicgstab_info(const mlb_handle *h, mlb_info *info) {
     info->block = kThreads;
     info->nnz_padded = h->nnz_pad;
     info->device_bytes = h->device_bytes;
+    info->qd_kernel_ms = h->qd_ms;
     return MLB_OK;
 }
 
@@ -1008,24 +1022,35 @@ int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
     if (!is_device_ptr(x) || !is_device_ptr(y)) return MLB_ERR_ARG;
     cudaStream_t st = h->stream;
     cudaError_t e;
-    // x is read through the padded internal buffer so that every gather
-    // stays inside an allocation of ld entries
-    const size_t nb = (size_t)h->N * h->esize;
-    MLB_CUDA(cudaMemcpyAsync(h->b, x, nb, cudaMemcpyDeviceToDevice, st));
-    if (h->dtype == MLB_C128)
-        e = launch_spmv_qdot<cdouble>(make_view<cdouble>(h), (const cdouble *)h->b, (cdouble *)h->r,
-                                      h->qd_partials, h->qd_grid, h->qd_out, st);
+    // x is gathered from the caller's array (SELL padding columns are
+    // clamped below N); y goes to the caller's array and to the handle's
+    // padded buffer r, which the inner products stream back
+    const int grid = std::max(1, std::min(h->grid_want, h->grid_max));
+    // tiles of the product carry the fused columns of Q as epilogue vectors
+    const bool cplx = h->dtype == MLB_C128;
+    const int spt = std::min(slices_per_tile(h->maxw, h->esize, qd_fused_columns(h->n_active, cplx)), h->spt_cap);
+    if (cplx)
+        e = launch_spmv_qdot_tiled<cdouble>(make_view<cdouble>(h), spt, (const cdouble *)x, (cdouble *)h->r,
+                                            (cdouble *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket,
+                                            h->qd_out, h->ev0, st);
     else
-        e = launch_spmv_qdot<double>(make_view<double>(h), (const double *)h->b, (double *)h->r,
-                                     h->qd_partials, h->qd_grid, h->qd_out, st);
+        e = launch_spmv_qdot_tiled<double>(make_view<double>(h), spt, (const double *)x, (double *)h->r,
+                                           (double *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket,
+                                           h->qd_out, h->ev0, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return MLB_ERR_CUDA;
     }
-    MLB_CUDA(cudaMemcpyAsync(y, h->r, nb, cudaMemcpyDeviceToDevice, st));
-    MLB_CUDA(cudaMemcpyAsync(d, h->qd_out, (size_t)h->n * (h->dtype == MLB_C128 ? 16 : 8),
-                             cudaMemcpyDeviceToHost, st));
+    MLB_CUDA(cudaEventRecord(h->ev1, st));
+    // d and the status flag behind it in one copy, through pinned memory
+    const size_t nv = (size_t)h->n_active * (cplx ? 2 : 1);
+    MLB_CUDA(cudaMemcpyAsync(h->qd_host, h->qd_out, (nv + 1) * 8, cudaMemcpyDeviceToHost, st));
     MLB_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->qd_ms = ms;
+    cudaGetLastError();
+    if (h->qd_host[nv] != 0.0) return MLB_ERR_TIMEOUT;
+    memcpy(d, h->qd_host, nv * 8);
     return MLB_OK;
 }
 

@@ -71,6 +71,23 @@ cudaError_t launch_ahq(const int64_t *rp, const int32_t *ci, const T *av,
 // Fused y = A x, d = Q^H y.  `partials` holds grid * kQdMaxN * 2 doubles;
 // d (device) receives n values (2n doubles for complex).
 constexpr int kQdMaxN = 64;
+// Tiled form: one CTA of kThreads per SM (grid <= the handle's grid_max),
+// dynamic shared memory kRingBytes.  The first qd_fused_columns(n, .) columns
+// of Q are epilogue vectors of the SELL product, whose tiles hold `spt`
+// slices (sized for that many epilogue vectors); the others take tile
+// passes over y.  x: the caller's N values (SELL padding columns stay below
+// N); y: a padded scratch vector of ld values; yout: the caller's N values.
+// status: one int per CTA (written every launch, nonzero where a tile wait
+// timed out); ticket: a counter that is 0 between launches (zero it once
+// at allocation); d (device) receives the n inner products (2n doubles for
+// complex) and then d[n * DS] = 1.0 if any CTA timed out, else 0.0.
+// ev (optional) is recorded on st directly before the kernel launch.
+// Fused columns: at most 2 for complex values (4 spill registers).
+inline int qd_fused_columns(int n, bool cplx) { return n >= 4 && !cplx ? 4 : (n >= 2 ? 2 : 1); }
+template <typename T>
+cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
+                                   int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
+                                   cudaStream_t st);
 constexpr int kQdThreads = 256;
 template <typename T>
 cudaError_t launch_spmv_qdot(const SysView<T> &sys, const T *x, T *y,

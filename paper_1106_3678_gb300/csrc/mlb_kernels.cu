@@ -536,6 +536,161 @@ __global__ void qdot_finish_kernel(const double *partials, int grid, int n, doub
     }
 }
 
+// Tiled form (the library's entry point): one CTA per SM, each owning a
+// contiguous slice range.  The first NE columns of Q ride through the
+// engine's TMA-fed SELL product as epilogue vectors, so their inner
+// products are taken as each row of y is formed (FP64 arithmetic is scarce
+// on this GPU: the dot products then share the product's pass instead of
+// following it).  Columns beyond NE take further tile passes over the
+// CTA's rows of y (written by the first pass) and up to G columns of Q at
+// a time.  Every pass touches only the CTA's rows, so no grid barrier is
+// needed.  Per-CTA sums go to `partials` in fixed order.
+//
+// A timed-out wait makes the CTA stop at the next pass boundary (decided
+// CTA-wide with __syncthreads_or, so every thread takes the same barriers)
+// and set its `status` slot.
+
+// CTA sums of the first nv (<= NV) accumulators of every thread into
+// out[0, nv): one shuffle level, then per value a 4-way pair tree over the
+// 64 groups of 4 and a warp's xor tree (fixed order).  `scratch` holds
+// NV * kThreads / 2 doubles.
+template <int NV, typename ACC>
+__device__ __forceinline__ void cta_sums(const ACC (&acc)[NV], int nv, double *scratch, double *out) {
+    constexpr int P0 = kThreads / 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // unrolled over the fixed bound so every index into acc is a constant
+    // (a run-time index would put acc in local memory for the whole pass)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (v < nv) {
+            const double h = (double)acc[v] + __shfl_down_sync(0xffffffffu, (double)acc[v], 16);
+            if (lane < 16) scratch[v * P0 + warp * 16 + lane] = h;
+        }
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < nv * 64; task += kThreads) {
+        double *q = scratch + (task / 64) * P0 + task % 64;
+        q[0] = (q[0] + q[64]) + (q[128] + q[192]);
+    }
+    __syncthreads();
+    for (int v = warp; v < nv; v += kThreads / 32) {
+        const double *q = scratch + v * P0 + lane;
+        double t = q[0] + q[32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) out[v] = t;
+    }
+    __syncthreads();   // scratch (the stages) is reused by the next pass
+}
+
+template <typename T, int NE>
+__global__ void __launch_bounds__(kThreads, 1)
+    spmv_qdot_tiled_kernel(SysView<T> sys, int spt, const T *x, T *y, T *yout, double *partials, int *status,
+                           unsigned *ticket, double *d) {
+    constexpr int DS = dslots<T>();
+    constexpr int CPS = 32 * sizeof(T) / 16;
+    // Q columns per later pass: as many accumulators as fit in registers
+    // beside the tile loads (each extra pass re-reads only y)
+    constexpr int G = DS == 1 ? 8 : 4;
+    using ACC = typename real_of<T>::type;
+    extern __shared__ unsigned char dsm[];
+    __shared__ TileRing ring;
+    ring_init(&ring, ring_buffer(dsm));
+    int64_t s_lo, s_hi;
+    own_range(sys.nslices, gridDim.x, blockIdx.x, s_lo, s_hi);
+    soff_load(&ring, sys.slice_ptr, s_lo, s_hi);
+    const uint64_t to = 2000000000ull;
+    const int n = sys.n;
+    double *const scratch = reinterpret_cast<double *>(ring.buf);   // the stages, free between passes
+    double *const part = partials + (size_t)blockIdx.x * kQdMaxN * DS;
+    unsigned sq = 0;   // this thread's tile counter (issued or consumed)
+    bool ok, bad;
+    {
+        ACC acc[NE * DS];
+#pragma unroll
+        for (int k = 0; k < NE * DS; ++k) acc[k] = ACC(0);
+        const T *epi[NE];
+#pragma unroll
+        for (int m = 0; m < NE; ++m) epi[m] = sys.Q + (int64_t)m * sys.ld;
+        const int64_t nrows = sys.N;
+        const bool keep = n > NE;   // later passes read y back
+        ok = sell_spmv<NE>(&ring, sq, sq, to, s_lo, s_hi, spt, sys.slice_ptr, sys.scol, sys.sval, x, epi,
+                           threadIdx.x & 31,
+                           [=](int64_t row, T v, const T (&e)[NE], ACC (&a)[NE * DS]) {
+                               if (keep) y[row] = v;                // padded copy
+                               if (row < nrows) yout[row] = v;      // the caller's y
+#pragma unroll
+                               for (int m = 0; m < NE; ++m) acc_dot(&a[m * DS], e[m], v);
+                           },
+                           acc);
+        bad = __syncthreads_or(!ok);   // also: this CTA's rows of y are written and fenced
+        if (!bad) cta_sums(acc, NE * DS, scratch, part);
+    }
+    const int64_t c_lo = s_lo * CPS, c_hi = s_hi * CPS;
+    for (int g0 = NE; g0 < n && !bad; g0 += G) {
+        const int ng = n - g0 < G ? n - g0 : G;
+        TilePass P;
+        P.ni = 1 + ng;
+        P.in[0] = y;
+        for (int m = 0; m < ng; ++m) P.in[1 + m] = sys.Q + (int64_t)(g0 + m) * sys.ld;
+        P.tc = tile_chunks_for(P.ni);
+        P.c_lo = c_lo;
+        P.c_hi = c_hi;
+        ACC acc[G * DS];
+#pragma unroll
+        for (int k = 0; k < G * DS; ++k) acc[k] = ACC(0);
+        const int tc = P.tc;
+        if ((threadIdx.x >> 5) == kConsumerWarps) {
+            if ((threadIdx.x & 31) == 0) ok = produce(&ring, P, sq, to);
+        } else {
+            ok = consume(&ring, P, sq, to, [&](int64_t, const unsigned char *st, int k) {
+                const Pack<T> yy = lds<T>(st, tc, 0, k);
+#pragma unroll
+                for (int m = 0; m < G; ++m) {
+                    if (m < ng) {
+                        const Pack<T> qq = lds<T>(st, tc, 1 + m, k);
+#pragma unroll
+                        for (int e = 0; e < Pack<T>::W; ++e) acc_dot(&acc[m * DS], qq.e[e], yy.e[e]);
+                    }
+                }
+            });
+        }
+        bad = __syncthreads_or(!ok);   // every tile consumed: the stages are free
+        if (!bad) cta_sums(acc, ng * DS, scratch, part + (size_t)g0 * DS);
+    }
+    if (threadIdx.x == 0) status[blockIdx.x] = bad ? 1 : 0;
+    ring_drain(&ring, sq, sq, to);
+    // The last CTA to finish sums every CTA's partials (fixed order, the
+    // same whichever CTA it is) and ORs the status slots into d[n * DS];
+    // it resets the ticket for the next launch.  No CTA waits for another.
+    __shared__ int s_last;
+    __threadfence();   // this CTA's partials and status before its ticket
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // one warp per value: lanes stride over the CTAs in index order, then
+    // the warp's xor tree
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int v = warp; v < n * DS; v += kThreads / 32) {
+            double t = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&partials[(size_t)b * kQdMaxN * DS + v]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) d[v] = t;
+        }
+    }
+    int st = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) st |= __ldcg(&status[b]);
+    st = __syncthreads_or(st);
+    if (threadIdx.x == 0) {
+        d[n * DS] = st ? 1.0 : 0.0;
+        *ticket = 0u;
+    }
+}
+
 template <typename T, int NB>
 static int qd_occupancy() {
     int nb = 0;
@@ -551,6 +706,32 @@ int spmv_qdot_grid() {
     int nb = qd_occupancy<T, kQdMaxN>();
     if (nb < 1) nb = 1;
     return sms * nb;
+}
+
+template <typename T, int NE>
+static cudaError_t launch_qd_tiled_ne(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
+                                      int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
+                                      cudaStream_t st) {
+    cudaError_t e = allow_ring((const void *)spmv_qdot_tiled_kernel<T, NE>);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev, st);
+    if (e != cudaSuccess) return e;
+    spmv_qdot_tiled_kernel<T, NE>
+        <<<grid, kThreads, kRingBytes, st>>>(sys, spt, x, y, yout, partials, status, ticket, d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
+                                   int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
+                                   cudaStream_t st) {
+    constexpr int DS = dslots<T>();
+    const int ne = qd_fused_columns(sys.n, DS == 2);
+    if constexpr (DS == 1) {
+        if (ne == 4)
+            return launch_qd_tiled_ne<T, 4>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
+    }
+    if (ne == 2) return launch_qd_tiled_ne<T, 2>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
+    return launch_qd_tiled_ne<T, 1>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
 }
 
 template <typename T>
@@ -615,6 +796,12 @@ template cudaError_t launch_spmv_qdot<double>(const SysView<double> &, const dou
                                               int, double *, cudaStream_t);
 template cudaError_t launch_spmv_qdot<cdouble>(const SysView<cdouble> &, const cdouble *, cdouble *,
                                                double *, int, double *, cudaStream_t);
+template cudaError_t launch_spmv_qdot_tiled<double>(const SysView<double> &, int, const double *, double *, double *,
+                                                    double *, int, int *, unsigned *, double *, cudaEvent_t,
+                                                    cudaStream_t);
+template cudaError_t launch_spmv_qdot_tiled<cdouble>(const SysView<cdouble> &, int, const cdouble *, cdouble *,
+                                                     cdouble *, double *, int, int *, unsigned *, double *,
+                                                     cudaEvent_t, cudaStream_t);
 template int spmv_qdot_grid<double>();
 template int spmv_qdot_grid<cdouble>();
 template cudaError_t launch_refine<float, double>(const SysView<float> &, const RefView<double> &,

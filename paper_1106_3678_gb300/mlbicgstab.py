@@ -71,7 +71,7 @@ class mlb_info(C.Structure):
                 ("grid", C.c_int32), ("block", C.c_int32),
                 ("precond", C.c_int32), ("nnz_padded", C.c_int64),
                 ("device_bytes", C.c_int64), ("n_active", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("reserved1", C.c_int32), ("qd_kernel_ms", C.c_double)]
 
 
 class mlb_tune_result(C.Structure):
@@ -351,12 +351,13 @@ def mlbicgstab_autotune(h: Handle, iters: int = 20, use_cache: bool = True) -> d
 
 
 def mlbicgstab_spmv_qdot(h: Handle, x, y) -> np.ndarray:
-    """y = A x and d = Q^H y (x, y CUDA tensors); returns d (host)."""
+    """y = A x and d = Q^H y (x, y CUDA tensors); returns d (host), one
+    value per active shadow vector (mlbicgstab_set_n)."""
     px, dx = _ptr(x)
     py, dy = _ptr(y)
     if not (dx and dy):
         raise ValueError("x and y must be CUDA tensors")
-    d = np.empty(h.n, dtype=h.dtype)
+    d = np.empty(mlbicgstab_info(h)["n_active"], dtype=h.dtype)
     _check(load().mlbicgstab_spmv_qdot(h.ptr, px, py, d.ctypes.data),
            "mlbicgstab_spmv_qdot")
     return d

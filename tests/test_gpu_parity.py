@@ -103,9 +103,32 @@ def _check_spmv_qdot(A, n, seed=0, grid_rows=None):
     return h
 
 
-@pytest.mark.parametrize("n", [1, 4, 16])
+# n <= 4: every column fused into the product's epilogue (1, 2 or 4 at a
+# time); larger n adds passes of up to 8 columns (4 for complex) over y
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 13, 16, 64])
 def test_spmv_qdot_cd2d(n):
     _check_spmv_qdot(W.cd2d(32), n)
+
+
+@pytest.mark.parametrize("n", [1, 2, 9])
+def test_spmv_qdot_complex_splits(n):
+    _check_spmv_qdot(W.helmholtz3d_c(9, 8, 7), n, seed=n)
+
+
+def test_spmv_qdot_after_set_n():
+    """A handle created with n = 8 and set to 3 returns the 3 active inner
+    products, equal to those of a handle created with n = 3."""
+    import torch
+    A = W.cd3d_lognormal(16)
+    x = torch.tensor(np.random.default_rng(2).standard_normal(A.n_rows), device="cuda")
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    h8 = M.mlbicgstab_create(A, n=8, q_seed=0)
+    M.mlbicgstab_set_n(h8, 3)
+    d8 = M.mlbicgstab_spmv_qdot(h8, x, y1)
+    d3 = M.mlbicgstab_spmv_qdot(M.mlbicgstab_create(A, n=3, q_seed=0), x, y2)
+    assert d8.shape == (3,)
+    np.testing.assert_array_equal(d8, d3)
+    assert torch.equal(y1, y2)
 
 
 def test_spmv_qdot_cd3d_several_slices_ragged_tail():
