@@ -61,7 +61,6 @@ struct mlb_handle {
     unsigned *qd_ticket = nullptr;  // last-CTA counter, 0 between launches
     double qd_ms = 0.0;           // device time of the last fused product
     double *qd_host = nullptr;    // pinned copy of qd_out
-    int qd_grid = 0;
     DevResult *hres = nullptr;  // pinned
     // batch workspace (owned by the first handle of a batch call)
     void *bws = nullptr;
@@ -503,10 +502,9 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     if ((rc = dev_alloc_t(h, &h->partials, (size_t)2 * maxg * kMaxSums * 8))) return rc;
     if ((rc = dev_alloc_t(h, &h->bar, sizeof(BarrierState)))) return rc;
     if ((rc = dev_alloc_t(h, &h->dres, sizeof(DevResult)))) return rc;
-    h->qd_grid = cplx ? spmv_qdot_grid<cdouble>() : spmv_qdot_grid<double>();
-    if ((rc = dev_alloc_t(h, &h->qd_partials, (size_t)std::max(h->qd_grid, maxg) * kQdMaxN * 2 * 8))) return rc;
+    if ((rc = dev_alloc_t(h, &h->qd_partials, (size_t)h->grid_max * kQdMaxN * 2 * 8))) return rc;
     if ((rc = dev_alloc_t(h, &h->qd_out, (size_t)(kQdMaxN * 2 + 1) * 8))) return rc;
-    if ((rc = dev_alloc_t(h, &h->qd_status, (size_t)std::max(h->qd_grid, maxg) * sizeof(int)))) return rc;
+    if ((rc = dev_alloc_t(h, &h->qd_status, (size_t)h->grid_max * sizeof(int)))) return rc;
     if ((rc = dev_alloc_t(h, &h->qd_ticket, sizeof(unsigned)))) return rc;
     MLB_CUDA(cudaMemsetAsync(h->qd_ticket, 0, sizeof(unsigned), st));
     if (cudaMallocHost(&h->qd_host, (size_t)(kQdMaxN * 2 + 1) * 8) != cudaSuccess) {

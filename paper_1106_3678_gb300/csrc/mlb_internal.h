@@ -68,10 +68,9 @@ cudaError_t launch_ahq(const int64_t *rp, const int32_t *ci, const T *av,
                        int64_t N, int64_t ld, const T *Q, T *F, int m,
                        cudaStream_t st);
 
-// Fused y = A x, d = Q^H y.  `partials` holds grid * kQdMaxN * 2 doubles;
-// d (device) receives n values (2n doubles for complex).
+// Fused y = A x, d = Q^H y.  `partials` holds grid * kQdMaxN * 2 doubles.
 constexpr int kQdMaxN = 64;
-// Tiled form: one CTA of kThreads per SM (grid <= the handle's grid_max),
+// One CTA of kThreads per SM (grid <= the handle's grid_max),
 // dynamic shared memory kRingBytes.  The first qd_fused_columns(n, .) columns
 // of Q are epilogue vectors of the SELL product, whose tiles hold `spt`
 // slices (sized for that many epilogue vectors); the others take tile
@@ -88,13 +87,6 @@ template <typename T>
 cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
                                    int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
                                    cudaStream_t st);
-constexpr int kQdThreads = 256;
-template <typename T>
-cudaError_t launch_spmv_qdot(const SysView<T> &sys, const T *x, T *y,
-                             double *partials, int grid, double *d,
-                             cudaStream_t st);
-template <typename T>
-int spmv_qdot_grid();
 
 // Failure-detection self-test of the grid barrier (see the C ABI).
 cudaError_t launch_barrier_selftest(int grid, BarrierState *bs,

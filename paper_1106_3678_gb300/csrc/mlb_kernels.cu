@@ -451,91 +451,6 @@ cudaError_t launch_ahq(const int64_t *rp, const int32_t *ci, const T *av, int64_
 // ===========================================================================
 // fused y = A x, d = Q^H y (all n shadow inner products)
 // ===========================================================================
-// Pass 1: one warp per 32-row SELL slice; each lane keeps NB running inner
-// products over its rows; per-CTA sums go to `partials` in fixed order.
-template <typename T, int NB>
-__global__ void __launch_bounds__(kQdThreads) spmv_qdot_kernel(SysView<T> sys, const T *x, T *y,
-                                                               double *partials) {
-    constexpr int DS = dslots<T>();
-    using ACC = typename real_of<T>::type;
-    __shared__ double red[33 * DS];
-    const int n = sys.n;
-    const int lane = threadIdx.x & 31;
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    ACC acc[NB * DS];
-#pragma unroll
-    for (int k = 0; k < NB * DS; ++k) acc[k] = ACC(0);
-    for (int64_t s = gwarp; s < sys.nslices; s += nwarps) {
-        const int64_t off = __ldg(sys.slice_ptr + s);
-        const int w = (int)((__ldg(sys.slice_ptr + s + 1) - off) >> 5);
-        const int32_t *cp = sys.scol + off + lane;
-        const T *vp = sys.sval + off + lane;
-        T sum{};
-        int k = 0;
-        for (; k + 8 <= w; k += 8) {
-            int32_t cc[8];
-            T vv[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) cc[u] = __ldcs(cp + 32 * (k + u));
-#pragma unroll
-            for (int u = 0; u < 8; ++u) vv[u] = ldcs_val(vp + 32 * (k + u));
-#pragma unroll
-            for (int u = 0; u < 8; ++u) sum = efma(vv[u], ldg_val(x + cc[u]), sum);
-        }
-        if (k < w) {
-            int32_t cc[8];
-            T vv[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (k + u < w) cc[u] = __ldcs(cp + 32 * (k + u));
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (k + u < w) vv[u] = ldcs_val(vp + 32 * (k + u));
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (k + u < w) sum = efma(vv[u], ldg_val(x + cc[u]), sum);
-        }
-        const int64_t row = s * 32 + lane;
-        y[row] = sum;
-#pragma unroll
-        for (int q = 0; q < NB; ++q)
-            if (q < n) acc_dot(&acc[q * DS], ldg_val(sys.Q + (int64_t)q * sys.ld + row), sum);
-    }
-    for (int q = 0; q < NB; ++q) {
-        if (q >= n) break;
-        double v[DS];
-#pragma unroll
-        for (int t = 0; t < DS; ++t) v[t] = (double)acc[q * DS + t];
-        block_sum_all<DS>(v, red);
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int t = 0; t < DS; ++t)
-                partials[((size_t)blockIdx.x * kQdMaxN + q) * DS + t] = v[t];
-        }
-    }
-}
-
-// Pass 2: one CTA sums the per-CTA partials in fixed order.
-template <int DS>
-__global__ void qdot_finish_kernel(const double *partials, int grid, int n, double *d) {
-    __shared__ double red[33 * DS];
-    for (int q = 0; q < n; ++q) {
-        double v[DS];
-#pragma unroll
-        for (int t = 0; t < DS; ++t) v[t] = 0.0;
-        for (int b = threadIdx.x; b < grid; b += blockDim.x) {
-#pragma unroll
-            for (int t = 0; t < DS; ++t) v[t] += partials[((size_t)b * kQdMaxN + q) * DS + t];
-        }
-        block_sum_all<DS>(v, red);
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int t = 0; t < DS; ++t) d[q * DS + t] = v[t];
-        }
-    }
-}
-
 // Tiled form (the library's entry point): one CTA per SM, each owning a
 // contiguous slice range.  The first NE columns of Q ride through the
 // engine's TMA-fed SELL product as epilogue vectors, so their inner
@@ -691,23 +606,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <typename T, int NB>
-static int qd_occupancy() {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_qdot_kernel<T, NB>, kQdThreads, 0);
-    return nb;
-}
-
-template <typename T>
-int spmv_qdot_grid() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nb = qd_occupancy<T, kQdMaxN>();
-    if (nb < 1) nb = 1;
-    return sms * nb;
-}
-
 template <typename T, int NE>
 static cudaError_t launch_qd_tiled_ne(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
                                       int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
@@ -732,22 +630,6 @@ cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T
     }
     if (ne == 2) return launch_qd_tiled_ne<T, 2>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
     return launch_qd_tiled_ne<T, 1>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
-}
-
-template <typename T>
-cudaError_t launch_spmv_qdot(const SysView<T> &sys, const T *x, T *y, double *partials, int grid,
-                             double *d, cudaStream_t st) {
-    constexpr int DS = dslots<T>();
-    const int n = sys.n;
-    if (n <= 4) spmv_qdot_kernel<T, 4><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
-    else if (n <= 8) spmv_qdot_kernel<T, 8><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
-    else if (n <= 16) spmv_qdot_kernel<T, 16><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
-    else if (n <= 32) spmv_qdot_kernel<T, 32><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
-    else spmv_qdot_kernel<T, 64><<<grid, kQdThreads, 0, st>>>(sys, x, y, partials);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    qdot_finish_kernel<DS><<<1, 1024, 0, st>>>(partials, grid, n, d);
-    return cudaGetLastError();
 }
 
 // ===========================================================================
@@ -792,18 +674,12 @@ template cudaError_t launch_ahq<double>(const int64_t *, const int32_t *, const 
                                         const double *, double *, int, cudaStream_t);
 template cudaError_t launch_ahq<cdouble>(const int64_t *, const int32_t *, const cdouble *, int64_t, int64_t,
                                          const cdouble *, cdouble *, int, cudaStream_t);
-template cudaError_t launch_spmv_qdot<double>(const SysView<double> &, const double *, double *, double *,
-                                              int, double *, cudaStream_t);
-template cudaError_t launch_spmv_qdot<cdouble>(const SysView<cdouble> &, const cdouble *, cdouble *,
-                                               double *, int, double *, cudaStream_t);
 template cudaError_t launch_spmv_qdot_tiled<double>(const SysView<double> &, int, const double *, double *, double *,
                                                     double *, int, int *, unsigned *, double *, cudaEvent_t,
                                                     cudaStream_t);
 template cudaError_t launch_spmv_qdot_tiled<cdouble>(const SysView<cdouble> &, int, const cdouble *, cdouble *,
                                                      cdouble *, double *, int, int *, unsigned *, double *,
                                                      cudaEvent_t, cudaStream_t);
-template int spmv_qdot_grid<double>();
-template int spmv_qdot_grid<cdouble>();
 template cudaError_t launch_refine<float, double>(const SysView<float> &, const RefView<double> &,
                                                   const SolveCtl &, const RefCtl &, int, cudaStream_t);
 template cudaError_t launch_refine<cfloat, cdouble>(const SysView<cfloat> &, const RefView<cdouble> &,
