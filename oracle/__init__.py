@@ -14,7 +14,10 @@ Functions
     ahq                 F = A^H Q(:, :m)                (Algorithm 4.1, step 2)
     q_gauss             shadow vectors from the library's documented
                         SplitMix64 + Box–Muller generator
-    mlbicgstabt         one call of Algorithm 7.1 with M = I
+    mlbicgstabt         one call of Algorithm 7.1 (M = I, a diagonal M, or
+                        ILU(0) factors)
+    ilu0                ILU(0) factors of A in A's pattern
+    minv, minv_h        M^{-1} v and M^{-H} v
     solve               repeated calls from the current x until the true
                         residual meets tol (restart wrapper, not in the paper)
 """
@@ -63,8 +66,17 @@ def load(path: str | None = None):
         f = getattr(lib, f"orc_mlbicgstabt_{sfx}")
         f.restype = C.c_int
         f.argtypes = [C.c_int64, P, P, P, C.c_int32, P, P, P, C.c_int64,
-                      C.c_double, C.c_double, P, C.POINTER(_Result),
+                      C.c_double, C.c_double, P, P, P, C.POINTER(_Result),
                       P, C.c_int64, P, C.c_int64, P, C.c_int64, P, C.c_int64]
+        f = getattr(lib, f"orc_ilu0_{sfx}")
+        f.restype = C.c_int
+        f.argtypes = [C.c_int64, P, P, P, P, P]
+        f = getattr(lib, f"orc_minv_{sfx}")
+        f.restype = None
+        f.argtypes = [C.c_int64, P, P, P, P, P, P, P]
+        f = getattr(lib, f"orc_minv_h_{sfx}")
+        f.restype = None
+        f.argtypes = [C.c_int64, P, P, P, P, P, P]
     if path is None:
         _LIB = lib
     return lib
@@ -161,11 +173,82 @@ class Result:
     true_relres: float | None = None
 
 
+class IluError(ValueError):
+    """ILU(0) does not exist for this input (code -1: a row unsorted or
+    without a diagonal entry; -3: a zero pivot)."""
+
+
+@dataclasses.dataclass
+class Ilu:
+    """ILU(0) factors in the pattern of A: ``lu`` holds L's strictly lower
+    entries (unit diagonal implied) and U's entries, ``dpos[r]`` the
+    position of row r's diagonal."""
+    lu: np.ndarray
+    dpos: np.ndarray
+
+
+def ilu0(A, lib=None) -> Ilu:
+    """ILU(0) of A (Saad, Algorithm 10.4; the paper's experiments use ILU(0),
+    §5).  Column indices must increase within each row."""
+    lib = lib or load()
+    cplx = np.iscomplexobj(A.val)
+    rp, ci, av = _mat(A, cplx)
+    lu = np.empty_like(av)
+    dpos = np.empty(A.n_rows, dtype=np.int64)
+    fn = lib.orc_ilu0_z if cplx else lib.orc_ilu0_d
+    rc = fn(A.n_rows, _ptr(rp), _ptr(ci), _ptr(av), _ptr(lu), _ptr(dpos))
+    if rc == -2:
+        raise MemoryError("oracle allocation failed")
+    if rc != 0:
+        raise IluError(rc)
+    return Ilu(lu=lu, dpos=dpos)
+
+
+def _pc_args(A, cplx, mdiag, ilu):
+    dt = np.complex128 if cplx else np.float64
+    md = None if mdiag is None else np.ascontiguousarray(mdiag, dtype=dt)
+    if md is not None and md.shape != (A.n_rows,):
+        raise ValueError("mdiag must hold N entries")
+    if md is not None and ilu is not None:
+        raise ValueError("give mdiag or ilu, not both")
+    lu = None if ilu is None else np.ascontiguousarray(ilu.lu, dtype=dt)
+    dp = None if ilu is None else np.ascontiguousarray(ilu.dpos, dtype=np.int64)
+    return md, lu, dp
+
+
+def minv(A, v, mdiag=None, ilu=None, lib=None) -> np.ndarray:
+    """M^{-1} v for M = diag(mdiag) or M = L U from ``ilu``."""
+    lib = lib or load()
+    cplx = np.iscomplexobj(A.val) or np.iscomplexobj(v)
+    dt = np.complex128 if cplx else np.float64
+    rp, ci, _ = _mat(A, cplx)
+    md, lu, dp = _pc_args(A, cplx, mdiag, ilu)
+    src = np.ascontiguousarray(v, dtype=dt)
+    dst = np.empty_like(src)
+    fn = lib.orc_minv_z if cplx else lib.orc_minv_d
+    fn(A.n_rows, _ptr(rp), _ptr(ci), _ptr(md), _ptr(lu), _ptr(dp), _ptr(src), _ptr(dst))
+    return dst
+
+
+def minv_h(A, v, mdiag=None, ilu=None, lib=None) -> np.ndarray:
+    """M^{-H} v for M = diag(mdiag) or M = L U from ``ilu``."""
+    lib = lib or load()
+    cplx = np.iscomplexobj(A.val) or np.iscomplexobj(v)
+    dt = np.complex128 if cplx else np.float64
+    rp, ci, _ = _mat(A, cplx)
+    md, lu, dp = _pc_args(A, cplx, mdiag, ilu)
+    w = np.array(v, dtype=dt, copy=True)
+    fn = lib.orc_minv_h_z if cplx else lib.orc_minv_h_d
+    fn(A.n_rows, _ptr(rp), _ptr(ci), _ptr(md), _ptr(lu), _ptr(dp), _ptr(w))
+    return w
+
+
 def mlbicgstabt(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
                 err_hist: bool = False, x_hist: int = 0, blk_ops: int = 0,
-                trace: bool = False, lib=None, mdiag=None) -> Result:
+                trace: bool = False, lib=None, mdiag=None, ilu=None) -> Result:
     """One call of ML(n)BiCGStabt (Algorithm 7.1) from x0; ``mdiag`` is the
-    diagonal of the preconditioner M (None: M = I)."""
+    diagonal of the preconditioner M, ``ilu`` its ILU(0) factors (from
+    ``ilu0``); neither: M = I."""
     lib = lib or load()
     cplx = (np.iscomplexobj(A.val) or np.iscomplexobj(b)
             or np.iscomplexobj(Q) or np.iscomplexobj(x0))
@@ -176,9 +259,7 @@ def mlbicgstabt(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
     Qf = np.asfortranarray(Q, dtype=dt)
     b = np.ascontiguousarray(b, dtype=dt)
     x = np.array(x0, dtype=dt, copy=True)
-    md = None if mdiag is None else np.ascontiguousarray(mdiag, dtype=dt)
-    if md is not None and md.shape != (N,):
-        raise ValueError("mdiag must hold N entries")
+    md, lu, dp = _pc_args(A, cplx, mdiag, ilu)
     cap = int(maxit) + 1
     eh = np.full(cap, np.nan) if err_hist else None
     xh = np.zeros((x_hist, N), dtype=dt) if x_hist else None
@@ -187,7 +268,7 @@ def mlbicgstabt(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
     res = _Result()
     fn = lib.orc_mlbicgstabt_z if cplx else lib.orc_mlbicgstabt_d
     rc = fn(N, _ptr(rp), _ptr(ci), _ptr(av), n, _ptr(Qf), _ptr(b), _ptr(x),
-            int(maxit), float(tol), float(kappa), _ptr(md), C.byref(res),
+            int(maxit), float(tol), float(kappa), _ptr(md), _ptr(lu), _ptr(dp), C.byref(res),
             _ptr(eh), cap if eh is not None else 0,
             _ptr(xh), x_hist, _ptr(bo), blk_ops,
             _ptr(tr), cap if tr is not None else 0)
@@ -221,7 +302,7 @@ def true_relres(A, b, x, lib=None) -> float:
 
 
 def solve(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
-          max_outer: int = 10, lib=None, mdiag=None) -> Result:
+          max_outer: int = 10, lib=None, mdiag=None, ilu=None) -> Result:
     """Call ``mlbicgstabt`` again from the current x while its recursive
     residual met ``tol`` but the true residual ||b - A x||/||b|| did not;
     each new call recomputes r = b - A x and returns at once (iter 0) when
@@ -233,7 +314,7 @@ def solve(A, b, x0, Q, maxit: int, tol: float, kappa: float = 0.0,
     outer = 0
     res = None
     while True:
-        res = mlbicgstabt(A, b, x, Q, maxit - total, tol, kappa, lib=lib, mdiag=mdiag)
+        res = mlbicgstabt(A, b, x, Q, maxit - total, tol, kappa, lib=lib, mdiag=mdiag, ilu=ilu)
         x = res.x
         total += res.iter
         if res.flag != 0 or res.iter == 0 or total >= maxit:

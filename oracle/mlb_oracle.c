@@ -12,9 +12,13 @@
  *   orc_spmv_{d,z}           y = A x, definition of the CSR product
  *   orc_ahq_{d,z}            F = A^H Q(:,1:n-1)            (Algorithm 4.1, step 2)
  *   orc_mlbicgstabt_{d,z}    ML(n)BiCGStabt = Algorithm 7.1 (M = I, which is
- *                            Algorithm 4.1, or a diagonal M applied as
- *                            written), stopping rule and flags of §5, omega
+ *                            Algorithm 4.1, or a diagonal or ILU(0) M applied
+ *                            as written), stopping rule and flags of §5, omega
  *                            guard of Eq. 5.1
+ *   orc_ilu0_{d,z}           ILU(0) factors of A (the preconditioner of the
+ *                            paper's experiments, §5; textbook definition)
+ *   orc_minv_{d,z},          M^{-1} v and M^{-H} v for a diagonal or ILU(0) M
+ *   orc_minv_h_{d,z}         (Algorithm 7.1, steps 2, 31, 37, 50)
  *   orc_qgauss               N(0,1) shadow vectors from the counter-based
  *                            generator the library documents: SplitMix64
  *                            (Steele, Lea & Flood, OOPSLA 2014) evaluated at
@@ -24,7 +28,10 @@
  * Parity pins (tests/test_oracle_*.py): Table 2.1 bit-exact; n = 1 against
  * an independently written textbook BiCGStab; n >= N finite termination and
  * block-0 bi-orthogonality (Algorithm 3.1 Petrov–Galerkin conditions);
- * agreement with a dense LU solve; Table 4.3 operation counts per block.
+ * agreement with a dense LU solve; Table 4.3 operation counts per block;
+ * ILU(0): (L U)_ij = a_ij on A's pattern, exact LU when the pattern has no
+ * fill, M^{-1} and M^{-H} against dense solves, one-step convergence when
+ * M = A.
  */
 #include <complex.h>
 #include <math.h>

@@ -111,11 +111,149 @@ void SFX(orc_ahq)(int64_t N, const int64_t *rp, const int32_t *ci,
     }
 }
 
-/* dst = M^{-1} src for a diagonal M (elementwise division by mdiag). */
-static void SFX(minv)(int64_t N, const S *mdiag, const S *src, S *dst)
+/*
+ * ILU(0), the preconditioner of the paper's experiments (§5): L unit lower
+ * triangular and U upper triangular, both with the sparsity pattern of A,
+ * such that (L U)_ij = a_ij for every (i, j) in that pattern.  Computed by
+ * the textbook row-oriented elimination restricted to the pattern (Saad,
+ * Iterative Methods for Sparse Linear Systems, 2nd ed., Algorithm 10.4):
+ * for each row i and each k < i of its pattern in increasing order,
+ * a_ik <- a_ik / a_kk, then a_ij <- a_ij - a_ik a_kj for every j > k that
+ * is in the pattern of both row i and row k.
+ *
+ * In: CSR A, column indices increasing within each row, a stored diagonal
+ * entry in every row.  Out: lu (the nnz values in A's pattern: strictly
+ * lower part = L without its unit diagonal, the rest = U) and dpos[r] =
+ * position of row r's diagonal.  Returns 0; -1 when a row is unsorted or
+ * has no diagonal; -3 when a pivot u_kk is zero; -2 on allocation failure.
+ */
+int SFX(orc_ilu0)(int64_t N, const int64_t *rp, const int32_t *ci, const S *av,
+                  S *lu, int64_t *dpos)
 {
+    for (int64_t r = 0; r < N; ++r) {
+        dpos[r] = -1;
+        for (int64_t k = rp[r]; k < rp[r + 1]; ++k) {
+            if (k > rp[r] && ci[k] <= ci[k - 1])
+                return -1;
+            if (ci[k] == r)
+                dpos[r] = k;
+        }
+        if (dpos[r] < 0)
+            return -1;
+    }
+    for (int64_t k = 0; k < rp[N]; ++k)
+        lu[k] = av[k];
+    int64_t *pos = (int64_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
+    if (!pos)
+        return -2;
     for (int64_t t = 0; t < N; ++t)
-        dst[t] = src[t] / mdiag[t];
+        pos[t] = -1;
+    int rc = 0;
+    for (int64_t i = 0; i < N && rc == 0; ++i) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            pos[ci[k]] = k;
+        for (int64_t ik = rp[i]; ik < dpos[i]; ++ik) {
+            const int64_t k = ci[ik];
+            const S ukk = lu[dpos[k]];
+            if (ukk == 0) {
+                rc = -3;
+                break;
+            }
+            lu[ik] = lu[ik] / ukk;
+            for (int64_t kj = dpos[k] + 1; kj < rp[k + 1]; ++kj) {
+                const int64_t ij = pos[ci[kj]];
+                if (ij >= 0)
+                    lu[ij] = lu[ij] - lu[ik] * lu[kj];
+            }
+        }
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            pos[ci[k]] = -1;
+    }
+    free(pos);
+    for (int64_t i = 0; i < N && rc == 0; ++i)
+        if (lu[dpos[i]] == 0)
+            rc = -3;
+    return rc;
+}
+
+/* The preconditioner M of Algorithm 7.1 handed to the oracle: none, a
+ * diagonal (mdiag), or ILU(0) factors in A's pattern (lu, dpos). */
+typedef struct {
+    int64_t N;
+    const int64_t *rp;
+    const int32_t *ci;
+    const S *mdiag;
+    const S *lu;
+    const int64_t *dpos;
+} SFX(pc_t);
+
+/* dst = M^{-1} src.  Diagonal: elementwise division.  ILU(0): L y = src
+ * by forward substitution, then U dst = y by backward substitution (rows
+ * in order, each a plain sequential sum). */
+static void SFX(minv)(const SFX(pc_t) *pc, const S *src, S *dst)
+{
+    const int64_t N = pc->N;
+    if (pc->mdiag) {
+        const S *mdiag = pc->mdiag;
+        for (int64_t t = 0; t < N; ++t)
+            dst[t] = src[t] / mdiag[t];
+        return;
+    }
+    const int64_t *rp = pc->rp, *dp = pc->dpos;
+    const int32_t *ci = pc->ci;
+    const S *lu = pc->lu;
+    for (int64_t i = 0; i < N; ++i) {
+        S s = src[i];
+        for (int64_t k = rp[i]; k < dp[i]; ++k)
+            s -= lu[k] * dst[ci[k]];
+        dst[i] = s;
+    }
+    for (int64_t i = N - 1; i >= 0; --i) {
+        S s = dst[i];
+        for (int64_t k = dp[i] + 1; k < rp[i + 1]; ++k)
+            s -= lu[k] * dst[ci[k]];
+        dst[i] = s / lu[dp[i]];
+    }
+}
+
+/* v <- M^{-H} v (for F = M^{-H} A^H Q).  Diagonal: division by conj(m).
+ * ILU(0): M^H = U^H L^H, so first U^H t = v (U^H is lower triangular:
+ * forward, column by column of U^H, i.e. row by row of U), then
+ * L^H v = t (unit upper: backward, row by row of L). */
+static void SFX(minv_h)(const SFX(pc_t) *pc, S *v)
+{
+    const int64_t N = pc->N;
+    if (pc->mdiag) {
+        const S *mdiag = pc->mdiag;
+        for (int64_t t = 0; t < N; ++t)
+            v[t] = v[t] / CONJ(mdiag[t]);
+        return;
+    }
+    const int64_t *rp = pc->rp, *dp = pc->dpos;
+    const int32_t *ci = pc->ci;
+    const S *lu = pc->lu;
+    for (int64_t i = 0; i < N; ++i) {
+        v[i] = v[i] / CONJ(lu[dp[i]]);
+        for (int64_t k = dp[i] + 1; k < rp[i + 1]; ++k)
+            v[ci[k]] -= CONJ(lu[k]) * v[i];
+    }
+    for (int64_t i = N - 1; i >= 0; --i)
+        for (int64_t k = rp[i]; k < dp[i]; ++k)
+            v[ci[k]] -= CONJ(lu[k]) * v[i];
+}
+
+/* The two applications, exported for the pins. */
+void SFX(orc_minv)(int64_t N, const int64_t *rp, const int32_t *ci, const S *mdiag,
+                   const S *lu, const int64_t *dpos, const S *src, S *dst)
+{
+    SFX(pc_t) pc = {N, rp, ci, mdiag, lu, dpos};
+    SFX(minv)(&pc, src, dst);
+}
+void SFX(orc_minv_h)(int64_t N, const int64_t *rp, const int32_t *ci, const S *mdiag,
+                     const S *lu, const int64_t *dpos, S *v)
+{
+    SFX(pc_t) pc = {N, rp, ci, mdiag, lu, dpos};
+    SFX(minv_h)(&pc, v);
 }
 
 /*
@@ -132,12 +270,13 @@ static void SFX(minv)(int64_t N, const S *mdiag, const S *src, S *dst)
  * of Algorithm 7.1 read; slot i is then overwritten in place.
  *
  * Preconditioning (Algorithm 7.1 with M != I): mdiag, when not NULL, is
- * the diagonal of M (right preconditioning).  Then, as written in the
+ * the diagonal of M; ilu and ilu_dpos, when not NULL, are the ILU(0)
+ * factors of A from orc_ilu0 (M = L U).  Right preconditioning: as written in the
  * algorithm: F = M^{-H} A^H Q (step 2), g^ = M^{-1} g is kept beside every
  * g (steps 2, 31, 50) and is what x advances along (steps 6, 35) and what
  * A multiplies (w = A g^); u^ = M^{-1} u (step 37) gives z = A u^ and
  * x += omega u^ (steps 38-39); the guard of Eq. 5.1 is taken with A u^ in
- * place of A u.  mdiag == NULL is M = I: no g^ is formed and the
+ * place of A u.  With neither given, M = I: no g^ is formed and the
  * arithmetic is exactly that of Algorithm 4.1.
  *
  * Inputs: CSR A (N rows), Q (N x n, column-major, ld N), b, x (in: x_0,
@@ -151,7 +290,7 @@ static void SFX(minv)(int64_t N, const S *mdiag, const S *src, S *dst)
 int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
                          const S *av, int32_t n, const S *Q, const S *b,
                          S *x, int64_t maxit, double tol, double kappa,
-                         const S *mdiag,
+                         const S *mdiag, const S *ilu, const int64_t *ilu_dpos,
                          orc_result *res,
                          double *err_hist, int64_t err_cap,
                          S *x_hist, int64_t x_cap,
@@ -169,11 +308,13 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
     S *z = (S *)calloc((size_t)N, sizeof(S));
     S *c = (S *)calloc((size_t)n, sizeof(S));
     /* g^ slots and u^ (M != I only; with M = I they are G and r) */
-    S *Gh = mdiag ? (S *)calloc((size_t)N * n, sizeof(S)) : G;
-    S *uh = mdiag ? (S *)calloc((size_t)N, sizeof(S)) : r;
+    const SFX(pc_t) pc = {N, rp, ci, mdiag, ilu, ilu_dpos};
+    const int pc_on = mdiag || ilu;
+    S *Gh = pc_on ? (S *)calloc((size_t)N * n, sizeof(S)) : G;
+    S *uh = pc_on ? (S *)calloc((size_t)N, sizeof(S)) : r;
     if (!G || !W || (n > 1 && !F) || !r || !z || !c || !Gh || !uh) {
         free(G); free(W); free(F); free(r); free(z); free(c);
-        if (mdiag) { free(Gh); free(uh); }
+        if (pc_on) { free(Gh); free(uh); }
         return -2;
     }
 
@@ -213,17 +354,16 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
     /* step 2: [f_1..f_{n-1}] = M^{-H} A^H [q_1..q_{n-1}] */
     if (n > 1) {
         SFX(orc_ahq)(N, rp, ci, av, n - 1, Q, F);
-        if (mdiag)
+        if (pc_on)
             for (int32_t s = 0; s < n - 1; ++s)
-                for (int64_t t = 0; t < N; ++t)
-                    F[(int64_t)s * N + t] = F[(int64_t)s * N + t] / CONJ(mdiag[t]);
+                SFX(minv_h)(&pc, F + (int64_t)s * N);
     }
 
     /* step 2: g_0 = r_0, g^_0 = M^{-1} r_0, w_0 = A g^_0, c_0 = q_1^H w_0,
      * e_0 = q_1^H r_0 */
     memcpy(G, r, (size_t)N * sizeof(S));
-    if (mdiag)
-        SFX(minv)(N, mdiag, G, Gh);
+    if (pc_on)
+        SFX(minv)(&pc, G, Gh);
     SFX(matvec)(N, rp, ci, av, Gh, W, ops);
     c[0] = SFX(dot)(N, Q, W, ops);
     if (c[0] == 0) {
@@ -286,8 +426,8 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
             }
 
             /* steps 31-32: g^ = M^{-1} g, w = A g^, c = q_{i+1}^H w */
-            if (mdiag)
-                SFX(minv)(N, mdiag, gi, Gh + (int64_t)i * N);
+            if (pc_on)
+                SFX(minv)(&pc, gi, Gh + (int64_t)i * N);
             SFX(matvec)(N, rp, ci, av, Gh + (int64_t)i * N, wi, ops);
             c[i] = SFX(dot)(N, Q + (int64_t)i * N, wi, ops);
             if (c[i] == 0) {
@@ -310,8 +450,8 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
         }
 
         /* step 37: u^ = M^{-1} u; step 38: omega = (A u^)^H u / ||A u^||^2 */
-        if (mdiag)
-            SFX(minv)(N, mdiag, r, uh);
+        if (pc_on)
+            SFX(minv)(&pc, r, uh);
         SFX(matvec)(N, rp, ci, av, uh, z, ops);
         S zz = SFX(dot)(N, z, z, ops);
         if (zz == 0) {
@@ -360,8 +500,8 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
         /* step 50: g = z_w - g / omega_{j+1} */
         SFX(omega_corr)(N, W, omega, G, ops);
         /* step 50 (end): g^ = M^{-1} g; step 51: w = A g^, c = q_1^H w */
-        if (mdiag)
-            SFX(minv)(N, mdiag, G, Gh);
+        if (pc_on)
+            SFX(minv)(&pc, G, Gh);
         SFX(matvec)(N, rp, ci, av, Gh, W, ops);
         c[0] = SFX(dot)(N, Q, W, ops);
         if (c[0] == 0) {
@@ -377,6 +517,6 @@ done:
     res->j = (int32_t)j;
     res->i = i;
     free(G); free(W); free(F); free(r); free(z); free(c);
-    if (mdiag) { free(Gh); free(uh); }
+    if (pc_on) { free(Gh); free(uh); }
     return 0;
 }

@@ -58,12 +58,25 @@ MUTANTS = [
      "SFX(matvec)(N, rp, ci, av, Gh + (int64_t)i * N, wi, ops);",
      "SFX(matvec)(N, rp, ci, av, gi, wi, ops);"),
     ("precond_F_unscaled", BODY,
-     "F[(int64_t)s * N + t] = F[(int64_t)s * N + t] / CONJ(mdiag[t]);",
-     "F[(int64_t)s * N + t] = F[(int64_t)s * N + t];"),
+     "v[t] = v[t] / CONJ(mdiag[t]);", "v[t] = v[t];"),
     ("precond_omega_step_u", BODY, "SFX(axpy)(N, omega, uh, x, ops);",
      "SFX(axpy)(N, omega, r, x, ops);"),
     ("precond_minv_multiplies", BODY, "dst[t] = src[t] / mdiag[t];",
      "dst[t] = src[t] * mdiag[t];"),
+    # ILU(0) factors and their application
+    ("ilu_no_update", BODY, "lu[ij] = lu[ij] - lu[ik] * lu[kj];", "lu[ij] = lu[ij];"),
+    ("ilu_no_divide", BODY, "lu[ik] = lu[ik] / ukk;", "lu[ik] = lu[ik];"),
+    ("ilu_update_sign", BODY, "lu[ij] = lu[ij] - lu[ik] * lu[kj];", "lu[ij] = lu[ij] + lu[ik] * lu[kj];"),
+    ("ilu_backward_no_div", BODY, "dst[i] = s / lu[dp[i]];", "dst[i] = s;"),
+    ("ilu_forward_drops_last_term", BODY,
+     "for (int64_t k = rp[i]; k < dp[i]; ++k)\n            s -= lu[k] * dst[ci[k]];",
+     "for (int64_t k = rp[i]; k + 1 < dp[i]; ++k)\n            s -= lu[k] * dst[ci[k]];"),
+    ("ilu_minv_h_no_conj", BODY,
+     "for (int64_t k = dp[i] + 1; k < rp[i + 1]; ++k)\n            v[ci[k]] -= CONJ(lu[k]) * v[i];",
+     "for (int64_t k = dp[i] + 1; k < rp[i + 1]; ++k)\n            v[ci[k]] -= lu[k] * v[i];"),
+    ("ilu_minv_h_skips_L", BODY,
+     "for (int64_t k = rp[i]; k < dp[i]; ++k)\n            v[ci[k]] -= CONJ(lu[k]) * v[i];",
+     "for (int64_t k = rp[i]; k < rp[i]; ++k)\n            v[ci[k]] -= CONJ(lu[k]) * v[i];"),
 ]
 
 # fast pins, in the order they are tried
@@ -83,6 +96,9 @@ PINS = [
     lambda o: P.test_cd2d_agrees_with_dense_lu(o, 4),
     lambda o: P.test_precond_equals_method_on_right_scaled_system(o, False),
     lambda o: P.test_precond_finite_termination(o, 8, 3),
+    lambda o: P.test_ilu0_reproduces_A_on_its_pattern(o, True, 0.2),
+    lambda o: P.test_ilu_minv_and_minv_h_match_dense_solves(o, True),
+    lambda o: P.test_ilu_precond_equals_method_on_right_preconditioned_system(o, False),
 ]
 
 

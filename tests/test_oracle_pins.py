@@ -431,3 +431,196 @@ def test_jacobi_diag_definition(orc):
     A = W.CSR(row_ptr=np.array([0, 2, 4, 5], dtype=np.int64), col=np.array([0, 0, 0, 2, 2], dtype=np.int32),
               val=np.array([1.0, 2.0, -3.0, 5.0, 7.0]), n_rows=3)
     np.testing.assert_array_equal(orc.jacobi_diag(A), [3.0, 0.0, 7.0])
+
+
+# ------------------------------------------- ILU(0) preconditioning --------
+# The paper's experiments precondition with ILU(0) (§5); Algorithm 7.1 takes
+# any M.  ILU(0) is pinned by its definition (Saad, Algorithm 10.4): L unit
+# lower and U upper triangular, both inside A's pattern, with (L U)_ij = a_ij
+# on that pattern; where elimination makes no fill outside the pattern this
+# is the exact LU factorisation.
+
+def _random_sparse(N, density, seed, cplx=False, shift=4.0):
+    """Random sparse matrix with a full diagonal, diagonally shifted."""
+    rng = np.random.default_rng(seed)
+    M = np.where(rng.uniform(size=(N, N)) < density, rng.standard_normal((N, N)), 0.0)
+    if cplx:
+        M = M + 1j * np.where(M != 0, rng.standard_normal((N, N)), 0.0)
+    M = M + shift * np.eye(N)
+    return W.dense_to_csr(M), M
+
+
+def _ilu_dense(A, f):
+    """Dense L (unit diagonal) and U from the factors in A's pattern."""
+    N = A.n_rows
+    L = np.eye(N, dtype=f.lu.dtype)
+    U = np.zeros((N, N), dtype=f.lu.dtype)
+    for r in range(N):
+        for k in range(A.row_ptr[r], A.row_ptr[r + 1]):
+            c = A.col[k]
+            if c < r:
+                L[r, c] = f.lu[k]
+            else:
+                U[r, c] = f.lu[k]
+        assert A.col[f.dpos[r]] == r
+    return L, U
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("density", [0.05, 0.2])
+def test_ilu0_reproduces_A_on_its_pattern(orc, cplx, density):
+    A, M = _random_sparse(60, density, seed=300 + int(100 * density), cplx=cplx)
+    f = orc.ilu0(A)
+    L, U = _ilu_dense(A, f)
+    P = M != 0
+    LU = L @ U
+    np.testing.assert_allclose(LU[P], M[P], rtol=0, atol=1e-12 * np.abs(M).max())
+    # fill outside the pattern exists (this is an incomplete factorisation)
+    if density == 0.2:
+        assert np.abs(LU[~P]).max() > 1e-3
+
+
+@pytest.mark.parametrize("kind", ["full", "tridiagonal", "lower", "upper"])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_ilu0_without_fill_is_the_exact_lu(orc, kind, cplx):
+    """Patterns whose elimination creates no fill (dense, tridiagonal,
+    triangular): ILU(0) = LU, so M^{-1} b is A^{-1} b (LAPACK)."""
+    N = 30
+    rng = np.random.default_rng(310 + len(kind))
+    M = rng.standard_normal((N, N)) + (1j * rng.standard_normal((N, N)) if cplx else 0)
+    if kind == "tridiagonal":
+        M = np.triu(np.tril(M, 1), -1)
+    elif kind == "lower":
+        M = np.tril(M)
+    elif kind == "upper":
+        M = np.triu(M)
+    M = M + 6.0 * np.eye(N)
+    A = W.dense_to_csr(M)
+    f = orc.ilu0(A)
+    L, U = _ilu_dense(A, f)
+    np.testing.assert_allclose(L @ U, M, rtol=0, atol=1e-12 * np.abs(M).max())
+    b = rng.standard_normal(N) + (1j * rng.standard_normal(N) if cplx else 0)
+    np.testing.assert_allclose(orc.minv(A, b, ilu=f), np.linalg.solve(M, b), rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_ilu_minv_and_minv_h_match_dense_solves(orc, cplx):
+    """M^{-1} v and M^{-H} v (Algorithm 7.1, steps 2, 31, 37) against LAPACK
+    on the dense M = L U, for an incomplete factorisation with fill."""
+    A, _ = _random_sparse(50, 0.15, seed=320, cplx=cplx)
+    f = orc.ilu0(A)
+    L, U = _ilu_dense(A, f)
+    Md = L @ U
+    rng = np.random.default_rng(321)
+    v = rng.standard_normal(50) + (1j * rng.standard_normal(50) if cplx else 0)
+    np.testing.assert_allclose(orc.minv(A, v, ilu=f), np.linalg.solve(Md, v), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(orc.minv_h(A, v, ilu=f), np.linalg.solve(Md.conj().T, v), rtol=1e-10, atol=1e-12)
+
+
+def test_ilu_minv_of_diagonal_pattern_is_jacobi(orc):
+    """A diagonal matrix: L = I, U = A, so M^{-1} is the Jacobi division
+    (bit for bit) and M^{-H} the division by the conjugate."""
+    d = np.random.default_rng(322).uniform(0.5, 2.0, 20) * np.exp(1j * np.linspace(0, 1, 20))
+    A = W.dense_to_csr(np.diag(d))
+    f = orc.ilu0(A)
+    v = np.random.default_rng(323).standard_normal(20) + 0j
+    np.testing.assert_array_equal(orc.minv(A, v, ilu=f), orc.minv(A, v, mdiag=d))
+    np.testing.assert_array_equal(orc.minv_h(A, v, ilu=f), orc.minv_h(A, v, mdiag=d))
+    # numpy's complex division may round the last bit differently from C's
+    np.testing.assert_allclose(orc.minv_h(A, v, ilu=f), v / d.conj(), rtol=4e-16, atol=0)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_ilu_precond_with_M_equal_A_converges_in_one_step(orc, cplx):
+    """On a dense pattern ILU(0) is A itself, so A M^{-1} = I: the first
+    step gives alpha = 1, x_1 = A^{-1} b and r_1 = 0 (up to rounding)."""
+    A, M, b = W.random_dense_system(25, seed=324, complex_=cplx)
+    Q = np.random.default_rng(325).standard_normal((25, 4))
+    res = orc.mlbicgstabt(A, b, np.zeros(25, dtype=b.dtype), Q, maxit=5, tol=1e-12, ilu=orc.ilu0(A))
+    assert res.flag == 0 and res.iter == 1
+    xs = np.linalg.solve(M, b)
+    assert np.linalg.norm(res.x - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_ilu_precond_equals_method_on_right_preconditioned_system(orc, cplx):
+    """Algorithm 7.1 with M = L U gives the residuals of the M = I method on
+    A' = A M^{-1} (formed densely with LAPACK), and x_k = M^{-1} y_k."""
+    N, n = 40, 4
+    A, _ = _random_sparse(N, 0.12, seed=326, cplx=cplx, shift=3.0)
+    f = orc.ilu0(A)
+    L, U = _ilu_dense(A, f)
+    Md = L @ U
+    Ap = W.dense_to_csr(A_dense(A) @ np.linalg.inv(Md))
+    rng = np.random.default_rng(327)
+    b = rng.standard_normal(N) + (1j * rng.standard_normal(N) if cplx else 0)
+    Q = rng.standard_normal((N, n)) + (1j * rng.standard_normal((N, n)) if cplx else 0)
+    x0 = np.zeros(N, dtype=b.dtype)
+    K = 15
+    rp = orc.mlbicgstabt(A, b, x0, Q, maxit=K, tol=0.0, err_hist=True, x_hist=K, ilu=f)
+    ry = orc.mlbicgstabt(Ap, b, x0, Q, maxit=K, tol=0.0, err_hist=True, x_hist=K)
+    np.testing.assert_allclose(rp.err_hist, ry.err_hist, rtol=1e-7)
+    for k in range(K):
+        xk = np.linalg.solve(Md, ry.x_hist[k])
+        assert np.linalg.norm(rp.x_hist[k] - xk) <= 1e-7 * np.linalg.norm(xk), k
+
+
+def A_dense(A):
+    D = np.zeros((A.n_rows, A.n_rows), dtype=A.val.dtype)
+    for r in range(A.n_rows):
+        D[r, A.col[A.row_ptr[r]:A.row_ptr[r + 1]]] += A.val[A.row_ptr[r]:A.row_ptr[r + 1]]
+    return D
+
+
+@pytest.mark.parametrize("N,n", [(8, 3), (9, 9)])
+def test_ilu_precond_finite_termination(orc, N, n):
+    """A M^{-1} is N x N: the ILU-preconditioned method stops by step N in
+    exact arithmetic; at tol 1e-14 it converges by iteration N and agrees
+    with LAPACK on A x = b."""
+    A, M = _random_sparse(N, 0.3, seed=330 + N + n)
+    b = np.random.default_rng(N).standard_normal(N)
+    Q = np.random.default_rng(N + 1).standard_normal((N, n))
+    res = orc.mlbicgstabt(A, b, np.zeros(N), Q, maxit=4 * N, tol=1e-14, ilu=orc.ilu0(A))
+    assert res.flag == 0 and res.iter <= N
+    xs = np.linalg.solve(M, b)
+    assert np.linalg.norm(res.x - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_ilu0_rejects_inputs_without_a_factorisation(orc):
+    # zero pivot: [[0, 1], [1, 0]] with the diagonal stored as zeros
+    Z = W.CSR(row_ptr=np.array([0, 2, 4], dtype=np.int64), col=np.array([0, 1, 0, 1], dtype=np.int32),
+              val=np.array([0.0, 1.0, 1.0, 0.0]), n_rows=2)
+    with pytest.raises(orc_mod().IluError) as e:
+        orc.ilu0(Z)
+    assert e.value.args[0] == -3
+    # a row without a stored diagonal entry
+    D = W.CSR(row_ptr=np.array([0, 1, 2], dtype=np.int64), col=np.array([1, 1], dtype=np.int32),
+              val=np.array([1.0, 2.0]), n_rows=2)
+    with pytest.raises(orc_mod().IluError) as e:
+        orc.ilu0(D)
+    assert e.value.args[0] == -1
+    # columns not increasing within a row
+    U = W.CSR(row_ptr=np.array([0, 2, 3], dtype=np.int64), col=np.array([1, 0, 1], dtype=np.int32),
+              val=np.array([1.0, 2.0, 3.0]), n_rows=2)
+    with pytest.raises(orc_mod().IluError):
+        orc.ilu0(U)
+
+
+def orc_mod():
+    import oracle
+    return oracle
+
+
+def test_ilu_precond_cuts_iterations_on_convection_diffusion(orc):
+    """ILU(0) is the preconditioner the paper's experiments use (§5); on
+    the 2-D convection-diffusion system it must converge to the same
+    solution as M = I in far fewer iterations."""
+    A = W.cd2d(32)
+    b = W.row_sums(A)
+    N = A.n_rows
+    Q = orc.q_gauss(0, N, 4)
+    r0 = orc.solve(A, b, np.zeros(N), Q, 3000, 1e-10)
+    r1 = orc.solve(A, b, np.zeros(N), Q, 3000, 1e-10, ilu=orc.ilu0(A))
+    assert r0.flag == 0 and r1.flag == 0
+    assert r1.iter * 2 < r0.iter
+    np.testing.assert_allclose(r1.x, 1.0, rtol=1e-7)
