@@ -55,6 +55,7 @@ extern "C" {
 /* Preconditioner M of Algorithm 7.1 (right preconditioning). */
 #define MLB_PRECOND_NONE 0   /* M = I: Algorithm 4.1 */
 #define MLB_PRECOND_JACOBI 1 /* M = diag(A) (every diagonal entry nonzero) */
+#define MLB_PRECOND_ILU0 2   /* M = L U, the ILU(0) factors of A (FP64 only) */
 
 #define MLB_PREC_FP64 0     /* matrix, vectors and arithmetic in FP64 */
 #define MLB_PREC_FP32_REFINED 1 /* inner ML(n)BiCGStab in FP32 (values,
@@ -111,7 +112,20 @@ typedef struct {
                              back to x = M^{-1} y, which is the algorithm's
                              x-recurrence along g^ = M^{-1} g (steps 6, 35,
                              39).  Stopping rule and residuals are those of
-                             A x = b. */
+                             A x = b.
+                             MLB_PRECOND_ILU0: M = L U, the ILU(0)
+                             factors of A (the preconditioner of the
+                             paper's experiments, §5; L unit lower and U
+                             upper triangular in A's pattern with
+                             (LU)_ij = a_ij there), computed on the host at
+                             create.  Every product of the iteration is
+                             A (M^{-1} v), M^{-1} by level-scheduled
+                             triangular solves on the device; F = M^{-H}
+                             A^H Q; the solve iterates on y = M x, mapped in
+                             the kernel.  FP64 precision only
+                             (MLB_ERR_UNSUPPORTED otherwise); MLB_ERR_ARG
+                             when a row has no stored diagonal or a pivot
+                             is zero. */
     int32_t reserved0;    /* must be 0 */
 } mlb_options;
 

@@ -24,6 +24,13 @@ struct mlb_handle {
     int n_active = 4;   // shadow vectors the next solve uses (<= n)
     int precond = MLB_PRECOND_NONE;
     void *mdiag = nullptr;   // diagonal of M (Jacobi), device, N values
+    // ILU(0) factors and level sets (device; see IluHost)
+    int64_t *ilu_rp = nullptr;
+    int32_t *ilu_ci = nullptr, *ilu_dpos = nullptr;
+    int32_t *ilu_lrows = nullptr, *ilu_lptr = nullptr, *ilu_urows = nullptr, *ilu_uptr = nullptr;
+    void *ilu_lu = nullptr, *ilu_t = nullptr;
+    int ilu_nlev_l = 0, ilu_nlev_u = 0;
+    int64_t ilu_nnz = 0;
     int precision = MLB_PREC_FP64;
     int64_t N = 0, ld = 0, nnz = 0, nnz_pad = 0, nslices = 0;
     int64_t maxw = 0;   // widest SELL-32 slice (entries per row)
@@ -220,6 +227,21 @@ SysView<T> make_view(const mlb_handle *h) {
     v.z = (T *)h->z;
     v.b = (T *)h->b;
     v.n = h->n_active;
+    v.ilu = IluView<T>{};
+    if (h->precond == MLB_PRECOND_ILU0) {
+        v.ilu.rp = h->ilu_rp;
+        v.ilu.ci = h->ilu_ci;
+        v.ilu.lu = (const T *)h->ilu_lu;
+        v.ilu.dpos = h->ilu_dpos;
+        v.ilu.lrows = h->ilu_lrows;
+        v.ilu.lptr = h->ilu_lptr;
+        v.ilu.urows = h->ilu_urows;
+        v.ilu.uptr = h->ilu_uptr;
+        v.ilu.nlev_l = h->ilu_nlev_l;
+        v.ilu.nlev_u = h->ilu_nlev_u;
+        v.ilu.nnz = h->ilu_nnz;
+        v.ilu.t = (T *)h->ilu_t;
+    }
     return v;
 }
 
@@ -243,6 +265,7 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.z = (T32 *)h->z32;
     v.b = (T32 *)h->b32;
     v.n = h->n_active;
+    v.ilu = IluView<T32>{};
     return v;
 }
 
@@ -274,9 +297,10 @@ bool is_device_ptr(const void *p) {
 
 // With a preconditioner the kernels iterate on y = M x (A M^{-1} y = b):
 // before a solve the caller's x_0 becomes y_0 = M x_0, afterwards the
-// result y becomes x = M^{-1} y, on the handle's buffer h->x.
+// result y becomes x = M^{-1} y, on the handle's buffer h->x.  Here for
+// the Jacobi M; the solve kernel maps ILU(0) itself.
 int map_solution(mlb_handle *h, bool to_x, cudaStream_t st) {
-    if (h->precond == MLB_PRECOND_NONE) return MLB_OK;
+    if (h->precond != MLB_PRECOND_JACOBI) return MLB_OK;
     cudaError_t e = h->dtype == MLB_C128
                         ? launch_diag_apply<cdouble>((cdouble *)h->x, (const cdouble *)h->mdiag, h->N, to_x, st)
                         : launch_diag_apply<double>((double *)h->x, (const double *)h->mdiag, h->N, to_x, st);
@@ -327,7 +351,13 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     h->n = o->n;
     h->n_active = o->n;
     h->precond = o->precond;
-    // with a preconditioner the handle stores A M^{-1} (and M^{-H} A^H)
+    // ILU(0): factors and level sets on the host (the handle keeps A itself)
+    IluHost ih;
+    if (o->precond == MLB_PRECOND_ILU0) {
+        const int rci = ilu0_build(A, ih);
+        if (rci) return rci;
+    }
+    // with a Jacobi preconditioner the handle stores A M^{-1} (and M^{-H} A^H)
     std::vector<char> jd, jav, jahv;
     mlb_matrix As, AHs;
     if (o->precond == MLB_PRECOND_JACOBI) {
@@ -401,6 +431,30 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         if ((rc = dev_alloc(h, &h->mdiag, vb))) return rc;
         MLB_CUDA(cudaMemcpy(h->mdiag, jd.data(), (size_t)h->N * es, cudaMemcpyHostToDevice));
     }
+    if (h->precond == MLB_PRECOND_ILU0) {
+        const int64_t N = h->N;
+        h->ilu_nnz = ih.nnz;
+        h->ilu_nlev_l = ih.nlev_l;
+        h->ilu_nlev_u = ih.nlev_u;
+        if ((rc = dev_alloc_t(h, &h->ilu_rp, (size_t)(N + 1) * 8))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_ci, (size_t)ih.nnz * 4))) return rc;
+        if ((rc = dev_alloc(h, &h->ilu_lu, (size_t)ih.nnz * es))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_dpos, (size_t)N * 4))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_lrows, (size_t)N * 4))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_lptr, ih.lptr.size() * 4))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_urows, (size_t)N * 4))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_uptr, ih.uptr.size() * 4))) return rc;
+        if ((rc = dev_alloc(h, &h->ilu_t, vb))) return rc;
+        MLB_CUDA(cudaMemcpy(h->ilu_rp, ih.rp.data(), (size_t)(N + 1) * 8, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_ci, ih.ci.data(), (size_t)ih.nnz * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_lu, ih.lu.data(), (size_t)ih.nnz * es, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_dpos, ih.dpos.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_lrows, ih.lrows.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_lptr, ih.lptr.data(), ih.lptr.size() * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_urows, ih.urows.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_uptr, ih.uptr.data(), ih.uptr.size() * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemsetAsync(h->ilu_t, 0, vb, st));
+    }
 
     // shadow vectors
     if (o->Q) {
@@ -458,6 +512,16 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         cudaFree(dci);
         cudaFree(dav);
         if (e != cudaSuccess) return MLB_ERR_CUDA;
+        // ILU(0): F = M^{-H} (A^H Q), column by column on the host
+        if (h->precond == MLB_PRECOND_ILU0) {
+            std::vector<char> col((size_t)h->N * es);
+            for (int m = 0; m < n - 1; ++m) {
+                char *dcol = (char *)h->F + (size_t)m * ld * es;
+                MLB_CUDA(cudaMemcpy(col.data(), dcol, col.size(), cudaMemcpyDeviceToHost));
+                ilu0_apply_h(ih, cplx, col.data());
+                MLB_CUDA(cudaMemcpy(dcol, col.data(), col.size(), cudaMemcpyHostToDevice));
+            }
+        }
     }
 
     // refined mode: FP32 copies of the values, Q and F; FP32 work vectors
@@ -578,7 +642,10 @@ int mlbicgstab_create(mlb_handle **out, const mlb_matrix *A, const mlb_matrix *A
     if (o.n < 1 || o.n > kMaxN) return MLB_ERR_ARG;
     if (o.precision != MLB_PREC_FP64 && o.precision != MLB_PREC_FP32_REFINED) return MLB_ERR_ARG;
     if (o.kappa < 0.0 || o.max_outer < 0 || o.timeout_ns <= 0) return MLB_ERR_ARG;
-    if ((o.precond != MLB_PRECOND_NONE && o.precond != MLB_PRECOND_JACOBI) || o.reserved0 != 0) return MLB_ERR_ARG;
+    if ((o.precond != MLB_PRECOND_NONE && o.precond != MLB_PRECOND_JACOBI && o.precond != MLB_PRECOND_ILU0) ||
+        o.reserved0 != 0)
+        return MLB_ERR_ARG;
+    if (o.precond == MLB_PRECOND_ILU0 && o.precision != MLB_PREC_FP64) return MLB_ERR_UNSUPPORTED;
     int rc = validate_csr(A);
     if (rc) return rc;
     if (AH) {

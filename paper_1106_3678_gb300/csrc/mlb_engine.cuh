@@ -72,6 +72,28 @@ struct Acct {
     cdouble z[4];
 };
 
+// ILU(0) preconditioner M = L U of Algorithm 7.1 (the preconditioner of
+// the paper's experiments, §5), stored in A's pattern: in row i, entries
+// before the diagonal are L's (unit diagonal implied), the rest U's.  The
+// solve iterates on y = M x, with every product A M^{-1} v formed as
+// A (M^{-1} v).  Rows are grouped by level for the triangular solves: a
+// row of level l depends only on rows of lower levels (of L, or of U taken
+// from the last row upwards).  lu == nullptr: no ILU(0) preconditioner.
+template <typename T>
+struct IluView {
+    const int64_t *rp;          // N+1; columns increase within each row
+    const int32_t *ci;
+    const T *lu;
+    const int32_t *dpos;        // position of row i's diagonal, relative to rp[i]
+    const int32_t *lrows;       // rows of L's levels: level l = lrows[lptr[l] .. lptr[l+1])
+    const int32_t *lptr;
+    const int32_t *urows;       // rows of U's levels
+    const int32_t *uptr;
+    int nlev_l, nlev_u;
+    int64_t nnz;
+    T *t;                       // ld: M^{-1} of the current product's input
+};
+
 // Device view of one linear system.  Vectors have leading dimension `ld`
 // (a multiple of 512 elements); entries N..ld-1 are zero and stay zero.
 template <typename T>
@@ -88,6 +110,7 @@ struct SysView {
     T *x, *r, *z;               // ld
     T *b;                       // ld (written only by the refined-mode inner start)
     int n;
+    IluView<T> ilu;             // ILU(0) preconditioner (ilu.lu == nullptr: none)
 };
 
 struct SolveCtl {
@@ -117,6 +140,13 @@ __device__ __forceinline__ cdouble ldg_val(const cdouble *p) {
 }
 __device__ __forceinline__ cfloat ldg_val(const cfloat *p) {
     float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return {v.x, v.y};
+}
+// Loads through L2 only: values another CTA wrote since the last team
+// barrier (an SM's L1 may still hold an older copy of the line).
+__device__ __forceinline__ double ldcg_val(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ cdouble ldcg_val(const cdouble *p) {
+    double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
     return {v.x, v.y};
 }
 __device__ __forceinline__ double ldcs_val(const double *p) { return __ldcs(p); }
@@ -614,6 +644,16 @@ struct Engine {
     // reports it.
     template <int K, int NE, typename Fin>
     __device__ __forceinline__ void spmv_rows(const T *xin, const T *const (&epi)[NE], Fin fin, ACC (&acc)[K]) {
+        if constexpr (!is_narrow<T>::value) {
+            // with ILU(0) the product is A (M^{-1} xin)
+            if (sys.ilu.lu) {
+                if (!ilu_solve(xin, sys.ilu.t)) {
+                    gs.ring->failed = 1;
+                    return;
+                }
+                xin = sys.ilu.t;
+            }
+        }
         unsigned sq = gs.seq();   // issued (producer lane) or consumed (consumers) tiles
         const bool okw = sell_spmv<NE>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
                                        sys.scol, sys.sval, xin, epi, threadIdx.x & 31, fin, acc);
@@ -623,6 +663,82 @@ struct Engine {
     __device__ __forceinline__ bool ring_ok() {
         if (gs.ring->failed) { gs.ok = false; return false; }
         return true;
+    }
+
+    // ------------------------------------------------------------------
+    // ILU(0) preconditioner (Algorithm 7.1 with M = L U)
+    // ------------------------------------------------------------------
+
+    // out = M^{-1} v: L z = v by forward substitution (unit diagonal), then
+    // U out = z by backward substitution, in place.  Level scheduling: all
+    // rows of one level at once over the team's threads, a team barrier
+    // between levels.  Each row is one sequential sum in pattern order, as
+    // in the definition; U's diagonal divides.
+    __device__ __noinline__ bool ilu_solve(const T *v, T *out) {
+        const IluView<T> &M = sys.ilu;
+        const int64_t nth = (int64_t)gs.nblocks * kThreads;
+        const int64_t me = (int64_t)gs.bid * kThreads + threadIdx.x;
+        const int64_t *rp = M.rp;
+        const int32_t *ci = M.ci, *dp = M.dpos;
+        const T *lu = M.lu;
+        for (int l = 0; l < M.nlev_l; ++l) {
+            const int64_t hi = M.lptr[l + 1];
+            for (int64_t q = M.lptr[l] + me; q < hi; q += nth) {
+                const int i = M.lrows[q];
+                const int64_t k0 = rp[i], kd = k0 + dp[i];
+                T s = v[i];
+                for (int64_t k = k0; k < kd; ++k) s = efma(-lu[k], ldcg_val(out + ci[k]), s);
+                out[i] = s;
+            }
+            if (!gs.sync()) return false;
+        }
+        for (int l = 0; l < M.nlev_u; ++l) {
+            const int64_t hi = M.uptr[l + 1];
+            for (int64_t q = M.uptr[l] + me; q < hi; q += nth) {
+                const int i = M.urows[q];
+                const int64_t kd = rp[i] + dp[i], k1 = rp[i + 1];
+                T s = ldcg_val(out + i);
+                for (int64_t k = kd + 1; k < k1; ++k) s = efma(-lu[k], ldcg_val(out + ci[k]), s);
+                out[i] = s / lu[kd];
+            }
+            if (!gs.sync()) return false;
+        }
+        if (threadIdx.x == 0)   // factors and row data once, v read, out written and re-read
+            acct->bytes += (double)M.nnz * (sizeof(T) + 4) + (double)sys.N * (8 + 4 + 8 + 3 * sizeof(T));
+        return true;
+    }
+
+    // y_0 = M x_0 = L (U x_0), in place on x: t = U x, then x = L t (two
+    // row-parallel products).
+    __device__ __noinline__ bool ilu_to_y() {
+        const IluView<T> &M = sys.ilu;
+        const int64_t nth = (int64_t)gs.nblocks * kThreads;
+        const int64_t me = (int64_t)gs.bid * kThreads + threadIdx.x;
+        T *const x = sys.x, *const t = M.t;
+        for (int64_t i = me; i < sys.N; i += nth) {
+            const int64_t kd = M.rp[i] + M.dpos[i], k1 = M.rp[i + 1];
+            T s{};
+            for (int64_t k = kd; k < k1; ++k) s = efma(M.lu[k], x[M.ci[k]], s);
+            t[i] = s;
+        }
+        if (!gs.sync()) return false;
+        for (int64_t i = me; i < sys.N; i += nth) {
+            const int64_t k0 = M.rp[i], kd = k0 + M.dpos[i];
+            T s = ldcg_val(t + i);
+            for (int64_t k = k0; k < kd; ++k) s = efma(M.lu[k], ldcg_val(t + M.ci[k]), s);
+            x[i] = s;
+        }
+        return gs.sync();
+    }
+
+    // x = M^{-1} y once the final residual pass has formed t = M^{-1} y.
+    __device__ __noinline__ bool ilu_to_x() {
+        const int64_t nth = (int64_t)gs.nblocks * kThreads;
+        const int64_t me = (int64_t)gs.bid * kThreads + threadIdx.x;
+        T *const x = sys.x;
+        const T *t = sys.ilu.t;
+        for (int64_t i = me; i < sys.N; i += nth) x[i] = ldcg_val(t + i);
+        return gs.sync();
     }
 
     // ------------------------------------------------------------------

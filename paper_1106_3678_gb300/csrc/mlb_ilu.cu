@@ -1,0 +1,145 @@
+// Host side of the ILU(0) preconditioner (Algorithm 7.1 with M = L U; the
+// paper's experiments precondition with ILU(0), §5): the factors in A's
+// pattern, the level sets of the two triangular solves, and M^{-H} v for
+// the setup product F = M^{-H} A^H Q.  The triangular solves of the
+// iteration run on the device (Engine::ilu_solve).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <utility>
+
+#include "mlb_internal.h"
+
+namespace mlb {
+namespace {
+
+inline double cj(double v) { return v; }
+inline std::complex<double> cj(std::complex<double> v) { return std::conj(v); }
+
+// Rows grouped by level: level(i) = 1 + the largest level among the rows
+// row i reads (0 if none), rows ascending within a level.
+void group_levels(const std::vector<int32_t> &lev, int nlev, std::vector<int32_t> &rows,
+                  std::vector<int32_t> &ptr) {
+    ptr.assign(nlev + 1, 0);
+    for (int32_t l : lev) ptr[l + 1]++;
+    for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
+    rows.assign(lev.size(), 0);
+    std::vector<int32_t> next(ptr.begin(), ptr.end() - 1);
+    for (size_t i = 0; i < lev.size(); ++i) rows[next[lev[i]]++] = (int32_t)i;
+}
+
+template <typename V>
+int build_t(const mlb_matrix *A, IluHost &f) {
+    const int64_t N = A->nrows;
+    const V *a = (const V *)A->values;
+    // A's pattern with columns increasing in each row; repeated entries of
+    // a row are one entry (their sum)
+    f.rp.assign(N + 1, 0);
+    f.dpos.assign(N, -1);
+    std::vector<int32_t> ci;
+    std::vector<V> val;
+    ci.reserve(A->nnz);
+    val.reserve(A->nnz);
+    std::vector<std::pair<int32_t, int64_t>> row;
+    for (int64_t r = 0; r < N; ++r) {
+        row.clear();
+        for (int64_t k = A->row_ptr[r]; k < A->row_ptr[r + 1]; ++k) row.emplace_back(A->col_idx[k], k);
+        std::stable_sort(row.begin(), row.end(),
+                         [](const std::pair<int32_t, int64_t> &p, const std::pair<int32_t, int64_t> &q) {
+                             return p.first < q.first;
+                         });
+        const int64_t start = (int64_t)ci.size();
+        for (const auto &e : row) {
+            if ((int64_t)ci.size() > start && ci.back() == e.first) {
+                val.back() += a[e.second];
+            } else {
+                ci.push_back(e.first);
+                val.push_back(a[e.second]);
+            }
+        }
+        for (int64_t k = start; k < (int64_t)ci.size(); ++k)
+            if (ci[k] == r) f.dpos[r] = (int32_t)(k - start);
+        if (f.dpos[r] < 0) return MLB_ERR_ARG;   // ILU(0) needs a stored diagonal
+        f.rp[r + 1] = (int64_t)ci.size();
+    }
+    // elimination restricted to the pattern, one row at a time: for each
+    // k < i stored in row i (increasing k), l_ik = a_ik / u_kk, then
+    // a_ij -= l_ik u_kj for the j > k stored in both rows i and k
+    std::vector<int64_t> at(N, -1);   // position of column j in the current row
+    int rc = MLB_OK;
+    for (int64_t i = 0; i < N && rc == MLB_OK; ++i) {
+        const int64_t r0 = f.rp[i], r1 = f.rp[i + 1], di = r0 + f.dpos[i];
+        for (int64_t k = r0; k < r1; ++k) at[ci[k]] = k;
+        for (int64_t p = r0; p < di; ++p) {
+            const int64_t k = ci[p];
+            const int64_t dk = f.rp[k] + f.dpos[k];
+            val[p] = val[p] / val[dk];
+            const V lik = val[p];
+            for (int64_t q = dk + 1; q < f.rp[k + 1]; ++q) {
+                const int64_t t = at[ci[q]];
+                if (t >= 0) val[t] -= lik * val[q];
+            }
+        }
+        for (int64_t k = r0; k < r1; ++k) at[ci[k]] = -1;
+        // a zero or non-finite pivot has no ILU(0)
+        if (!(std::abs(val[di]) > 0.0) || !std::isfinite(std::abs(val[di]))) rc = MLB_ERR_ARG;
+    }
+    if (rc) return rc;
+    for (const V &v : val)
+        if (!std::isfinite(std::abs(v))) return MLB_ERR_ARG;
+    f.ci = std::move(ci);
+    f.lu.assign((const char *)val.data(), (const char *)(val.data() + val.size()));
+    f.nnz = (int64_t)val.size();
+    // level sets: L from the first row down, U from the last row up
+    std::vector<int32_t> lev(N, 0);
+    int nl = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t l = 0;
+        for (int64_t k = f.rp[i]; k < f.rp[i] + f.dpos[i]; ++k) l = std::max(l, lev[f.ci[k]] + 1);
+        lev[i] = l;
+        nl = std::max(nl, l + 1);
+    }
+    group_levels(lev, nl, f.lrows, f.lptr);
+    f.nlev_l = nl;
+    int nu = 0;
+    for (int64_t i = N - 1; i >= 0; --i) {
+        int32_t l = 0;
+        for (int64_t k = f.rp[i] + f.dpos[i] + 1; k < f.rp[i + 1]; ++k) l = std::max(l, lev[f.ci[k]] + 1);
+        lev[i] = l;
+        nu = std::max(nu, l + 1);
+    }
+    group_levels(lev, nu, f.urows, f.uptr);
+    f.nlev_u = nu;
+    return MLB_OK;
+}
+
+// v <- M^{-H} v with M^H = U^H L^H: U^H t = v (U^H is lower triangular;
+// row i of U is column i of U^H), then L^H v = t (unit upper triangular).
+template <typename V>
+void apply_h_t(const IluHost &f, V *v) {
+    const int64_t N = (int64_t)f.rp.size() - 1;
+    const V *lu = (const V *)f.lu.data();
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t d = f.rp[i] + f.dpos[i];
+        v[i] = v[i] / cj(lu[d]);
+        const V vi = v[i];
+        for (int64_t k = d + 1; k < f.rp[i + 1]; ++k) v[f.ci[k]] -= cj(lu[k]) * vi;
+    }
+    for (int64_t i = N - 1; i >= 0; --i) {
+        const V vi = v[i];
+        for (int64_t k = f.rp[i]; k < f.rp[i] + f.dpos[i]; ++k) v[f.ci[k]] -= cj(lu[k]) * vi;
+    }
+}
+
+}  // namespace
+
+int ilu0_build(const mlb_matrix *A, IluHost &out) {
+    return A->dtype == MLB_C128 ? build_t<std::complex<double>>(A, out) : build_t<double>(A, out);
+}
+
+void ilu0_apply_h(const IluHost &f, bool cplx, void *v) {
+    if (cplx) apply_h_t(f, (std::complex<double> *)v);
+    else apply_h_t(f, (double *)v);
+}
+
+}  // namespace mlb

@@ -4,7 +4,9 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
+#include "../../include/mlbicgstab.h"
 #include "mlb_engine.cuh"
 #include "mlb_refine.cuh"
 
@@ -87,6 +89,24 @@ template <typename T>
 cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
                                    int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
                                    cudaStream_t st);
+
+// ILU(0) preconditioner, host side (mlb_ilu.cu).  Factors of A in A's
+// pattern (columns increasing within each row, repeated entries merged):
+// entries before row i's diagonal are L's (unit diagonal implied), the rest
+// U's; dpos[i] = position of the diagonal relative to rp[i]; rows grouped
+// into the level sets of the forward (L) and backward (U) solves.
+struct IluHost {
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci, dpos, lrows, lptr, urows, uptr;
+    std::vector<char> lu;   // nnz values of the handle's dtype
+    int64_t nnz = 0;
+    int nlev_l = 0, nlev_u = 0;
+};
+// MLB_OK, or MLB_ERR_ARG when a row has no stored diagonal or a pivot is
+// zero or not finite.
+int ilu0_build(const mlb_matrix *A, IluHost &out);
+// v <- M^{-H} v for the N values at v (M = L U from `f`).
+void ilu0_apply_h(const IluHost &f, bool cplx, void *v);
 
 // Failure-detection self-test of the grid barrier (see the C ABI).
 cudaError_t launch_barrier_selftest(int grid, BarrierState *bs,

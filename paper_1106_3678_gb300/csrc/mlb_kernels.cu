@@ -20,7 +20,12 @@ __device__ void run_fp64_solve(Engine<T> &E, GridSync &gs, const SolveCtl &ctl, 
     int64_t total = 0;
     int outer = 0;
     typename Engine<T>::Out o{1, 0, 0, 0, 0.0};
+    // ILU(0): the method iterates on y = M x (y_0 = M x_0; x = M^{-1} y at
+    // the end, from the final residual pass, which forms M^{-1} y)
+    const bool ilu = E.sys.ilu.lu != nullptr;
+    if (ilu) E.ilu_to_y();
     for (;;) {
+        if (!gs.ok) break;
         o = E.inner(ctl.maxit - total, outer == 0, ctl.tol);
         if (!gs.ok) break;
         total += o.iter;
@@ -37,6 +42,7 @@ __device__ void run_fp64_solve(Engine<T> &E, GridSync &gs, const SolveCtl &ctl, 
             double bn = sqrt(bb);
             if (bn == 0.0) bn = 1.0;
             true_rel = sqrt(rr) / bn;
+            if (ilu) E.ilu_to_x();
         }
     }
     if (gs.bid == 0 && threadIdx.x == 0) {

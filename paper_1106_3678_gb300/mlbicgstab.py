@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmlbicgstab.so")
 MLB_OK, MLB_ERR_ARG, MLB_ERR_CUDA, MLB_ERR_OOM, MLB_ERR_TIMEOUT, MLB_ERR_UNSUPPORTED = range(6)
 MLB_F64, MLB_C128 = 0, 2
 MLB_PREC_FP64, MLB_PREC_FP32_REFINED = 0, 1
-MLB_PRECOND_NONE, MLB_PRECOND_JACOBI = 0, 1
+MLB_PRECOND_NONE, MLB_PRECOND_JACOBI, MLB_PRECOND_ILU0 = 0, 1, 2
 
 # Every symbol the header declares (checked against the header by a test).
 EXPORTS = (

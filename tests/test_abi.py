@@ -101,6 +101,9 @@ def test_invalid_arguments_are_rejected_before_gpu_work(lib):
     assert _raw_create(lib, A, kappa=-1.0)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, precision=7)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, precond=5)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, precond=3)[0] == M.MLB_ERR_ARG
+    # ILU(0) runs in FP64 only
+    assert _raw_create(lib, A, precond=M.MLB_PRECOND_ILU0, precision=1)[0] == M.MLB_ERR_UNSUPPORTED
     assert _raw_create(lib, A, reserved0=1)[0] == M.MLB_ERR_ARG
     bad = W.CSR(A.row_ptr.copy(), A.col.copy(), A.val.copy(), A.n_rows)
     bad.col[3] = A.n_rows          # column out of range
