@@ -217,11 +217,15 @@ constexpr int kStatusTimeout = 4;  // == MLB_ERR_TIMEOUT
 // the same sequence, so barrier e completes when the counter reaches
 // e * expected.  The spin is bounded by timeout_ns (%globaltimer) and
 // gives up early when another CTA has already recorded a failure.
-__device__ __forceinline__ bool grid_arrive_wait(BarrierState *bs, unsigned &epoch, unsigned expected,
-                                                 uint64_t timeout_ns) {
+// grid_arrive and grid_wait are its two halves, for callers with work to
+// overlap with the wait.
+__device__ __forceinline__ void grid_arrive(BarrierState *bs, unsigned &epoch) {
     epoch += 1;
-    const unsigned target = epoch * expected;
     red_release_add_u32(&bs->count, 1u);
+}
+__device__ __forceinline__ bool grid_wait(BarrierState *bs, unsigned epoch, unsigned expected,
+                                          uint64_t timeout_ns) {
+    const unsigned target = epoch * expected;
     uint64_t t0 = 0;
     unsigned spins = 0;
     while ((int)(ld_acquire_u32(&bs->count) - target) < 0) {
@@ -239,6 +243,11 @@ __device__ __forceinline__ bool grid_arrive_wait(BarrierState *bs, unsigned &epo
     }
     fence_acq_rel_gpu();
     return true;
+}
+__device__ __forceinline__ bool grid_arrive_wait(BarrierState *bs, unsigned &epoch, unsigned expected,
+                                                 uint64_t timeout_ns) {
+    grid_arrive(bs, epoch);
+    return grid_wait(bs, epoch, expected, timeout_ns);
 }
 
 // Whole-CTA grid barrier: every thread calls it; returns false (uniformly

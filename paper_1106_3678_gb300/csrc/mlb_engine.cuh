@@ -518,6 +518,22 @@ struct GridSync {
         if (nblocks == 1) return true;
         return gbar();
     }
+
+    // sync() in two halves: arrive() once this CTA's writes are done,
+    // wait() before reading other CTAs' writes; work between the two that
+    // reads nothing written in this step overlaps the wait.  Every thread
+    // calls both; wait() returns false (uniformly) when the barrier failed.
+    __device__ __forceinline__ void arrive() {
+        __syncthreads();
+        if (nblocks > 1 && threadIdx.x == 0) grid_arrive(bar, epoch);
+    }
+    __device__ __forceinline__ bool wait() {
+        if (nblocks == 1) return true;   // arrive()'s __syncthreads ordered the CTA
+        if (threadIdx.x == 0) *sflag = grid_wait(bar, epoch, nblocks, timeout_ns) ? 1 : 0;
+        __syncthreads();
+        if (*sflag == 0) { ok = false; return false; }
+        return true;
+    }
 };
 
 template <typename T>
@@ -669,39 +685,114 @@ struct Engine {
     // ILU(0) preconditioner (Algorithm 7.1 with M = L U)
     // ------------------------------------------------------------------
 
+    // One row of a triangular solve, loaded ahead: its index, up to
+    // kIluReg entries (column, factor value) in registers, where the rest
+    // of its entries start and end, and the row's right-hand-side entry
+    // (forward) or its U diagonal (backward).  i < 0: no row.
+    static constexpr int kIluReg = 4;
+    struct IluRow {
+        int i, cnt;
+        int64_t rest, end;
+        int32_t c[kIluReg];
+        T a[kIluReg];
+        T v;
+    };
+    // Row q of L's level order (forward: entries before the diagonal).
+    __device__ __forceinline__ void ilu_fetch_l(int64_t q, int64_t hi, const T *v, IluRow &R) const {
+        R.i = -1;
+        if (q >= hi) return;
+        const IluView<T> &M = sys.ilu;
+        const int i = M.lrows[q];
+        const int64_t k0 = M.rp[i], kd = k0 + M.dpos[i];
+        const int cnt = (int)min(kd - k0, (int64_t)kIluReg);
+#pragma unroll
+        for (int e = 0; e < kIluReg; ++e)
+            if (e < cnt) {
+                R.c[e] = M.ci[k0 + e];
+                R.a[e] = M.lu[k0 + e];
+            }
+        R.i = i;
+        R.cnt = cnt;
+        R.rest = k0 + cnt;
+        R.end = kd;
+        R.v = v[i];
+    }
+    // Row q of U's level order (backward: entries after the diagonal).
+    __device__ __forceinline__ void ilu_fetch_u(int64_t q, int64_t hi, IluRow &R) const {
+        R.i = -1;
+        if (q >= hi) return;
+        const IluView<T> &M = sys.ilu;
+        const int i = M.urows[q];
+        const int64_t kd = M.rp[i] + M.dpos[i], k1 = M.rp[i + 1];
+        const int cnt = (int)min(k1 - kd - 1, (int64_t)kIluReg);
+#pragma unroll
+        for (int e = 0; e < kIluReg; ++e)
+            if (e < cnt) {
+                R.c[e] = M.ci[kd + 1 + e];
+                R.a[e] = M.lu[kd + 1 + e];
+            }
+        R.i = i;
+        R.cnt = cnt;
+        R.rest = kd + 1 + cnt;
+        R.end = k1;
+        R.v = M.lu[kd];
+    }
+    // s - sum of a_e out[c_e] over the row's entries, in pattern order.
+    __device__ __forceinline__ T ilu_row_sum(const IluRow &R, T s, const T *out) const {
+        const IluView<T> &M = sys.ilu;
+#pragma unroll
+        for (int e = 0; e < kIluReg; ++e)
+            if (e < R.cnt) s = efma(-R.a[e], ldcg_val(out + R.c[e]), s);
+        for (int64_t k = R.rest; k < R.end; ++k) s = efma(-M.lu[k], ldcg_val(out + M.ci[k]), s);
+        return s;
+    }
+
     // out = M^{-1} v: L z = v by forward substitution (unit diagonal), then
     // U out = z by backward substitution, in place.  Level scheduling: all
     // rows of one level at once over the team's threads, a team barrier
     // between levels.  Each row is one sequential sum in pattern order, as
-    // in the definition; U's diagonal divides.
+    // in the definition; U's diagonal divides.  A thread's first row of the
+    // next level (index, entries, right-hand side or diagonal) does not
+    // depend on the current level, so it is loaded while the barrier is
+    // pending, and only the values of earlier levels are read after it.
     __device__ __noinline__ bool ilu_solve(const T *v, T *out) {
         const IluView<T> &M = sys.ilu;
         const int64_t nth = (int64_t)gs.nblocks * kThreads;
-        const int64_t me = (int64_t)gs.bid * kThreads + threadIdx.x;
-        const int64_t *rp = M.rp;
-        const int32_t *ci = M.ci, *dp = M.dpos;
-        const T *lu = M.lu;
-        for (int l = 0; l < M.nlev_l; ++l) {
+        // a level's rows go round-robin over the CTAs (a level is a few
+        // thousand scattered rows: in CTA-sized blocks a few SMs would
+        // carry every level, each with thousands of scattered loads)
+        const int64_t me = (int64_t)threadIdx.x * gs.nblocks + gs.bid;
+        const int nl = M.nlev_l, nu = M.nlev_u;
+        IluRow R;
+        ilu_fetch_l(me, M.lptr[1], v, R);
+        for (int l = 0; l < nl; ++l) {
             const int64_t hi = M.lptr[l + 1];
-            for (int64_t q = M.lptr[l] + me; q < hi; q += nth) {
+            if (R.i >= 0) out[R.i] = ilu_row_sum(R, R.v, out);
+            for (int64_t q = M.lptr[l] + me + nth; q < hi; q += nth) {   // more rows than threads
                 const int i = M.lrows[q];
-                const int64_t k0 = rp[i], kd = k0 + dp[i];
-                T s = v[i];
-                for (int64_t k = k0; k < kd; ++k) s = efma(-lu[k], ldcg_val(out + ci[k]), s);
-                out[i] = s;
+                const int64_t k0 = M.rp[i], kd = k0 + M.dpos[i];
+                T t = v[i];
+                for (int64_t k = k0; k < kd; ++k) t = efma(-M.lu[k], ldcg_val(out + M.ci[k]), t);
+                out[i] = t;
             }
-            if (!gs.sync()) return false;
+            gs.arrive();
+            if (l + 1 < nl) ilu_fetch_l(hi + me, M.lptr[l + 2], v, R);
+            else ilu_fetch_u(me, M.uptr[1], R);
+            if (!gs.wait()) return false;
         }
-        for (int l = 0; l < M.nlev_u; ++l) {
+        for (int l = 0; l < nu; ++l) {
             const int64_t hi = M.uptr[l + 1];
-            for (int64_t q = M.uptr[l] + me; q < hi; q += nth) {
+            if (R.i >= 0) out[R.i] = ilu_row_sum(R, ldcg_val(out + R.i), out) / R.v;
+            for (int64_t q = M.uptr[l] + me + nth; q < hi; q += nth) {
                 const int i = M.urows[q];
-                const int64_t kd = rp[i] + dp[i], k1 = rp[i + 1];
-                T s = ldcg_val(out + i);
-                for (int64_t k = kd + 1; k < k1; ++k) s = efma(-lu[k], ldcg_val(out + ci[k]), s);
-                out[i] = s / lu[kd];
+                const int64_t kd = M.rp[i] + M.dpos[i], k1 = M.rp[i + 1];
+                T t = ldcg_val(out + i);
+                for (int64_t k = kd + 1; k < k1; ++k) t = efma(-M.lu[k], ldcg_val(out + M.ci[k]), t);
+                out[i] = t / M.lu[kd];
             }
-            if (!gs.sync()) return false;
+            gs.arrive();
+            if (l + 1 < nu) ilu_fetch_u(hi + me, M.uptr[l + 2], R);
+            if (!gs.wait()) return false;
         }
         if (threadIdx.x == 0)   // factors and row data once, v read, out written and re-read
             acct->bytes += (double)M.nnz * (sizeof(T) + 4) + (double)sys.N * (8 + 4 + 8 + 3 * sizeof(T));

@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <vector>
 
-#include "../../include/mlbicgstab.h"
+#include "mlbicgstab.h"
 #include "mlb_engine.cuh"
 #include "mlb_refine.cuh"
 
