@@ -58,6 +58,11 @@ WORKLOADS = {
     # about 4x slower than M = I, in the oracle as well)
     "cd3d128_n4_fp64_jacobi": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=0,
                                    precond=1),
+    # ILU(0) right preconditioning (Algorithm 7.1 with M = L U, the
+    # preconditioner of the paper's experiments, §5) on the headline system
+    # and on the batch (one CTA per system, CTA barriers between levels)
+    "cd3d128_n4_fp64_ilu0": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=0, precond=2),
+    "batch512_n4_fp64_ilu0": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0, precond=2),
     "reservoir_n8_fp64": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0),
     "batch512_n4_fp64": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0),
     # the autotuner on a mid-size system (default configuration vs tuned)
@@ -84,8 +89,9 @@ DEFAULT = "cd3d128_n4_fp64"
 # iteration count.  Set to None whenever the kernel changes until it is
 # captured again.
 NCU_DRAM_BYTES_PER_ITER = (136.79e9 + 34.50e9) / 300
-VARIANTS = ["spmv_qdot_cd3d128", "batch512_n4_fp64", "batch512_n4_refined", "helmholtz_n8_c128",
-            "helmholtz_n8_c128_kappa07", "sequence8_cd3d64", "tune_cd2d256", "cd3d128_n4_refined"]
+VARIANTS = ["spmv_qdot_cd3d128", "cd3d128_n4_fp64_ilu0", "batch512_n4_fp64", "batch512_n4_fp64_ilu0",
+            "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07", "sequence8_cd3d64",
+            "tune_cd2d256", "cd3d128_n4_refined"]
 
 
 def _load_peaks():
@@ -151,6 +157,8 @@ def _variant_desc(name, wl, systems):
         extra += f", omega guard kappa={wl['kappa']:g} (Eq. 5.1)"
     if wl.get("precond", 0) == 1:
         extra += ", Jacobi M=diag(A) (Algorithm 7.1)"
+    if wl.get("precond", 0) == 2:
+        extra += ", ILU(0) M=LU (Algorithm 7.1; level-scheduled triangular solves)"
     return f"{what} (N={N:,}, nnz={nnz:,}), n={wl['n']}, {_prec_name(wl)}{extra}, tol {wl['tol']:g}"
 
 
@@ -330,7 +338,7 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
     steps = max(1, args.variant_steps)
     out = {"workload": name, "config": _variant_desc(name, vwl, systems),
            "precision": _prec_name(vwl), "n": vwl["n"], "unit": UNIT,
-           "kappa": vwl.get("kappa", 0.0), "precond": ["none", "jacobi"][vwl.get("precond", 0)]}
+           "kappa": vwl.get("kappa", 0.0), "precond": ["none", "jacobi", "ilu0"][vwl.get("precond", 0)]}
     if vwl["kind"] == "batch":
         def once():
             for x in xs:
@@ -531,9 +539,14 @@ def run_ours(args, wl):
             base = by_name["helmholtz_n8_c128"]
             v["vs_kappa0"] = {"speedup": v["value"] / base["value"],
                               "iters": v["iters_per_solve"], "iters_kappa0": base["iters_per_solve"]}
-        if v["workload"] == "cd3d128_n4_fp64_jacobi":
+        if v["workload"] in ("cd3d128_n4_fp64_jacobi", "cd3d128_n4_fp64_ilu0"):
             v["vs_unpreconditioned"] = {"speedup": v["value"] / head_value,
                                         "iters": v["iters_per_solve"]}
+        if v["workload"] == "batch512_n4_fp64_ilu0" and "batch512_n4_fp64" in by_name:
+            base = by_name["batch512_n4_fp64"]
+            v["vs_batch_unpreconditioned"] = {"speedup": v["value"] / base["value"],
+                                              "iters_total": v["iters_total"],
+                                              "iters_total_unpreconditioned": base["iters_total"]}
 
     # end to end through the C ABI with pinned host buffers
     b_h = torch.tensor(b, dtype=torch.float64).pin_memory()
