@@ -889,6 +889,8 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
                       : (cplx ? batch_blocks_per_sm<cdouble>() : batch_blocks_per_sm<double>());
     if (bps < 1) return MLB_ERR_CUDA;
     const int grid = std::min(count, sms * bps);
+    bool any_ilu = false;
+    for (int q = 0; q < count; ++q) any_ilu = any_ilu || hs[q]->precond == MLB_PRECOND_ILU0;
     const int *dorder = (const int *)(dws + off_order);
     unsigned *queue = (unsigned *)dws;
     const void *ditems = dws + off_items;
@@ -902,9 +904,9 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
             e = launch_batch_refine<float, double>((const BatchItemR<float, double> *)ditems, dorder, count, queue,
                                                    grid, st);
     } else if (cplx) {
-        e = launch_batch<cdouble>((const BatchItem<cdouble> *)ditems, dorder, count, queue, grid, st);
+        e = launch_batch<cdouble>((const BatchItem<cdouble> *)ditems, dorder, count, queue, grid, any_ilu, st);
     } else {
-        e = launch_batch<double>((const BatchItem<double> *)ditems, dorder, count, queue, grid, st);
+        e = launch_batch<double>((const BatchItem<double> *)ditems, dorder, count, queue, grid, any_ilu, st);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -536,7 +536,10 @@ struct GridSync {
     }
 };
 
-template <typename T>
+// PC: built with the ILU(0) preconditioner passes (ilu_pre and the
+// product passes' switch to M^{-1} of their input); without it none of
+// that code is reachable.
+template <typename T, bool PC = false>
 struct Engine {
     using S = typename coef_of<T>::type;                      // FP64 coefficient
     using ACC = typename real_of<T>::type;                    // thread accumulator
@@ -660,15 +663,10 @@ struct Engine {
     // reports it.
     template <int K, int NE, typename Fin>
     __device__ __forceinline__ void spmv_rows(const T *xin, const T *const (&epi)[NE], Fin fin, ACC (&acc)[K]) {
-        if constexpr (!is_narrow<T>::value) {
-            // with ILU(0) the product is A (M^{-1} xin)
-            if (sys.ilu.lu) {
-                if (!ilu_solve(xin, sys.ilu.t)) {
-                    gs.ring->failed = 1;
-                    return;
-                }
-                xin = sys.ilu.t;
-            }
+        // with ILU(0) the product is A t, t = M^{-1} xin formed by the
+        // caller (ilu_pre) before the pass
+        if constexpr (PC) {
+            if (sys.ilu.lu) xin = sys.ilu.t;
         }
         unsigned sq = gs.seq();   // issued (producer lane) or consumed (consumers) tiles
         const bool okw = sell_spmv<NE>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
@@ -797,6 +795,18 @@ struct Engine {
         if (threadIdx.x == 0)   // factors and row data once, v read, out written and re-read
             acct->bytes += (double)M.nnz * (sizeof(T) + 4) + (double)sys.N * (8 + 4 + 8 + 3 * sizeof(T));
         return true;
+    }
+
+    // Before a product pass with ILU(0): t = M^{-1} in, where `in` is the
+    // pass's input vector (the pass then multiplies t).  A separate call,
+    // so the product passes themselves carry no call to the solve.
+    __device__ __forceinline__ bool ilu_pre(const T *in) {
+        if constexpr (!PC || is_narrow<T>::value) {
+            return true;
+        } else {
+            if (!sys.ilu.lu) return true;
+            return ilu_solve(in, sys.ilu.t);
+        }
     }
 
     // y_0 = M x_0 = L (U x_0), in place on x: t = U x, then x = L t (two
@@ -1273,7 +1283,7 @@ struct Engine {
             }
         }
         if (!started) {
-            if (!ph_residual(bb, rr, e, true)) return o;
+            if (!ilu_pre(sys.x) || !ph_residual(bb, rr, e, true)) return o;
             op(OP_NORM, 2);
             op(OP_MATVEC, 1);
         }
@@ -1288,7 +1298,7 @@ struct Engine {
 
         // w_0 = A g_0, c_0 = q_1^H w_0; e_0 = q_1^H r_0 came with r_0
         S cv;
-        if (!ph_spmv_c(0, 0, cv)) return o;
+        if (!ilu_pre(Gc(0)) || !ph_spmv_c(0, 0, cv)) return o;
         op(OP_MATVEC);
         op(OP_DOT);
         if (threadIdx.x == 0) c[0] = cv;
@@ -1365,7 +1375,7 @@ struct Engine {
                     }
                 }
                 // steps 31-32: w = A g, c = q_{i+1}^H w
-                if (!ph_spmv_c(i, i, cv)) return o;
+                if (!ilu_pre(Gc(i)) || !ph_spmv_c(i, i, cv)) return o;
                 op(OP_MATVEC);
                 op(OP_DOT);
                 if (threadIdx.x == 0) c[i] = cv;
@@ -1394,7 +1404,7 @@ struct Engine {
                 // step 38: omega = (A u)^H u / ||A u||^2, Eq. 5.1 guard
                 double zz;
                 S zu;
-                if (!ph_spmv_z(zz, zu)) return o;
+                if (!ilu_pre(sys.r) || !ph_spmv_z(zz, zu)) return o;
                 op(OP_MATVEC);
                 op(OP_DOT);
                 if (zz == 0.0 || !isfinite(zz)) { o.flag = -1; return o; }
@@ -1452,7 +1462,7 @@ struct Engine {
                 }
                 op(OP_SAXPY);   // omega-correction
                 // step 51: w = A g, c = q_1^H w
-                if (!ph_spmv_c(0, 0, cv)) return o;
+                if (!ilu_pre(Gc(0)) || !ph_spmv_c(0, 0, cv)) return o;
                 op(OP_MATVEC);
                 op(OP_DOT);
                 if (threadIdx.x == 0) c[0] = cv;

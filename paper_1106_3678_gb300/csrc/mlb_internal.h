@@ -48,9 +48,11 @@ struct BatchItemR {
     SolveCtl ctl;
     RefCtl rc;
 };
+// ilu: some item has an ILU(0) preconditioner (the kernel with those passes
+// then runs every item, each by its own view).
 template <typename T>
 cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
-                         cudaStream_t st);
+                         bool ilu, cudaStream_t st);
 template <typename T32, typename T64>
 cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
                                 int grid, cudaStream_t st);

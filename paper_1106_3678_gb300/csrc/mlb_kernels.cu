@@ -3,163 +3,31 @@
 
 #include "mlb_internal.h"
 #include "mlb_refine.cuh"
+#include "mlb_solve.cuh"
 
 namespace mlb {
 
-// ===========================================================================
-// persistent solve kernel
-// ===========================================================================
-// One solve by the team described by `gs`: repeated calls of the method
-// from the current x while the recursive residual met tol but the true
-// residual did not (restart rule of this library), all iterations counted
-// against one maxit; then the true residual; the team's rank-0 CTA writes
-// the result record.
+// Solve and batch launches: the kernels with the ILU(0) passes only for
+// handles that have that preconditioner.
 template <typename T>
-__device__ void run_fp64_solve(Engine<T> &E, GridSync &gs, const SolveCtl &ctl, Acct &acct, DevResult *res) {
-    using S = typename coef_of<T>::type;
-    int64_t total = 0;
-    int outer = 0;
-    typename Engine<T>::Out o{1, 0, 0, 0, 0.0};
-    // ILU(0): the method iterates on y = M x (y_0 = M x_0; x = M^{-1} y at
-    // the end, from the final residual pass, which forms M^{-1} y)
-    const bool ilu = E.sys.ilu.lu != nullptr;
-    if (ilu) E.ilu_to_y();
-    for (;;) {
-        if (!gs.ok) break;
-        o = E.inner(ctl.maxit - total, outer == 0, ctl.tol);
-        if (!gs.ok) break;
-        total += o.iter;
-        if (o.flag != 0 || o.iter == 0 || total >= ctl.maxit || outer >= ctl.max_outer) break;
-        outer++;
-    }
-    int64_t ops_last[5];
-    for (int q = 0; q < 5; ++q) ops_last[q] = acct.ops[q];
-    double true_rel = __longlong_as_double(0x7ff8000000000000LL);
-    if (gs.ok) {
-        double bb, rr;
-        S qr;
-        if (E.ph_residual(bb, rr, qr, false)) {
-            double bn = sqrt(bb);
-            if (bn == 0.0) bn = 1.0;
-            true_rel = sqrt(rr) / bn;
-            if (ilu) E.ilu_to_x();
-        }
-    }
-    if (gs.bid == 0 && threadIdx.x == 0) {
-        res->flag = o.flag;
-        res->j = o.j;
-        res->i = o.i;
-        res->status = gs.ok ? 0 : (gs.bar ? ld_relaxed_i32(&gs.bar->status) : kStatusTimeout);
-        if (!gs.ok && res->status == 0) res->status = kStatusTimeout;
-        res->iter = total;
-        res->spmv = acct.spmv;
-        res->outer = outer;
-        res->err = o.err;
-        res->true_relres = true_rel;
-        res->bytes = acct.bytes;
-        for (int q = 0; q < 5; ++q) res->ops[q] = ops_last[q];
-    }
+cudaError_t launch_solve(const SysView<T> &sys, const SolveCtl &ctl, int grid, cudaStream_t st) {
+    return sys.ilu.lu ? launch_solve_pc<T, true>(sys, ctl, grid, st) : launch_solve_pc<T, false>(sys, ctl, grid, st);
 }
-
-// Raw shared storage for an object constructed in place by thread 0
-// (per-CTA state shared by all threads of the CTA).
-template <typename X>
-struct alignas(16) SharedSlot {
-    unsigned char raw[sizeof(X)];
-    __device__ X *get() { return reinterpret_cast<X *>(raw); }
-};
-
-// Allow the ring's dynamic shared memory for a kernel (idempotent).
-static cudaError_t allow_ring(const void *fn) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-}
-
-__device__ __forceinline__ void acct_reset(Acct &acct) {
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 5; ++q) acct.ops[q] = 0;
-        acct.spmv = 0;
-        acct.bytes = 0.0;
-    }
-    __syncthreads();
-}
-
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, SolveCtl ctl) {
-    using S = typename coef_of<T>::type;
-    extern __shared__ unsigned char dsm[];
-    __shared__ double red[kRedDoubles];
-    __shared__ S cbuf[kMaxN];
-    __shared__ S btbuf[kMaxN];
-    __shared__ int sflag;
-    __shared__ Acct acct;
-    __shared__ TileRing ring;
-    __shared__ SysView<T> s_sys;
-    __shared__ SolveCtl s_ctl;
-    __shared__ SharedSlot<GridSync> gs_slot;
-    __shared__ SharedSlot<Engine<T>> e_slot;
-    __shared__ unsigned seqs[kThreads];
-    ring_init(&ring, ring_buffer(dsm));
-    seqs[threadIdx.x] = 0;
-    if (threadIdx.x == 0) {
-        s_sys = sys;
-        s_ctl = ctl;
-        new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring, seqs);
-        new (e_slot.get()) Engine<T>(s_sys, s_ctl, *gs_slot.get(), cbuf, btbuf, &acct);
-    }
-    acct_reset(acct);   // includes the __syncthreads that publishes the objects
-    GridSync &gs = *gs_slot.get();
-    Engine<T> &E = *e_slot.get();
-    E.attach();
-    run_fp64_solve(E, gs, s_ctl, acct, s_ctl.res);
-    __syncthreads();
-    ring_drain(&ring, seqs[kConsumers], seqs[0], s_ctl.timeout_ns);
+int solve_blocks_per_sm() {
+    const int a = solve_blocks_per_sm_pc<T, false>(), b = solve_blocks_per_sm_pc<T, true>();
+    return a < b ? a : b;
 }
-
-// ===========================================================================
-// batch: many independent systems in one persistent launch
-// ===========================================================================
-// Each CTA takes the next system from a device queue (systems ordered
-// largest first by the host) and solves it alone: the same method with
-// CTA-wide barriers and reductions in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1)
-    batch_kernel(const BatchItem<T> *items, const int *order, int count, unsigned *queue) {
-    using S = typename coef_of<T>::type;
-    extern __shared__ unsigned char dsm[];
-    __shared__ TileRing ring;
-    __shared__ double red[kRedDoubles];
-    __shared__ S cbuf[kMaxN];
-    __shared__ S btbuf[kMaxN];
-    __shared__ int sflag;
-    __shared__ Acct acct;
-    __shared__ int s_next;
-    __shared__ BatchItem<T> item;
-    __shared__ SharedSlot<GridSync> gs_slot;
-    __shared__ SharedSlot<Engine<T>> e_slot;
-    __shared__ unsigned seqs[kThreads];   // tile counters, kept across systems
-    ring_init(&ring, ring_buffer(dsm));
-    seqs[threadIdx.x] = 0;
-    uint64_t timeout = 2000000000ull;
-    for (;;) {
-        if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        const int q = s_next;
-        if (q >= count) break;
-        if (threadIdx.x == 0) item = items[order[q]];
-        acct_reset(acct);   // includes the __syncthreads that publishes `item`
-        timeout = item.ctl.timeout_ns;
-        if (threadIdx.x == 0) {
-            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
-            new (e_slot.get()) Engine<T>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
-        }
-        __syncthreads();
-        GridSync &gs = *gs_slot.get();
-        Engine<T> &E = *e_slot.get();
-        E.attach();
-        run_fp64_solve(E, gs, item.ctl, acct, item.ctl.res);
-        __syncthreads();
-    }
-    ring_drain(&ring, seqs[kConsumers], seqs[0], timeout);
+cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
+                         bool ilu, cudaStream_t st) {
+    return ilu ? launch_batch_pc<T, true>(items, order, count, queue, grid, st)
+               : launch_batch_pc<T, false>(items, order, count, queue, grid, st);
+}
+template <typename T>
+int batch_blocks_per_sm() {
+    const int a = batch_blocks_per_sm_pc<T, false>(), b = batch_blocks_per_sm_pc<T, true>();
+    return a < b ? a : b;
 }
 
 template <typename T32, typename T64>
@@ -221,15 +89,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     ring_drain(&ring, seqs[kConsumers], seqs[0], timeout);
 }
 
-template <typename T>
-cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
-                         cudaStream_t st) {
-    cudaError_t e = allow_ring((const void *)batch_kernel<T>);
-    if (e != cudaSuccess) return e;
-    batch_kernel<T><<<grid, kThreads, kRingBytes, st>>>(items, order, count, queue);
-    return cudaGetLastError();
-}
-
 template <typename T32, typename T64>
 cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
                                 int grid, cudaStream_t st) {
@@ -239,42 +98,12 @@ cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *or
     return cudaGetLastError();
 }
 
-template <typename T>
-int batch_blocks_per_sm() {
-    int nb = 0;
-    if (allow_ring((const void *)batch_kernel<T>) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T>, kThreads, kRingBytes) != cudaSuccess)
-        return 0;
-    return nb;
-}
 template <typename T32, typename T64>
 int batch_refine_blocks_per_sm() {
     int nb = 0;
     if (allow_ring((const void *)batch_refine_kernel<T32, T64>) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_refine_kernel<T32, T64>, kThreads, kRingBytes) !=
             cudaSuccess)
-        return 0;
-    return nb;
-}
-
-template <typename T>
-cudaError_t launch_solve(const SysView<T> &sys, const SolveCtl &ctl, int grid, cudaStream_t st) {
-    SysView<T> s = sys;
-    SolveCtl c = ctl;
-    void *args[] = {(void *)&s, (void *)&c};
-    cudaError_t e = allow_ring((const void *)solve_kernel<T>);
-    if (e != cudaSuccess) return e;
-    if (grid <= 1)
-        return cudaLaunchKernel((const void *)solve_kernel<T>, dim3(1), dim3(kThreads), args, kRingBytes, st);
-    return cudaLaunchCooperativeKernel((const void *)solve_kernel<T>, dim3(grid), dim3(kThreads), args,
-                                       kRingBytes, st);
-}
-
-template <typename T>
-int solve_blocks_per_sm() {
-    int nb = 0;
-    if (allow_ring((const void *)solve_kernel<T>) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<T>, kThreads, kRingBytes) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -692,9 +521,9 @@ template cudaError_t launch_refine<cfloat, cdouble>(const SysView<cfloat> &, con
                                                     const SolveCtl &, const RefCtl &, int, cudaStream_t);
 template int refine_blocks_per_sm<float, double>();
 template int refine_blocks_per_sm<cfloat, cdouble>();
-template cudaError_t launch_batch<double>(const BatchItem<double> *, const int *, int, unsigned *, int,
+template cudaError_t launch_batch<double>(const BatchItem<double> *, const int *, int, unsigned *, int, bool,
                                           cudaStream_t);
-template cudaError_t launch_batch<cdouble>(const BatchItem<cdouble> *, const int *, int, unsigned *, int,
+template cudaError_t launch_batch<cdouble>(const BatchItem<cdouble> *, const int *, int, unsigned *, int, bool,
                                            cudaStream_t);
 template cudaError_t launch_batch_refine<float, double>(const BatchItemR<float, double> *, const int *, int,
                                                         unsigned *, int, cudaStream_t);

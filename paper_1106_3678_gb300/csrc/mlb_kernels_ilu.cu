@@ -1,0 +1,19 @@
+// Solve and batch kernels with the ILU(0) preconditioner passes (see
+// mlb_solve.cuh), in a translation unit of their own so that they compile
+// in parallel with the rest of the library.
+#include "mlb_solve.cuh"
+
+namespace mlb {
+
+template cudaError_t launch_solve_pc<double, true>(const SysView<double> &, const SolveCtl &, int, cudaStream_t);
+template cudaError_t launch_solve_pc<cdouble, true>(const SysView<cdouble> &, const SolveCtl &, int, cudaStream_t);
+template cudaError_t launch_batch_pc<double, true>(const BatchItem<double> *, const int *, int, unsigned *, int,
+                                                   cudaStream_t);
+template cudaError_t launch_batch_pc<cdouble, true>(const BatchItem<cdouble> *, const int *, int, unsigned *, int,
+                                                    cudaStream_t);
+template int solve_blocks_per_sm_pc<double, true>();
+template int solve_blocks_per_sm_pc<cdouble, true>();
+template int batch_blocks_per_sm_pc<double, true>();
+template int batch_blocks_per_sm_pc<cdouble, true>();
+
+}  // namespace mlb
