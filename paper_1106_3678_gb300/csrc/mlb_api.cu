@@ -31,6 +31,8 @@ struct mlb_handle {
     void *ilu_lu = nullptr, *ilu_t = nullptr;
     int ilu_nlev_l = 0, ilu_nlev_u = 0;
     int64_t ilu_nnz = 0;
+    int32_t *ilu_lcnt = nullptr, *ilu_ucnt = nullptr, *ilu_lell_c = nullptr, *ilu_uell_c = nullptr;
+    void *ilu_lell_a = nullptr, *ilu_uell_a = nullptr, *ilu_udiag = nullptr;
     int precision = MLB_PREC_FP64;
     int64_t N = 0, ld = 0, nnz = 0, nnz_pad = 0, nslices = 0;
     int64_t maxw = 0;   // widest SELL-32 slice (entries per row)
@@ -241,6 +243,13 @@ SysView<T> make_view(const mlb_handle *h) {
         v.ilu.nlev_u = h->ilu_nlev_u;
         v.ilu.nnz = h->ilu_nnz;
         v.ilu.t = (T *)h->ilu_t;
+        v.ilu.lcnt = h->ilu_lcnt;
+        v.ilu.ucnt = h->ilu_ucnt;
+        v.ilu.lell_c = h->ilu_lell_c;
+        v.ilu.uell_c = h->ilu_uell_c;
+        v.ilu.lell_a = (const T *)h->ilu_lell_a;
+        v.ilu.uell_a = (const T *)h->ilu_uell_a;
+        v.ilu.udiag = (const T *)h->ilu_udiag;
     }
     return v;
 }
@@ -311,6 +320,8 @@ int map_solution(mlb_handle *h, bool to_x, cudaStream_t st) {
     return MLB_OK;
 }
 int map_solution(mlb_handle *h, bool to_x) { return map_solution(h, to_x, h->stream); }
+
+static_assert(Engine<double, true>::kIluReg == kIluEll, "ILU(0) entries held by position = entries in registers");
 
 // Jacobi preconditioner M = diag(A) (Algorithm 7.1, right preconditioning):
 // d = diagonal of A (a row's diagonal entries summed), values of A M^{-1}
@@ -454,6 +465,21 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         MLB_CUDA(cudaMemcpy(h->ilu_urows, ih.urows.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
         MLB_CUDA(cudaMemcpy(h->ilu_uptr, ih.uptr.data(), ih.uptr.size() * 4, cudaMemcpyHostToDevice));
         MLB_CUDA(cudaMemsetAsync(h->ilu_t, 0, vb, st));
+        const size_t ne = (size_t)kIluEll * N;
+        if ((rc = dev_alloc_t(h, &h->ilu_lcnt, (size_t)N * 4))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_ucnt, (size_t)N * 4))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_lell_c, ne * 4))) return rc;
+        if ((rc = dev_alloc_t(h, &h->ilu_uell_c, ne * 4))) return rc;
+        if ((rc = dev_alloc(h, &h->ilu_lell_a, ne * es))) return rc;
+        if ((rc = dev_alloc(h, &h->ilu_uell_a, ne * es))) return rc;
+        if ((rc = dev_alloc(h, &h->ilu_udiag, (size_t)N * es))) return rc;
+        MLB_CUDA(cudaMemcpy(h->ilu_lcnt, ih.lcnt.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_ucnt, ih.ucnt.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_lell_c, ih.lell_c.data(), ne * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_uell_c, ih.uell_c.data(), ne * 4, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_lell_a, ih.lell_a.data(), ne * es, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_uell_a, ih.uell_a.data(), ne * es, cudaMemcpyHostToDevice));
+        MLB_CUDA(cudaMemcpy(h->ilu_udiag, ih.udiag.data(), (size_t)N * es, cudaMemcpyHostToDevice));
     }
 
     // shadow vectors

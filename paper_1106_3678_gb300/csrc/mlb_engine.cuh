@@ -92,6 +92,10 @@ struct IluView {
     int nlev_l, nlev_u;
     int64_t nnz;
     T *t;                       // ld: M^{-1} of the current product's input
+    // the same rows in level-position order: entry count and the first
+    // kIluEll entries of position q at e * N + q, U's diagonal at q
+    const int32_t *lcnt, *ucnt, *lell_c, *uell_c;
+    const T *lell_a, *uell_a, *udiag;
 };
 
 // Device view of one linear system.  Vectors have leading dimension `ld`
@@ -687,7 +691,7 @@ struct Engine {
     // kIluReg entries (column, factor value) in registers, where the rest
     // of its entries start and end, and the row's right-hand-side entry
     // (forward) or its U diagonal (backward).  i < 0: no row.
-    static constexpr int kIluReg = 4;
+    static constexpr int kIluReg = 4;   // == kIluEll (entries stored by position)
     struct IluRow {
         int i, cnt;
         int64_t rest, end;
@@ -696,23 +700,29 @@ struct Engine {
         T v;
     };
     // Row q of L's level order (forward: entries before the diagonal).
+    // Its count and first entries are read by position, independently of
+    // the row index; entries beyond kIluReg come from the pattern.
     __device__ __forceinline__ void ilu_fetch_l(int64_t q, int64_t hi, const T *v, IluRow &R) const {
         R.i = -1;
         if (q >= hi) return;
         const IluView<T> &M = sys.ilu;
+        const int64_t N = sys.N;
         const int i = M.lrows[q];
-        const int64_t k0 = M.rp[i], kd = k0 + M.dpos[i];
-        const int cnt = (int)min(kd - k0, (int64_t)kIluReg);
+        const int n = M.lcnt[q];
+        const int cnt = n < kIluReg ? n : kIluReg;
 #pragma unroll
         for (int e = 0; e < kIluReg; ++e)
             if (e < cnt) {
-                R.c[e] = M.ci[k0 + e];
-                R.a[e] = M.lu[k0 + e];
+                R.c[e] = M.lell_c[e * N + q];
+                R.a[e] = M.lell_a[e * N + q];
             }
         R.i = i;
         R.cnt = cnt;
-        R.rest = k0 + cnt;
-        R.end = kd;
+        R.rest = R.end = 0;
+        if (n > kIluReg) {
+            R.rest = M.rp[i] + kIluReg;
+            R.end = M.rp[i] + n;
+        }
         R.v = v[i];
     }
     // Row q of U's level order (backward: entries after the diagonal).
@@ -720,20 +730,25 @@ struct Engine {
         R.i = -1;
         if (q >= hi) return;
         const IluView<T> &M = sys.ilu;
+        const int64_t N = sys.N;
         const int i = M.urows[q];
-        const int64_t kd = M.rp[i] + M.dpos[i], k1 = M.rp[i + 1];
-        const int cnt = (int)min(k1 - kd - 1, (int64_t)kIluReg);
+        const int n = M.ucnt[q];
+        const int cnt = n < kIluReg ? n : kIluReg;
 #pragma unroll
         for (int e = 0; e < kIluReg; ++e)
             if (e < cnt) {
-                R.c[e] = M.ci[kd + 1 + e];
-                R.a[e] = M.lu[kd + 1 + e];
+                R.c[e] = M.uell_c[e * N + q];
+                R.a[e] = M.uell_a[e * N + q];
             }
         R.i = i;
         R.cnt = cnt;
-        R.rest = kd + 1 + cnt;
-        R.end = k1;
-        R.v = M.lu[kd];
+        R.rest = R.end = 0;
+        if (n > kIluReg) {
+            const int64_t d = M.rp[i] + M.dpos[i];
+            R.rest = d + 1 + kIluReg;
+            R.end = d + 1 + n;
+        }
+        R.v = M.udiag[q];
     }
     // s - sum of a_e out[c_e] over the row's entries, in pattern order.
     __device__ __forceinline__ T ilu_row_sum(const IluRow &R, T s, const T *out) const {
@@ -755,18 +770,24 @@ struct Engine {
     // pending, and only the values of earlier levels are read after it.
     __device__ __noinline__ bool ilu_solve(const T *v, T *out) {
         const IluView<T> &M = sys.ilu;
-        const int64_t nth = (int64_t)gs.nblocks * kThreads;
-        // a level's rows go round-robin over the CTAs (a level is a few
-        // thousand scattered rows: in CTA-sized blocks a few SMs would
-        // carry every level, each with thousands of scattered loads)
-        const int64_t me = (int64_t)threadIdx.x * gs.nblocks + gs.bid;
+        // a level's positions split into one contiguous chunk per CTA of
+        // ceil(size / CTAs): every CTA shares each level (a level is a few
+        // thousand scattered rows), and a warp reads consecutive positions
+        const int64_t G = gs.nblocks, bid = gs.bid;
+        const int tid = threadIdx.x;
+        auto chunk = [&](const int32_t *ptr, int l, int64_t &q0, int64_t &q1) {
+            const int64_t lo = ptr[l], hi = ptr[l + 1], ch = (hi - lo + G - 1) / G;
+            q0 = lo + bid * ch;
+            q1 = q0 + ch < hi ? q0 + ch : hi;
+        };
         const int nl = M.nlev_l, nu = M.nlev_u;
+        int64_t q0, q1;
         IluRow R;
-        ilu_fetch_l(me, M.lptr[1], v, R);
+        chunk(M.lptr, 0, q0, q1);
+        ilu_fetch_l(q0 + tid, q1, v, R);
         for (int l = 0; l < nl; ++l) {
-            const int64_t hi = M.lptr[l + 1];
             if (R.i >= 0) out[R.i] = ilu_row_sum(R, R.v, out);
-            for (int64_t q = M.lptr[l] + me + nth; q < hi; q += nth) {   // more rows than threads
+            for (int64_t q = q0 + tid + kThreads; q < q1; q += kThreads) {   // more rows than threads
                 const int i = M.lrows[q];
                 const int64_t k0 = M.rp[i], kd = k0 + M.dpos[i];
                 T t = v[i];
@@ -774,14 +795,18 @@ struct Engine {
                 out[i] = t;
             }
             gs.arrive();
-            if (l + 1 < nl) ilu_fetch_l(hi + me, M.lptr[l + 2], v, R);
-            else ilu_fetch_u(me, M.uptr[1], R);
+            if (l + 1 < nl) {
+                chunk(M.lptr, l + 1, q0, q1);
+                ilu_fetch_l(q0 + tid, q1, v, R);
+            } else {
+                chunk(M.uptr, 0, q0, q1);
+                ilu_fetch_u(q0 + tid, q1, R);
+            }
             if (!gs.wait()) return false;
         }
         for (int l = 0; l < nu; ++l) {
-            const int64_t hi = M.uptr[l + 1];
             if (R.i >= 0) out[R.i] = ilu_row_sum(R, ldcg_val(out + R.i), out) / R.v;
-            for (int64_t q = M.uptr[l] + me + nth; q < hi; q += nth) {
+            for (int64_t q = q0 + tid + kThreads; q < q1; q += kThreads) {
                 const int i = M.urows[q];
                 const int64_t kd = M.rp[i] + M.dpos[i], k1 = M.rp[i + 1];
                 T t = ldcg_val(out + i);
@@ -789,7 +814,10 @@ struct Engine {
                 out[i] = t / M.lu[kd];
             }
             gs.arrive();
-            if (l + 1 < nu) ilu_fetch_u(hi + me, M.uptr[l + 2], R);
+            if (l + 1 < nu) {
+                chunk(M.uptr, l + 1, q0, q1);
+                ilu_fetch_u(q0 + tid, q1, R);
+            }
             if (!gs.wait()) return false;
         }
         if (threadIdx.x == 0)   // factors and row data once, v read, out written and re-read

@@ -110,6 +110,34 @@ int build_t(const mlb_matrix *A, IluHost &f) {
     }
     group_levels(lev, nu, f.urows, f.uptr);
     f.nlev_u = nu;
+    // level-position copies (kIluEll entries per row, zero padded)
+    const V *lu = (const V *)f.lu.data();
+    f.lcnt.assign(N, 0);
+    f.ucnt.assign(N, 0);
+    f.lell_c.assign((size_t)kIluEll * N, 0);
+    f.uell_c.assign((size_t)kIluEll * N, 0);
+    std::vector<V> la((size_t)kIluEll * N, V(0)), ua((size_t)kIluEll * N, V(0)), ud(N, V(0));
+    for (int64_t q = 0; q < N; ++q) {
+        const int64_t i = f.lrows[q], k0 = f.rp[i], d = k0 + f.dpos[i];
+        f.lcnt[q] = (int32_t)(d - k0);
+        for (int64_t e = 0; e < kIluEll && k0 + e < d; ++e) {
+            f.lell_c[e * N + q] = f.ci[k0 + e];
+            la[e * N + q] = lu[k0 + e];
+        }
+        const int64_t j = f.urows[q], dj = f.rp[j] + f.dpos[j], k1 = f.rp[j + 1];
+        f.ucnt[q] = (int32_t)(k1 - dj - 1);
+        for (int64_t e = 0; e < kIluEll && dj + 1 + e < k1; ++e) {
+            f.uell_c[e * N + q] = f.ci[dj + 1 + e];
+            ua[e * N + q] = lu[dj + 1 + e];
+        }
+        ud[q] = lu[dj];
+    }
+    auto bytes = [](const std::vector<V> &x, std::vector<char> &out) {
+        out.assign((const char *)x.data(), (const char *)(x.data() + x.size()));
+    };
+    bytes(la, f.lell_a);
+    bytes(ua, f.uell_a);
+    bytes(ud, f.udiag);
     return MLB_OK;
 }
 

@@ -97,12 +97,21 @@ cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T
 // entries before row i's diagonal are L's (unit diagonal implied), the rest
 // U's; dpos[i] = position of the diagonal relative to rp[i]; rows grouped
 // into the level sets of the forward (L) and backward (U) solves.
+// For the solves, each triangle also in level-position order: position q
+// (row lrows[q] or urows[q]) has its entry count (lcnt/ucnt) and its first
+// kIluEll entries at e * N + q (columns lell_c/uell_c, values
+// lell_a/uell_a); udiag[q] is U's diagonal of row urows[q].  A row's
+// loads are then independent of each other (only the row's right-hand
+// side needs the row index).
+constexpr int kIluEll = 4;
 struct IluHost {
     std::vector<int64_t> rp;
     std::vector<int32_t> ci, dpos, lrows, lptr, urows, uptr;
     std::vector<char> lu;   // nnz values of the handle's dtype
     int64_t nnz = 0;
     int nlev_l = 0, nlev_u = 0;
+    std::vector<int32_t> lcnt, ucnt, lell_c, uell_c;
+    std::vector<char> lell_a, uell_a, udiag;
 };
 // MLB_OK, or MLB_ERR_ARG when a row has no stored diagonal or a pivot is
 // zero or not finite.
