@@ -65,6 +65,9 @@ WORKLOADS = {
     "cd3d128_n4_fp64_ilu0": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=0, precond=2),
     "batch512_n4_fp64_ilu0": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0, precond=2),
     "reservoir_n8_fp64": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0),
+    # the same 3x3-block reservoir system with ILU(0): a handful of
+    # iterations where M = I needs tens of thousands
+    "reservoir_n8_fp64_ilu0": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0, precond=2),
     "batch512_n4_fp64": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0),
     # the autotuner on a mid-size system (default configuration vs tuned)
     "tune_cd2d256": dict(kind="tune", m=256, n=4, tol=1e-10, maxit=40000, precision=0),
@@ -90,7 +93,8 @@ DEFAULT = "cd3d128_n4_fp64"
 # iteration count.  Set to None whenever the kernel changes until it is
 # captured again.
 NCU_DRAM_BYTES_PER_ITER = (136.79e9 + 34.50e9) / 300
-VARIANTS = ["spmv_qdot_cd3d128", "cd3d128_n4_fp64_ilu0", "batch512_n4_fp64", "batch512_n4_fp64_ilu0",
+VARIANTS = ["spmv_qdot_cd3d128", "cd3d128_n4_fp64_ilu0", "reservoir_n8_fp64", "reservoir_n8_fp64_ilu0",
+            "batch512_n4_fp64", "batch512_n4_fp64_ilu0",
             "batch512_n4_refined", "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07", "sequence8_cd3d64",
             "tune_cd2d256", "cd3d128_n4_refined"]
 
@@ -543,6 +547,11 @@ def run_ours(args, wl):
         if v["workload"] in ("cd3d128_n4_fp64_jacobi", "cd3d128_n4_fp64_ilu0"):
             v["vs_unpreconditioned"] = {"speedup": v["value"] / head_value,
                                         "iters": v["iters_per_solve"]}
+        if v["workload"] == "reservoir_n8_fp64_ilu0" and "reservoir_n8_fp64" in by_name:
+            base = by_name["reservoir_n8_fp64"]
+            v["vs_unpreconditioned"] = {"speedup": v["value"] / base["value"], "iters": v["iters_per_solve"],
+                                        "iters_unpreconditioned": base["iters_per_solve"],
+                                        "flags_unpreconditioned": base["flags"]}
         if v["workload"] == "batch512_n4_fp64_ilu0" and "batch512_n4_fp64" in by_name:
             base = by_name["batch512_n4_fp64"]
             v["vs_batch_unpreconditioned"] = {"speedup": v["value"] / base["value"],

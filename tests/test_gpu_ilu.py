@@ -191,3 +191,26 @@ def test_ilu_edge_cases():
     r, _ = M.mlbicgstab_solve(h0, b, x, 1e-10, 100)
     assert r.iter == 0 and r.flag == 0
     np.testing.assert_allclose(x, 1.0, rtol=1e-13)
+
+
+def test_ilu_block_reservoir_matches_oracle():
+    """3x3-block reservoir system (21 entries per row: most rows have more
+    entries per triangle than the solve keeps in registers).  ILU(0) solves
+    it in a handful of iterations where M = I needs thousands."""
+    A = W.bsr3_to_csr(W.reservoir_bsr3(8, 8, 4))
+    b = W.row_sums(A)
+    N = A.n_rows
+    f = O.ilu0(A)
+    Q = O.q_gauss(0, N, 8)
+    h = M.mlbicgstab_create(A, n=8, q_seed=0, precond=ILU)
+    x = np.zeros(N)
+    K = 6
+    res, eh = M.mlbicgstab_solve(h, b, x, 0.0, K, hist_cap=K + 1)
+    ref = O.mlbicgstabt(A, b, np.zeros(N), Q, K, 0.0, err_hist=True, ilu=f)
+    _hist_close(eh[:K + 1], ref.err_hist[:K + 1], N)
+    x = np.zeros(N)
+    res, _ = M.mlbicgstab_solve(h, b, x, 1e-10, 2000)
+    ref = O.solve(A, b, np.zeros(N), Q, 2000, 1e-10, ilu=f)
+    assert res.flag == 0 and ref.flag == 0 and res.true_relres < 1e-10
+    assert abs(res.iter - ref.iter) <= 2 and res.iter < 50
+    np.testing.assert_allclose(x, 1.0, rtol=1e-8)
