@@ -214,3 +214,36 @@ def test_ilu_block_reservoir_matches_oracle():
     assert res.flag == 0 and ref.flag == 0 and res.true_relres < 1e-10
     assert abs(res.iter - ref.iter) <= 2 and res.iter < 50
     np.testing.assert_allclose(x, 1.0, rtol=1e-8)
+
+
+def test_ilu_with_kappa_set_n_and_autotuned_grid():
+    """ILU(0) combined with the Eq. 5.1 guard, a handle built for n = 8 and
+    set to n = 4, and a launch configuration chosen by the autotuner (the
+    levels are then split over a different number of CTAs)."""
+    A = W.cd3d_lognormal(16)
+    b = W.uniform_rhs(A.n_rows, seed=7)
+    N = A.n_rows
+    f = O.ilu0(A)
+    h = M.mlbicgstab_create(A, n=8, q_seed=0, precond=ILU, kappa=0.7)
+    M.mlbicgstab_set_n(h, 4)
+    Q4 = O.q_gauss(0, N, 8)[:, :4]
+    ref = O.solve(A, b, np.zeros(N), Q4, 2000, 1e-10, kappa=0.7, ilu=f)
+    assert ref.flag == 0
+    x = np.zeros(N)
+    res, _ = M.mlbicgstab_solve(h, b, x, 1e-10, 2000)
+    assert res.flag == 0 and res.true_relres < 1e-10
+    assert abs(res.iter - ref.iter) <= max(2, ref.iter // 10)
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    grid0 = M.mlbicgstab_info(h)["grid"]
+    tune = M.mlbicgstab_autotune(h, iters=5, use_cache=False)
+    assert tune["grid"] == M.mlbicgstab_info(h)["grid"]
+    x2 = np.zeros(N)
+    res2, _ = M.mlbicgstab_solve(h, b, x2, 1e-10, 2000)
+    assert res2.flag == 0 and res2.true_relres < 1e-10
+    assert np.linalg.norm(x2 - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    # one CTA (the level loop with CTA barriers only) gives the same answer
+    h1 = M.mlbicgstab_create(A, n=4, q_seed=0, precond=ILU, kappa=0.7, grid=1)
+    x1 = np.zeros(N)
+    r1, _ = M.mlbicgstab_solve(h1, b, x1, 1e-10, 2000)
+    assert r1.flag == 0 and np.linalg.norm(x1 - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    assert grid0 >= 1
