@@ -247,3 +247,36 @@ def test_ilu_with_kappa_set_n_and_autotuned_grid():
     r1, _ = M.mlbicgstab_solve(h1, b, x1, 1e-10, 2000)
     assert r1.flag == 0 and np.linalg.norm(x1 - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
     assert grid0 >= 1
+
+
+def test_ilu_full_size_cd3d_first_iterations_elementwise():
+    """The 128^3 ILU(0) workload at full size in the bench's launch
+    geometry: 6 iterations against the oracle's, x element by element."""
+    A = W.cd3d_lognormal(128)
+    b = W.uniform_rhs(A.n_rows, seed=2)
+    N = A.n_rows
+    h = M.mlbicgstab_create(A, n=4, q_seed=0, precond=ILU)
+    K = 6
+    x = np.zeros(N)
+    res, eh = M.mlbicgstab_solve(h, b, x, 0.0, K, hist_cap=K + 1)
+    ref = O.mlbicgstabt(A, b, np.zeros(N), O.q_gauss(0, N, 4), K, 0.0, err_hist=True, ilu=O.ilu0(A))
+    assert (res.iter, res.j, res.i) == (ref.iter, ref.j, ref.i)
+    _hist_close(eh[:K + 1], ref.err_hist[:K + 1], N)
+    assert np.max(np.abs(x - ref.x)) <= 1e-8 * np.max(np.abs(ref.x))
+
+
+def test_ilu_full_size_reservoir_solve():
+    """The 3x3-block reservoir workload at full size (393,216 rows), solved
+    to 1e-10 with ILU(0): the oracle's iteration count and solution, and
+    the true residual recomputed on the host."""
+    A = W.bsr3_to_csr(W.reservoir_bsr3())
+    b = W.row_sums(A)
+    N = A.n_rows
+    h = M.mlbicgstab_create(A, n=8, q_seed=0, precond=ILU)
+    x = np.zeros(N)
+    res, _ = M.mlbicgstab_solve(h, b, x, 1e-10, 200)
+    ref = O.solve(A, b, np.zeros(N), O.q_gauss(0, N, 8), 200, 1e-10, ilu=O.ilu0(A))
+    assert res.flag == 0 and ref.flag == 0
+    assert abs(res.iter - ref.iter) <= 1
+    assert O.true_relres(A, b, x) < 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
