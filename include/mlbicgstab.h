@@ -104,8 +104,10 @@ typedef struct {
                              NULL = the legacy default stream */
     int64_t timeout_ns;   /* limit of every device-side wait (grid barrier
                              spin); default 2e9 (2 s) */
-    int32_t precond;      /* MLB_PRECOND_NONE (default) or MLB_PRECOND_JACOBI:
-                             Algorithm 7.1 with M = diag(A).  The handle
+    int32_t precond;      /* MLB_PRECOND_NONE (default), MLB_PRECOND_JACOBI
+                             or MLB_PRECOND_ILU0.
+                             MLB_PRECOND_JACOBI: Algorithm 7.1 with
+                             M = diag(A).  The handle
                              stores A M^{-1} (columns divided by the
                              diagonal), F = M^{-H} A^H Q (step 2), and each
                              solve maps x_0 to y_0 = M x_0 and the result
@@ -125,7 +127,8 @@ typedef struct {
                              the kernel.  FP64 precision only
                              (MLB_ERR_UNSUPPORTED otherwise); MLB_ERR_ARG
                              when a row has no stored diagonal or a pivot
-                             is zero. */
+                             is zero.  Handles with different
+                             preconditioners may share one batch. */
     int32_t reserved0;    /* must be 0 */
 } mlb_options;
 
