@@ -280,3 +280,22 @@ def test_ilu_full_size_reservoir_solve():
     assert abs(res.iter - ref.iter) <= 1
     assert O.true_relres(A, b, x) < 1e-10
     assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_batch_mixing_preconditioners():
+    """One batch with handles of every preconditioner: the kernel with the
+    ILU(0) passes runs every item by its own view, and each result equals
+    the same system solved alone on one CTA, bit for bit."""
+    systems = [A for A, _ in W.batch_cd(6, seed=71, n_min=300, n_max=2000)]
+    pcs = [M.MLB_PRECOND_NONE, M.MLB_PRECOND_JACOBI, ILU] * 2
+    hs = [M.mlbicgstab_create(A, n=4, q_seed=0, precond=pc) for A, pc in zip(systems, pcs)]
+    bs = [W.uniform_rhs(A.n_rows, seed=72) for A in systems]
+    xs = [np.zeros(A.n_rows) for A in systems]
+    res = M.mlbicgstab_solve_batch(hs, bs, xs, [1e-10] * 6, [4000] * 6)
+    for A, pc, b, r, x in zip(systems, pcs, bs, res, xs):
+        assert r.flag == 0 and r.true_relres < 1e-10
+        h1 = M.mlbicgstab_create(A, n=4, q_seed=0, precond=pc, grid=1)
+        x1 = np.zeros(A.n_rows)
+        r1, _ = M.mlbicgstab_solve(h1, b, x1, 1e-10, 4000)
+        assert (r.iter, r.flag) == (r1.iter, r1.flag), pc
+        np.testing.assert_array_equal(x, x1)
