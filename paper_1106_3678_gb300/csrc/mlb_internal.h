@@ -85,8 +85,12 @@ constexpr int kQdMaxN = 64;
 // at allocation); d (device) receives the n inner products (2n doubles for
 // complex) and then d[n * DS] = 1.0 if any CTA timed out, else 0.0.
 // ev (optional) is recorded on st directly before the kernel launch.
-// Fused columns: at most 2 for complex values (4 spill registers).
-inline int qd_fused_columns(int n, bool cplx) { return n >= 4 && !cplx ? 4 : (n >= 2 ? 2 : 1); }
+// Fused columns: 4 only when that is all of them (real n = 4): four
+// epilogue vectors leave room for 12 slices per tile, so 3 of the 15
+// consumer warps idle in the product, which costs more than a later pass
+// over y for the remaining columns (measured at n = 8: 107 us fusing 4,
+// 95 us fusing 2); complex values take at most 2 (4 spill registers).
+inline int qd_fused_columns(int n, bool cplx) { return n == 4 && !cplx ? 4 : (n >= 2 ? 2 : 1); }
 template <typename T>
 cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
                                    int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
