@@ -1,0 +1,27 @@
+"""Host-side pieces of bench.py that run before any GPU work: the workload
+table, the variant list and the description of every workload (a missing
+key there would only show up in a GPU run)."""
+from __future__ import annotations
+
+import bench
+from paper_1106_3678_gb300 import workloads as W
+
+
+def test_variants_and_default_are_known_workloads():
+    assert bench.DEFAULT in bench.WORKLOADS
+    assert set(bench.VARIANTS) <= set(bench.WORKLOADS)
+    assert len(set(bench.VARIANTS)) == len(bench.VARIANTS)
+    assert bench.DEFAULT not in bench.VARIANTS
+
+
+def test_every_workload_has_a_description():
+    A = W.cd2d(4)
+    for name, wl in bench.WORKLOADS.items():
+        d = bench._variant_desc(name, wl, [(A, None, None)])
+        assert isinstance(d, str) and d, name
+
+
+def test_headline_conversion_count_is_set():
+    # the reference arm converts its per-iteration time with this count
+    assert bench.WORKLOADS[bench.DEFAULT]["iters"] > 0
+    assert bench.NCU_DRAM_BYTES_PER_ITER is None or bench.NCU_DRAM_BYTES_PER_ITER > 0
