@@ -213,7 +213,9 @@ int mlbicgstab_create(mlb_handle **h, const mlb_matrix *A,
  * convergence and breakdown tests are taken on the device.
  *   b, x       N values each (dtype of A).  x holds x_0 on entry and the
  *              solution on return.  on_device = 0: host pointers (copied
- *              in and out inside the call); 1: device pointers.
+ *              in and out inside the call); 1: device pointers, in memory
+ *              of the handle's GPU or managed memory (MLB_ERR_ARG for
+ *              another GPU's memory).
  *   err_hist   optional host array (NULL to skip): err_hist[k] = relative
  *              recursive residual after iteration k (k = 0: initial), for
  *              k < hist_cap, over the first inner call.
@@ -297,7 +299,8 @@ int mlbicgstab_autotune(mlb_handle *h, int32_t iters, int32_t use_cache,
  * Fused hot operation: y = A x and d = Q^H y (all n shadow inner products,
  * a tall-skinny block reduction) in one pass over A — the per-iteration
  * product w = A g with c = q^H w of Algorithm 4.1 (step 32) generalised to
- * every q.  x, y: device arrays of N values; d: host array of n_active
+ * every q.  x, y: device arrays of N values (memory of the handle's GPU
+ * or managed memory; MLB_ERR_ARG otherwise); d: host array of n_active
  * values (the handle's n unless mlbicgstab_set_n chose fewer columns).
  * Reductions are deterministic (fixed order).  Blocks until d is ready.
  * MLB_ERR_TIMEOUT if a wait inside the kernel gave up (y and d invalid).
@@ -333,7 +336,9 @@ int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d);
  * streams, or from different host threads) race and give wrong results.
  * The first call on a device looks up the array's device address (set-up);
  * make that first call before any stream capture.  Returns MLB_ERR_ARG for
- * invalid sizes or non-device pointers, MLB_ERR_CUDA on launch failure.
+ * invalid sizes, or for a pointer that is neither device memory of the
+ * current device (cudaGetDevice) nor managed memory: memory of another GPU
+ * is refused.  MLB_ERR_CUDA on launch failure.
  */
 int mlbicgstab_spmv_qdot_noalloc(int64_t nrows, int64_t nnz,
                                  const int64_t *row_ptr,

@@ -295,13 +295,16 @@ RefView<T64> make_ref_view(const mlb_handle *h) {
     return v;
 }
 
-bool is_device_ptr(const void *p) {
+// Device memory of GPU `dev` (the handle's), or managed memory.  Memory of
+// another GPU is refused: the kernels run on `dev`.
+bool is_device_ptr(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 // With a preconditioner the kernels iterate on y = M x (A M^{-1} y = b):
@@ -737,7 +740,7 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     if (!(tol >= 0.0) || maxit < 0 || hist_cap < 0 || (on_device != 0 && on_device != 1)) return MLB_ERR_ARG;
     memset(res, 0, sizeof(*res));
     MLB_CUDA(cudaSetDevice(h->device));
-    if (on_device && (!is_device_ptr(b) || !is_device_ptr(x))) return MLB_ERR_ARG;
+    if (on_device && (!is_device_ptr(b, h->device) || !is_device_ptr(x, h->device))) return MLB_ERR_ARG;
     cudaStream_t st = h->stream;
     const size_t nb = (size_t)h->N * h->esize;
     const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1112,7 +1115,7 @@ int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
     if (!h || !x || !y || !d) return MLB_ERR_ARG;
     if (h->precond != MLB_PRECOND_NONE) return MLB_ERR_UNSUPPORTED;
     MLB_CUDA(cudaSetDevice(h->device));
-    if (!is_device_ptr(x) || !is_device_ptr(y)) return MLB_ERR_ARG;
+    if (!is_device_ptr(x, h->device) || !is_device_ptr(y, h->device)) return MLB_ERR_ARG;
     cudaStream_t st = h->stream;
     cudaError_t e;
     // x is gathered from the caller's array (SELL padding columns are

@@ -76,14 +76,21 @@ __global__ void __launch_bounds__(kNaThreads)
         for (int q = 0; q < NB; ++q)
             if (q < n) acc_dot(&acc[q * DS], ldv(Q + (int64_t)q * ldq + row), sum);
     }
-    for (int q = 0; q < n; ++q) {
-        double v[DS];
+    // unrolled over the fixed bound NB so that every index into acc is a
+    // compile-time constant (a run-time index would put acc in local
+    // memory); n is the same in every thread, so the barriers inside
+    // block_sum_all are reached uniformly
 #pragma unroll
-        for (int t = 0; t < DS; ++t) v[t] = (double)acc[q * DS + t];
-        block_sum_all<DS>(v, red);
-        if (threadIdx.x == 0) {
+    for (int q = 0; q < NB; ++q) {
+        if (q < n) {
+            double v[DS];
 #pragma unroll
-            for (int t = 0; t < DS; ++t) part[((size_t)blockIdx.x * NB + q) * DS + t] = v[t];
+            for (int t = 0; t < DS; ++t) v[t] = (double)acc[q * DS + t];
+            block_sum_all<DS>(v, red);
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int t = 0; t < DS; ++t) part[((size_t)blockIdx.x * NB + q) * DS + t] = v[t];
+            }
         }
     }
     if (threadIdx.x == 0) {
@@ -140,17 +147,23 @@ template <typename T>
 int dispatch(int dev, int64_t N, const int64_t *rp, const int32_t *ci, const T *av, const T *x, const T *Q,
              int64_t ldq, int n, T *y, T *d, double *scratch, cudaStream_t st) {
     if (n <= 4) return launch<T, 4>(dev, N, rp, ci, av, x, Q, ldq, n, y, d, scratch, st);
+    if (n <= 8) return launch<T, 8>(dev, N, rp, ci, av, x, Q, ldq, n, y, d, scratch, st);
     if (n <= 16) return launch<T, 16>(dev, N, rp, ci, av, x, Q, ldq, n, y, d, scratch, st);
+    if (n <= 32) return launch<T, 32>(dev, N, rp, ci, av, x, Q, ldq, n, y, d, scratch, st);
     return launch<T, kNaMaxN>(dev, N, rp, ci, av, x, Q, ldq, n, y, d, scratch, st);
 }
 
-bool on_device(const void *p) {
+// Device memory of the current device `dev`, or managed memory.  Memory of
+// another GPU is refused: the kernel runs on `dev`, where such a pointer
+// is either unmapped (without peer access) or read over NVLink.
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -170,8 +183,8 @@ extern "C" int mlbicgstab_spmv_qdot_noalloc(int64_t nrows, int64_t nnz, const in
         cudaGetLastError();
         return MLB_ERR_CUDA;
     }
-    if (!on_device(row_ptr) || !on_device(x) || !on_device(Q) || !on_device(y) || !on_device(d) ||
-        (nnz > 0 && (!on_device(col_idx) || !on_device(values))))
+    if (!on_device(row_ptr, dev) || !on_device(x, dev) || !on_device(Q, dev) || !on_device(y, dev) ||
+        !on_device(d, dev) || (nnz > 0 && (!on_device(col_idx, dev) || !on_device(values, dev))))
         return MLB_ERR_ARG;
     double *scratch = nullptr;
     int rc = scratch_address(dev, &scratch);
