@@ -55,14 +55,23 @@ extern "C" {
 /* Preconditioner M of Algorithm 7.1 (right preconditioning). */
 #define MLB_PRECOND_NONE 0   /* M = I: Algorithm 4.1 */
 #define MLB_PRECOND_JACOBI 1 /* M = diag(A) (every diagonal entry nonzero) */
-#define MLB_PRECOND_ILU0 2   /* M = L U, the ILU(0) factors of A (FP64 only) */
+#define MLB_PRECOND_ILU0 2   /* M = L U, the ILU(0) factors of A */
 
 #define MLB_PREC_FP64 0     /* matrix, vectors and arithmetic in FP64 */
 #define MLB_PREC_FP32_REFINED 1 /* inner ML(n)BiCGStab in FP32 (values,
-                                   vectors, accumulation) inside an FP64
-                                   iterative refinement: residual b - A x,
-                                   solution update and all recurrence
-                                   coefficients in FP64 */
+                                   vectors, preconditioner factors,
+                                   accumulation) inside an FP64 iterative
+                                   refinement: residual b - A x, solution
+                                   update and all recurrence coefficients
+                                   in FP64.  The inner solve keeps its
+                                   Krylov recurrences across refinement
+                                   steps: reliable updates move its iterate
+                                   into the FP64 solution and replace its
+                                   residual by the FP64 true residual (see
+                                   inner_tol).  It converges where FP32 can
+                                   carry the (preconditioned) iteration;
+                                   otherwise flag 1 with the solution of
+                                   smallest true residual found. */
 
 /* A sparse matrix in host memory (CSR).  The library copies it; the
  * caller's arrays may be freed after mlbicgstab_create returns. */
@@ -91,13 +100,26 @@ typedef struct {
                              standard minimisation step */
     int32_t max_outer;    /* FP64: restarts from the current x while the
                              recursive residual met tol but the true one did
-                             not.  Refined: maximum refinement steps (each
-                             one FP32 inner solve).  Default 10. */
+                             not.  Refined: maximum number of FP32 inner
+                             calls; a new call (a restart of the inner
+                             Krylov process from the current x) follows one
+                             that stagnated or reached inner_maxit.
+                             Default 10. */
     int32_t grid;         /* CTAs of the persistent solve kernel; 0 = auto
                              (all SMs x occupancy, fewer for small N) */
-    double inner_tol;     /* refined mode: relative tolerance of each FP32
-                             inner solve (default 1e-5) */
-    int64_t inner_maxit;  /* refined mode: iteration cap of one inner solve
+    double inner_tol;     /* refined mode, in (0, 1): reliable-update
+                             factor.  At a block end, when the FP32
+                             recursive residual has fallen below inner_tol
+                             times its largest value since the last update
+                             (or has met tol), the FP32 iterate is moved
+                             into the FP64 solution and the FP32 residual
+                             replaced by the FP64 true residual; the solve
+                             ends when that true residual meets tol.
+                             Default 1e-2.  An inner call also ends when its
+                             residual has not reached a new minimum for
+                             max(2000, iterations it took to reach the
+                             current one) iterations. */
+    int64_t inner_maxit;  /* refined mode: iteration cap of one inner call
                              (default 1e6; all inner iterations together
                              are capped by the maxit of the solve) */
     void *stream;         /* cudaStream_t for all work of this handle;
@@ -124,10 +146,10 @@ typedef struct {
                              A (M^{-1} v), M^{-1} by level-scheduled
                              triangular solves on the device; F = M^{-H}
                              A^H Q; the solve iterates on y = M x, mapped in
-                             the kernel.  FP64 precision only
-                             (MLB_ERR_UNSUPPORTED otherwise); MLB_ERR_ARG
-                             when a row has no stored diagonal or a pivot
-                             is zero.  Handles with different
+                             the kernel.  In refined mode the inner
+                             FP32 solve applies FP32 copies of the
+                             factors.  MLB_ERR_ARG when a row has no stored
+                             diagonal or a pivot is zero.  Handles with different
                              preconditioners may share one batch. */
     int32_t reserved0;    /* must be 0 */
 } mlb_options;

@@ -33,6 +33,10 @@ struct mlb_handle {
     int64_t ilu_nnz = 0;
     int32_t *ilu_lcnt = nullptr, *ilu_ucnt = nullptr, *ilu_lell_c = nullptr, *ilu_uell_c = nullptr;
     void *ilu_lell_a = nullptr, *ilu_uell_a = nullptr, *ilu_udiag = nullptr;
+    // refined mode with ILU(0): FP32 copies of the factor values and an
+    // FP32 work vector for M^{-1}
+    void *ilu_lu32 = nullptr, *ilu_t32 = nullptr, *ilu_lell_a32 = nullptr, *ilu_uell_a32 = nullptr,
+         *ilu_udiag32 = nullptr;
     int precision = MLB_PREC_FP64;
     int64_t N = 0, ld = 0, nnz = 0, nnz_pad = 0, nslices = 0;
     int64_t maxw = 0;   // widest SELL-32 slice (entries per row)
@@ -45,8 +49,8 @@ struct mlb_handle {
     uint64_t timeout_ns = 2000000000ull;
     double kappa = 0.0;
     int max_outer = 10;
-    double inner_tol = 1e-5;
-    int64_t inner_maxit = 10000;
+    double inner_tol = 1e-2;
+    int64_t inner_maxit = 1000000;
     size_t esize = 8;  // bytes per value
     // device buffers
     int64_t *slice_ptr = nullptr;
@@ -59,6 +63,7 @@ struct mlb_handle {
     // right-hand side)
     void *sval32 = nullptr, *Q32 = nullptr, *F32 = nullptr, *G32 = nullptr, *W32 = nullptr;
     void *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *b32 = nullptr;
+    void *xbest = nullptr;   // refined mode: best FP64 solution so far
     double *partials = nullptr;
     BarrierState *bar = nullptr;
     DevResult *dres = nullptr;
@@ -275,6 +280,27 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.b = (T32 *)h->b32;
     v.n = h->n_active;
     v.ilu = IluView<T32>{};
+    if (h->precond == MLB_PRECOND_ILU0) {
+        v.ilu.rp = h->ilu_rp;
+        v.ilu.ci = h->ilu_ci;
+        v.ilu.lu = (const T32 *)h->ilu_lu32;
+        v.ilu.dpos = h->ilu_dpos;
+        v.ilu.lrows = h->ilu_lrows;
+        v.ilu.lptr = h->ilu_lptr;
+        v.ilu.urows = h->ilu_urows;
+        v.ilu.uptr = h->ilu_uptr;
+        v.ilu.nlev_l = h->ilu_nlev_l;
+        v.ilu.nlev_u = h->ilu_nlev_u;
+        v.ilu.nnz = h->ilu_nnz;
+        v.ilu.t = (T32 *)h->ilu_t32;
+        v.ilu.lcnt = h->ilu_lcnt;
+        v.ilu.ucnt = h->ilu_ucnt;
+        v.ilu.lell_c = h->ilu_lell_c;
+        v.ilu.uell_c = h->ilu_uell_c;
+        v.ilu.lell_a = (const T32 *)h->ilu_lell_a32;
+        v.ilu.uell_a = (const T32 *)h->ilu_uell_a32;
+        v.ilu.udiag = (const T32 *)h->ilu_udiag32;
+    }
     return v;
 }
 
@@ -292,7 +318,20 @@ RefView<T64> make_ref_view(const mlb_handle *h) {
     v.x = (T64 *)h->x;
     v.b = (const T64 *)h->b;
     v.r = (T64 *)h->r;
+    v.xbest = (T64 *)h->xbest;
     return v;
+}
+
+// Controls of the refined mode's inner calls: reliable-update factor,
+// iteration cap, stagnation window (iterations without a new smallest
+// residual at a block end).
+constexpr int64_t kStallWindow = 2000;
+RefCtl ref_ctl(const mlb_handle *h) {
+    RefCtl rc;
+    rc.delta = h->inner_tol;
+    rc.inner_maxit = h->inner_maxit;
+    rc.window = kStallWindow;
+    return rc;
 }
 
 // Device memory of GPU `dev` (the handle's), or managed memory.  Memory of
@@ -565,6 +604,8 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         if ((rc = dev_alloc(h, &h->r32, vb32))) return rc;
         if ((rc = dev_alloc(h, &h->z32, vb32))) return rc;
         if ((rc = dev_alloc(h, &h->b32, vb32))) return rc;
+        if ((rc = dev_alloc(h, &h->xbest, vb))) return rc;
+        MLB_CUDA(cudaMemsetAsync(h->xbest, 0, vb, st));
         MLB_CUDA(cudaMemsetAsync(h->G32, 0, vb32 * n, st));
         MLB_CUDA(cudaMemsetAsync(h->W32, 0, vb32 * n, st));
         MLB_CUDA(cudaMemsetAsync(h->x32, 0, vb32, st));
@@ -576,6 +617,21 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         if (n > 1)
             MLB_CUDA(launch_narrow((const double *)h->F, (float *)h->F32, ld * (int64_t)(n - 1) * (int64_t)es / 8,
                                    st));
+        if (h->precond == MLB_PRECOND_ILU0) {
+            const int64_t N = h->N;
+            const size_t ne = (size_t)kIluEll * N;
+            if ((rc = dev_alloc(h, &h->ilu_lu32, (size_t)h->ilu_nnz * es / 2))) return rc;
+            if ((rc = dev_alloc(h, &h->ilu_t32, vb32))) return rc;
+            if ((rc = dev_alloc(h, &h->ilu_lell_a32, ne * es / 2))) return rc;
+            if ((rc = dev_alloc(h, &h->ilu_uell_a32, ne * es / 2))) return rc;
+            if ((rc = dev_alloc(h, &h->ilu_udiag32, (size_t)N * es / 2))) return rc;
+            MLB_CUDA(cudaMemsetAsync(h->ilu_t32, 0, vb32, st));
+            const int64_t dpe = (int64_t)es / 8;   // doubles per value
+            MLB_CUDA(launch_narrow((const double *)h->ilu_lu, (float *)h->ilu_lu32, h->ilu_nnz * dpe, st));
+            MLB_CUDA(launch_narrow((const double *)h->ilu_lell_a, (float *)h->ilu_lell_a32, (int64_t)ne * dpe, st));
+            MLB_CUDA(launch_narrow((const double *)h->ilu_uell_a, (float *)h->ilu_uell_a32, (int64_t)ne * dpe, st));
+            MLB_CUDA(launch_narrow((const double *)h->ilu_udiag, (float *)h->ilu_udiag32, N * dpe, st));
+        }
     }
 
     // launch geometry and scratch
@@ -644,7 +700,7 @@ void mlbicgstab_default_options(mlb_options *o) {
     o->kappa = 0.0;
     o->max_outer = 10;
     o->grid = 0;
-    o->inner_tol = 1e-5;
+    o->inner_tol = 1e-2;
     o->inner_maxit = 1000000;
     o->stream = nullptr;
     o->timeout_ns = 2000000000LL;
@@ -671,10 +727,11 @@ int mlbicgstab_create(mlb_handle **out, const mlb_matrix *A, const mlb_matrix *A
     if (o.n < 1 || o.n > kMaxN) return MLB_ERR_ARG;
     if (o.precision != MLB_PREC_FP64 && o.precision != MLB_PREC_FP32_REFINED) return MLB_ERR_ARG;
     if (o.kappa < 0.0 || o.max_outer < 0 || o.timeout_ns <= 0) return MLB_ERR_ARG;
+    if (o.precision == MLB_PREC_FP32_REFINED && (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.inner_maxit < 1))
+        return MLB_ERR_ARG;
     if ((o.precond != MLB_PRECOND_NONE && o.precond != MLB_PRECOND_JACOBI && o.precond != MLB_PRECOND_ILU0) ||
         o.reserved0 != 0)
         return MLB_ERR_ARG;
-    if (o.precond == MLB_PRECOND_ILU0 && o.precision != MLB_PREC_FP64) return MLB_ERR_UNSUPPORTED;
     int rc = validate_csr(A);
     if (rc) return rc;
     if (AH) {
@@ -773,9 +830,7 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     MLB_CUDA(cudaEventRecord(h->ev0, st));
     cudaError_t e;
     if (h->precision == MLB_PREC_FP32_REFINED) {
-        RefCtl rc;
-        rc.inner_tol = h->inner_tol;
-        rc.inner_maxit = h->inner_maxit;
+        const RefCtl rc = ref_ctl(h);
         if (h->dtype == MLB_C128)
             e = launch_refine<cfloat, cdouble>(make_view32<cfloat>(h), make_ref_view<cdouble>(h), ctl, rc, h->grid,
                                                st);
@@ -885,9 +940,7 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
         ctl.timeout_ns = h->timeout_ns;
         char *dst = hws + off_items + (size_t)s * item_bytes;
         if (refined) {
-            RefCtl rc;
-            rc.inner_tol = h->inner_tol;
-            rc.inner_maxit = h->inner_maxit;
+            const RefCtl rc = ref_ctl(h);
             if (cplx) {
                 BatchItemR<cfloat, cdouble> it{make_view32<cfloat>(h), make_ref_view<cdouble>(h), ctl, rc};
                 memcpy(dst, &it, sizeof(it));
@@ -928,10 +981,10 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
     if (refined) {
         if (cplx)
             e = launch_batch_refine<cfloat, cdouble>((const BatchItemR<cfloat, cdouble> *)ditems, dorder, count, queue,
-                                                     grid, st);
+                                                     grid, any_ilu, st);
         else
             e = launch_batch_refine<float, double>((const BatchItemR<float, double> *)ditems, dorder, count, queue,
-                                                   grid, st);
+                                                   grid, any_ilu, st);
     } else if (cplx) {
         e = launch_batch<cdouble>((const BatchItem<cdouble> *)ditems, dorder, count, queue, grid, any_ilu, st);
     } else {

@@ -48,6 +48,12 @@ __host__ __device__ __forceinline__ cdouble operator/(cdouble a, cdouble b) {
     return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
 }
 __host__ __device__ __forceinline__ cdouble operator/(cdouble a, double s) { return {a.re / s, a.im / s}; }
+// FP32 complex (the ILU(0) triangular solves of the refined mode)
+__host__ __device__ __forceinline__ cfloat operator-(cfloat a) { return {-a.re, -a.im}; }
+__host__ __device__ __forceinline__ cfloat operator/(cfloat a, cfloat b) {
+    float d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
 __host__ __device__ __forceinline__ bool is_zero(double a) { return a == 0.0; }
 __host__ __device__ __forceinline__ bool is_zero(cdouble a) { return a.re == 0.0 && a.im == 0.0; }
 __host__ __device__ __forceinline__ double abs_of(double a) { return fabs(a); }

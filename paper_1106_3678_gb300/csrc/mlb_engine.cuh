@@ -149,8 +149,13 @@ __device__ __forceinline__ cfloat ldg_val(const cfloat *p) {
 // Loads through L2 only: values another CTA wrote since the last team
 // barrier (an SM's L1 may still hold an older copy of the line).
 __device__ __forceinline__ double ldcg_val(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg_val(const float *p) { return __ldcg(p); }
 __device__ __forceinline__ cdouble ldcg_val(const cdouble *p) {
     double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cfloat ldcg_val(const cfloat *p) {
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
     return {v.x, v.y};
 }
 __device__ __forceinline__ double ldcs_val(const double *p) { return __ldcs(p); }
@@ -540,6 +545,12 @@ struct GridSync {
     }
 };
 
+// A call of Engine::inner without residual replacement (every solve but
+// the refined mode's FP32 inner one).
+struct NoHook {
+    static constexpr bool kActive = false;
+};
+
 // PC: built with the ILU(0) preconditioner passes (ilu_pre and the
 // product passes' switch to M^{-1} of their input); without it none of
 // that code is reachable.
@@ -829,7 +840,7 @@ struct Engine {
     // pass's input vector (the pass then multiplies t).  A separate call,
     // so the product passes themselves carry no call to the solve.
     __device__ __forceinline__ bool ilu_pre(const T *in) {
-        if constexpr (!PC || is_narrow<T>::value) {
+        if constexpr (!PC) {
             return true;
         } else {
             if (!sys.ilu.lu) return true;
@@ -957,6 +968,60 @@ struct Engine {
         rr = v[1];
         qr = mk_coef<T>(v + 2);
         if (threadIdx.x == 0) acct->bytes += (double)sys.N * (sizeof(TW) + 5.0 * sizeof(T));
+        return true;
+    }
+
+    // Refined mode, residual replacement: r = src * scale, with src the
+    // FP64 true residual b - A x of the outer iteration (rows of this CTA);
+    // sums ||r||^2, q_qcol^H r (qcol >= 0) and, when f0, f_1^H r: the
+    // inner products the step that follows the replaced update needs.
+    // Direct loads.
+    __device__ __noinline__ bool ph_replace_narrow(const typename wide_of<T>::type *src, double scale, int qcol,
+                                                   bool f0, double &rr, S &qr, S &fr) {
+        using TW = typename wide_of<T>::type;
+        constexpr int K = 1 + 2 * DS;
+        static_assert(PW * sizeof(TW) == 32, "a chunk of the FP32 vector is two 16-byte source loads");
+        const T *qv = qcol >= 0 ? Qc(qcol) : nullptr;
+        const T *fv = f0 ? Fc(0) : nullptr;
+        ACC acc[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = ACC(0);
+        T *const rq = sys.r;
+        const int64_t clo = c_lo, chi = c_hi;
+        if ((threadIdx.x >> 5) < kConsumerWarps) {
+            for (int64_t ch = clo + threadIdx.x; ch < chi; ch += kConsumers) {
+                const uint4 *sp = reinterpret_cast<const uint4 *>(src) + 2 * ch;
+                uint4 w2[2] = {sp[0], sp[1]};
+                TW tw[PW];
+                memcpy(tw, w2, sizeof(tw));
+                Pack<T> p;
+#pragma unroll
+                for (int e = 0; e < PW; ++e) p.e[e] = narrow_scaled(tw[e], scale);
+                stp(rq, ch, p);
+#pragma unroll
+                for (int e = 0; e < PW; ++e) acc_nrm(&acc[0], p.e[e]);
+                if (qv) {
+                    Pack<T> qq = ldp_ro(qv, ch);
+#pragma unroll
+                    for (int e = 0; e < PW; ++e) acc_dot(&acc[1], qq.e[e], p.e[e]);
+                }
+                if (fv) {
+                    Pack<T> ff = ldp_ro(fv, ch);
+#pragma unroll
+                    for (int e = 0; e < PW; ++e) acc_dot(&acc[1 + DS], ff.e[e], p.e[e]);
+                }
+            }
+        }
+        fence_proxy_async_global();
+        double v[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
+        if (!reduce<K>(v)) return false;
+        rr = v[0];
+        qr = mk_coef<T>(v + 1);
+        fr = mk_coef<T>(v + 1 + DS);
+        if (threadIdx.x == 0)
+            acct->bytes += (double)sys.N * (sizeof(TW) + (1.0 + (qv ? 1 : 0) + (fv ? 1 : 0)) * sizeof(T));
         return true;
     }
 
@@ -1290,9 +1355,20 @@ struct Engine {
     };
 
     // `init` (refined mode only): start from x_0 = 0 with b = init * scale
-    // instead of reading b and x.
+    // instead of reading b and x.  `hook` (refined mode only): residual
+    // replacement by the FP64 outer iteration.  hook->replace(qcol, f0, rr,
+    // qr, fr, conv) moves the FP32 iterate into the FP64 solution, replaces
+    // r by the scaled FP64 true residual and returns ||r||^2 and the inner
+    // products of the replaced r that the next step needs, and whether the
+    // true residual met the outer tolerance.  It is called when the
+    // recursive residual meets `tol` (instead of stopping: the inner call
+    // stops only once the true residual has met the outer tolerance) and,
+    // at block ends, when hook->want(err) (reliable updates); a block end
+    // also ends the call when hook->stalled(iter, err).
+    template <typename Hook = NoHook>
     __device__ Out inner(int64_t maxit, bool rec, double tol,
-                         const typename wide_of<T>::type *init = nullptr, double scale = 1.0) {
+                         const typename wide_of<T>::type *init = nullptr, double scale = 1.0,
+                         Hook *hook = nullptr) {
         const int n = sys.n;
         Out o{1, 0, 0, 0, 0.0};
         unsigned bsl = 0;   // rotating broadcast slot of once_s / once_d
@@ -1323,6 +1399,7 @@ struct Engine {
         o.err = err;
         record(rec, 0, err);
         if (err < tol) { o.flag = 0; return o; }
+        if constexpr (Hook::kActive) hook->reset(err);
 
         // w_0 = A g_0, c_0 = q_1^H w_0; e_0 = q_1^H r_0 came with r_0
         S cv;
@@ -1348,11 +1425,21 @@ struct Engine {
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
                 err = once_d(bsl, [&] { return sqrt(r2) / bnrm2; });
-                o.err = err;
                 iter++;
                 o.iter = iter;
+                if constexpr (Hook::kActive) {
+                    hook->track(err);
+                    if (err < tol) {
+                        bool conv;
+                        if (!hook->replace(i, j == 0, r2, qr, fr, conv)) return o;
+                        err = once_d(bsl, [&] { return sqrt(r2) / bnrm2; });
+                        hook->reset(err);
+                        if (conv) { o.err = err; o.flag = 0; return o; }
+                    }
+                }
+                o.err = err;
                 record(rec, iter, err);
-                if (err < tol) { o.flag = 0; return o; }
+                if (!Hook::kActive && err < tol) { o.flag = 0; return o; }
                 if (iter >= maxit) return o;
                 e = qr;
                 op(OP_DOT);
@@ -1421,8 +1508,27 @@ struct Engine {
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
                 err = once_d(bsl, [&] { return sqrt(u2) / bnrm2; });
+                if constexpr (Hook::kActive) {
+                    hook->track(err);
+                    if (err < tol) {
+                        // u (kept in r) replaced by the true residual; the
+                        // omega step then works on the replaced u
+                        bool conv;
+                        S dq, df;
+                        if (!hook->replace(-1, false, u2, dq, df, conv)) return o;
+                        err = once_d(bsl, [&] { return sqrt(u2) / bnrm2; });
+                        hook->reset(err);
+                        if (conv) {
+                            iter++;
+                            o.iter = iter;
+                            o.err = err;
+                            o.flag = 0;
+                            return o;
+                        }
+                    }
+                }
                 o.err = err;
-                if (err < tol) {
+                if (!Hook::kActive && err < tol) {
                     iter++;
                     o.iter = iter;
                     record(rec, iter, err);
@@ -1455,11 +1561,23 @@ struct Engine {
                 op(OP_SAXPY, 2);
                 op(OP_NORM);
                 err = once_d(bsl, [&] { return sqrt(r2) / bnrm2; });
-                o.err = err;
                 iter++;
                 o.iter = iter;
+                if constexpr (Hook::kActive) {
+                    hook->track(err);
+                    if (err < tol || hook->want(err)) {
+                        bool conv;
+                        S df;
+                        if (!hook->replace(0, false, r2, q1r, df, conv)) return o;
+                        err = once_d(bsl, [&] { return sqrt(r2) / bnrm2; });
+                        hook->reset(err);
+                        if (conv) { o.err = err; o.flag = 0; return o; }
+                    }
+                    if (hook->stalled(iter, err)) { o.err = err; return o; }
+                }
+                o.err = err;
                 record(rec, iter, err);
-                if (err < tol) { o.flag = 0; return o; }
+                if (!Hook::kActive && err < tol) { o.flag = 0; return o; }
                 if (iter >= maxit) return o;
                 e = q1r;
                 op(OP_DOT);

@@ -55,7 +55,7 @@ cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count,
                          bool ilu, cudaStream_t st);
 template <typename T32, typename T64>
 cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
-                                int grid, cudaStream_t st);
+                                int grid, bool ilu, cudaStream_t st);
 template <typename T>
 int batch_blocks_per_sm();
 template <typename T32, typename T64>

@@ -30,167 +30,30 @@ int batch_blocks_per_sm() {
     return a < b ? a : b;
 }
 
-template <typename T32, typename T64>
-__global__ void __launch_bounds__(kThreads, 1)
-    batch_refine_kernel(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue) {
-    using S = typename coef_of<T32>::type;
-    extern __shared__ unsigned char dsm[];
-    __shared__ TileRing ring;
-    __shared__ double red[kRedDoubles];
-    __shared__ S cbuf[kMaxN];
-    __shared__ S btbuf[kMaxN];
-    __shared__ int sflag;
-    __shared__ Acct acct;
-    __shared__ int s_next;
-    __shared__ BatchItemR<T32, T64> item;
-    __shared__ SharedSlot<GridSync> gs_slot;
-    __shared__ SharedSlot<Engine<T32>> e_slot;
-    __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
-    __shared__ unsigned seqs[kThreads];   // tile counters, kept across systems
-    ring_init(&ring, ring_buffer(dsm));
-    seqs[threadIdx.x] = 0;
-    uint64_t timeout = 2000000000ull;
-    for (;;) {
-        if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        const int q = s_next;
-        if (q >= count) break;
-        if (threadIdx.x == 0) item = items[order[q]];
-        acct_reset(acct);
-        timeout = item.ctl.timeout_ns;
-        if (threadIdx.x == 0) {
-            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
-            new (e_slot.get()) Engine<T32>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
-            new (r_slot.get()) Refiner<T64, T32>(item.rv, *g, &acct, item.sys.x);
-        }
-        __syncthreads();
-        GridSync &gs = *gs_slot.get();
-        Engine<T32> &E = *e_slot.get();
-        Refiner<T64, T32> &R = *r_slot.get();
-        E.attach();
-        RefineOut o = refine_solve<T32, T64>(E, R, item.ctl, item.rc);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            DevResult *res = item.ctl.res;
-            res->flag = o.flag;
-            res->j = 0;
-            res->i = 0;
-            res->status = gs.ok ? 0 : kStatusTimeout;
-            res->iter = o.iter;
-            res->spmv = acct.spmv;
-            res->outer = o.outer;
-            res->err = o.err;
-            res->true_relres = o.err;
-            res->bytes = acct.bytes;
-            for (int k = 0; k < 5; ++k) res->ops[k] = acct.ops[k];
-        }
-        __syncthreads();
-    }
-    ring_drain(&ring, seqs[kConsumers], seqs[0], timeout);
-}
-
-template <typename T32, typename T64>
-cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
-                                int grid, cudaStream_t st) {
-    cudaError_t e = allow_ring((const void *)batch_refine_kernel<T32, T64>);
-    if (e != cudaSuccess) return e;
-    batch_refine_kernel<T32, T64><<<grid, kThreads, kRingBytes, st>>>(items, order, count, queue);
-    return cudaGetLastError();
-}
-
-template <typename T32, typename T64>
-int batch_refine_blocks_per_sm() {
-    int nb = 0;
-    if (allow_ring((const void *)batch_refine_kernel<T32, T64>) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_refine_kernel<T32, T64>, kThreads, kRingBytes) !=
-            cudaSuccess)
-        return 0;
-    return nb;
-}
-
-// ===========================================================================
-// FP32-inner / FP64-refined persistent solve kernel
-// ===========================================================================
-template <typename T32, typename T64>
-__global__ void __launch_bounds__(kThreads, 1)
-    refine_kernel(SysView<T32> sys, RefView<T64> rv, SolveCtl ctl, RefCtl rc) {
-    using S = typename coef_of<T32>::type;
-    extern __shared__ unsigned char dsm[];
-    __shared__ TileRing ring;
-    __shared__ double red[kRedDoubles];
-    __shared__ S cbuf[kMaxN];
-    __shared__ S btbuf[kMaxN];
-    __shared__ int sflag;
-    __shared__ Acct acct;
-    __shared__ SysView<T32> s_sys;
-    __shared__ RefView<T64> s_rv;
-    __shared__ SolveCtl s_ctl;
-    __shared__ RefCtl s_rc;
-    __shared__ SharedSlot<GridSync> gs_slot;
-    __shared__ SharedSlot<Engine<T32>> e_slot;
-    __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
-    __shared__ unsigned seqs[kThreads];
-    ring_init(&ring, ring_buffer(dsm));
-    seqs[threadIdx.x] = 0;
-    if (threadIdx.x == 0) {
-        s_sys = sys;
-        s_rv = rv;
-        s_ctl = ctl;
-        s_rc = rc;
-        GridSync *g = new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring, seqs);
-        new (e_slot.get()) Engine<T32>(s_sys, s_ctl, *g, cbuf, btbuf, &acct);
-        new (r_slot.get()) Refiner<T64, T32>(s_rv, *g, &acct, s_sys.x);
-    }
-    acct_reset(acct);   // includes the __syncthreads that publishes the objects
-    GridSync &gs = *gs_slot.get();
-    Engine<T32> &E = *e_slot.get();
-    Refiner<T64, T32> &R = *r_slot.get();
-    E.attach();
-    RefineOut o = refine_solve<T32, T64>(E, R, s_ctl, s_rc);
-    __syncthreads();
-    ring_drain(&ring, seqs[kConsumers], seqs[0], ctl.timeout_ns);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        DevResult *res = ctl.res;
-        res->flag = o.flag;
-        res->j = 0;
-        res->i = 0;
-        res->status = gs.ok ? 0 : ld_relaxed_i32(&ctl.bar->status);
-        if (!gs.ok && res->status == 0) res->status = kStatusTimeout;
-        res->iter = o.iter;
-        res->spmv = acct.spmv;
-        res->outer = o.outer;
-        res->err = o.err;
-        res->true_relres = o.err;
-        res->bytes = acct.bytes;
-        for (int q = 0; q < 5; ++q) res->ops[q] = acct.ops[q];
-    }
-}
-
+// FP32-inner / FP64-refined launches: the kernels with the ILU(0) passes
+// only when a system has that preconditioner.
 template <typename T32, typename T64>
 cudaError_t launch_refine(const SysView<T32> &sys, const RefView<T64> &rv, const SolveCtl &ctl,
                           const RefCtl &rc, int grid, cudaStream_t st) {
-    SysView<T32> s = sys;
-    RefView<T64> r = rv;
-    SolveCtl c = ctl;
-    RefCtl q = rc;
-    void *args[] = {(void *)&s, (void *)&r, (void *)&c, (void *)&q};
-    cudaError_t e = allow_ring((const void *)refine_kernel<T32, T64>);
-    if (e != cudaSuccess) return e;
-    if (grid <= 1)
-        return cudaLaunchKernel((const void *)refine_kernel<T32, T64>, dim3(1), dim3(kThreads), args, kRingBytes,
-                                st);
-    return cudaLaunchCooperativeKernel((const void *)refine_kernel<T32, T64>, dim3(grid), dim3(kThreads),
-                                       args, kRingBytes, st);
+    return sys.ilu.lu ? launch_refine_pc<T32, T64, true>(sys, rv, ctl, rc, grid, st)
+                      : launch_refine_pc<T32, T64, false>(sys, rv, ctl, rc, grid, st);
 }
-
 template <typename T32, typename T64>
 int refine_blocks_per_sm() {
-    int nb = 0;
-    if (allow_ring((const void *)refine_kernel<T32, T64>) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, refine_kernel<T32, T64>, kThreads, kRingBytes) !=
-            cudaSuccess)
-        return 0;
-    return nb;
+    const int a = refine_blocks_per_sm_pc<T32, T64, false>(), b = refine_blocks_per_sm_pc<T32, T64, true>();
+    return a < b ? a : b;
+}
+template <typename T32, typename T64>
+cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
+                                int grid, bool ilu, cudaStream_t st) {
+    return ilu ? launch_batch_refine_pc<T32, T64, true>(items, order, count, queue, grid, st)
+               : launch_batch_refine_pc<T32, T64, false>(items, order, count, queue, grid, st);
+}
+template <typename T32, typename T64>
+int batch_refine_blocks_per_sm() {
+    const int a = batch_refine_blocks_per_sm_pc<T32, T64, false>(),
+              b = batch_refine_blocks_per_sm_pc<T32, T64, true>();
+    return a < b ? a : b;
 }
 
 // FP64 -> FP32 copies (matrix values, Q, F); interleaved complex data is a
@@ -526,9 +389,9 @@ template cudaError_t launch_batch<double>(const BatchItem<double> *, const int *
 template cudaError_t launch_batch<cdouble>(const BatchItem<cdouble> *, const int *, int, unsigned *, int, bool,
                                            cudaStream_t);
 template cudaError_t launch_batch_refine<float, double>(const BatchItemR<float, double> *, const int *, int,
-                                                        unsigned *, int, cudaStream_t);
+                                                        unsigned *, int, bool, cudaStream_t);
 template cudaError_t launch_batch_refine<cfloat, cdouble>(const BatchItemR<cfloat, cdouble> *, const int *, int,
-                                                          unsigned *, int, cudaStream_t);
+                                                          unsigned *, int, bool, cudaStream_t);
 template int batch_blocks_per_sm<double>();
 template int batch_blocks_per_sm<cdouble>();
 template int batch_refine_blocks_per_sm<float, double>();

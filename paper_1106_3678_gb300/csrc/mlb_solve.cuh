@@ -9,6 +9,7 @@
 #include <new>
 
 #include "mlb_internal.h"
+#include "mlb_refine.cuh"
 
 namespace mlb {
 
@@ -211,7 +212,190 @@ int solve_blocks_per_sm_pc() {
     return nb;
 }
 
+// ===========================================================================
+// FP32-inner / FP64-refined persistent solve and batch kernels
+// ===========================================================================
+template <typename T32, typename T64, bool PC>
+__global__ void __launch_bounds__(kThreads, 1)
+    batch_refine_kernel(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue) {
+    using S = typename coef_of<T32>::type;
+    extern __shared__ unsigned char dsm[];
+    __shared__ TileRing ring;
+    __shared__ double red[kRedDoubles];
+    __shared__ S cbuf[kMaxN];
+    __shared__ S btbuf[kMaxN];
+    __shared__ int sflag;
+    __shared__ Acct acct;
+    __shared__ int s_next;
+    __shared__ BatchItemR<T32, T64> item;
+    __shared__ SharedSlot<GridSync> gs_slot;
+    __shared__ SharedSlot<Engine<T32, PC>> e_slot;
+    __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
+    __shared__ unsigned seqs[kThreads];   // tile counters, kept across systems
+    ring_init(&ring, ring_buffer(dsm));
+    seqs[threadIdx.x] = 0;
+    uint64_t timeout = 2000000000ull;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int q = s_next;
+        if (q >= count) break;
+        if (threadIdx.x == 0) item = items[order[q]];
+        acct_reset(acct);
+        timeout = item.ctl.timeout_ns;
+        if (threadIdx.x == 0) {
+            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
+            new (e_slot.get()) Engine<T32, PC>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
+            new (r_slot.get()) Refiner<T64, T32>(item.rv, *g, &acct);
+        }
+        __syncthreads();
+        GridSync &gs = *gs_slot.get();
+        Engine<T32, PC> &E = *e_slot.get();
+        Refiner<T64, T32> &R = *r_slot.get();
+        E.attach();
+        RefineOut o = refine_solve<T32, T64, PC>(E, R, item.ctl, item.rc);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DevResult *res = item.ctl.res;
+            res->flag = o.flag;
+            res->j = 0;
+            res->i = 0;
+            res->status = gs.ok ? 0 : kStatusTimeout;
+            res->iter = o.iter;
+            res->spmv = acct.spmv;
+            res->outer = o.outer;
+            res->err = o.err;
+            res->true_relres = o.err;
+            res->bytes = acct.bytes;
+            for (int k = 0; k < 5; ++k) res->ops[k] = acct.ops[k];
+        }
+        __syncthreads();
+    }
+    ring_drain(&ring, seqs[kConsumers], seqs[0], timeout);
+}
+
+template <typename T32, typename T64, bool PC>
+cudaError_t launch_batch_refine_pc(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
+                                int grid, cudaStream_t st) {
+    cudaError_t e = allow_ring((const void *)batch_refine_kernel<T32, T64, PC>);
+    if (e != cudaSuccess) return e;
+    batch_refine_kernel<T32, T64, PC><<<grid, kThreads, kRingBytes, st>>>(items, order, count, queue);
+    return cudaGetLastError();
+}
+
+template <typename T32, typename T64, bool PC>
+int batch_refine_blocks_per_sm_pc() {
+    int nb = 0;
+    if (allow_ring((const void *)batch_refine_kernel<T32, T64, PC>) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_refine_kernel<T32, T64, PC>, kThreads, kRingBytes) !=
+            cudaSuccess)
+        return 0;
+    return nb;
+}
+
+// ===========================================================================
+// FP32-inner / FP64-refined persistent solve kernel
+// ===========================================================================
+template <typename T32, typename T64, bool PC>
+__global__ void __launch_bounds__(kThreads, 1)
+    refine_kernel(SysView<T32> sys, RefView<T64> rv, SolveCtl ctl, RefCtl rc) {
+    using S = typename coef_of<T32>::type;
+    extern __shared__ unsigned char dsm[];
+    __shared__ TileRing ring;
+    __shared__ double red[kRedDoubles];
+    __shared__ S cbuf[kMaxN];
+    __shared__ S btbuf[kMaxN];
+    __shared__ int sflag;
+    __shared__ Acct acct;
+    __shared__ SysView<T32> s_sys;
+    __shared__ RefView<T64> s_rv;
+    __shared__ SolveCtl s_ctl;
+    __shared__ RefCtl s_rc;
+    __shared__ SharedSlot<GridSync> gs_slot;
+    __shared__ SharedSlot<Engine<T32, PC>> e_slot;
+    __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
+    __shared__ unsigned seqs[kThreads];
+    ring_init(&ring, ring_buffer(dsm));
+    seqs[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        s_sys = sys;
+        s_rv = rv;
+        s_ctl = ctl;
+        s_rc = rc;
+        GridSync *g = new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring, seqs);
+        new (e_slot.get()) Engine<T32, PC>(s_sys, s_ctl, *g, cbuf, btbuf, &acct);
+        new (r_slot.get()) Refiner<T64, T32>(s_rv, *g, &acct);
+    }
+    acct_reset(acct);   // includes the __syncthreads that publishes the objects
+    GridSync &gs = *gs_slot.get();
+    Engine<T32, PC> &E = *e_slot.get();
+    Refiner<T64, T32> &R = *r_slot.get();
+    E.attach();
+    RefineOut o = refine_solve<T32, T64, PC>(E, R, s_ctl, s_rc);
+    __syncthreads();
+    ring_drain(&ring, seqs[kConsumers], seqs[0], ctl.timeout_ns);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        DevResult *res = ctl.res;
+        res->flag = o.flag;
+        res->j = 0;
+        res->i = 0;
+        res->status = gs.ok ? 0 : ld_relaxed_i32(&ctl.bar->status);
+        if (!gs.ok && res->status == 0) res->status = kStatusTimeout;
+        res->iter = o.iter;
+        res->spmv = acct.spmv;
+        res->outer = o.outer;
+        res->err = o.err;
+        res->true_relres = o.err;
+        res->bytes = acct.bytes;
+        for (int q = 0; q < 5; ++q) res->ops[q] = acct.ops[q];
+    }
+}
+
+template <typename T32, typename T64, bool PC>
+cudaError_t launch_refine_pc(const SysView<T32> &sys, const RefView<T64> &rv, const SolveCtl &ctl,
+                          const RefCtl &rc, int grid, cudaStream_t st) {
+    SysView<T32> s = sys;
+    RefView<T64> r = rv;
+    SolveCtl c = ctl;
+    RefCtl q = rc;
+    void *args[] = {(void *)&s, (void *)&r, (void *)&c, (void *)&q};
+    cudaError_t e = allow_ring((const void *)refine_kernel<T32, T64, PC>);
+    if (e != cudaSuccess) return e;
+    if (grid <= 1)
+        return cudaLaunchKernel((const void *)refine_kernel<T32, T64, PC>, dim3(1), dim3(kThreads), args, kRingBytes,
+                                st);
+    return cudaLaunchCooperativeKernel((const void *)refine_kernel<T32, T64, PC>, dim3(grid), dim3(kThreads),
+                                       args, kRingBytes, st);
+}
+
+template <typename T32, typename T64, bool PC>
+int refine_blocks_per_sm_pc() {
+    int nb = 0;
+    if (allow_ring((const void *)refine_kernel<T32, T64, PC>) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, refine_kernel<T32, T64, PC>, kThreads, kRingBytes) !=
+            cudaSuccess)
+        return 0;
+    return nb;
+}
+
 // Instantiated in mlb_kernels_ilu.cu.
+extern template cudaError_t launch_refine_pc<float, double, true>(const SysView<float> &, const RefView<double> &,
+                                                                  const SolveCtl &, const RefCtl &, int,
+                                                                  cudaStream_t);
+extern template cudaError_t launch_refine_pc<cfloat, cdouble, true>(const SysView<cfloat> &,
+                                                                    const RefView<cdouble> &, const SolveCtl &,
+                                                                    const RefCtl &, int, cudaStream_t);
+extern template int refine_blocks_per_sm_pc<float, double, true>();
+extern template int refine_blocks_per_sm_pc<cfloat, cdouble, true>();
+extern template cudaError_t launch_batch_refine_pc<float, double, true>(const BatchItemR<float, double> *,
+                                                                        const int *, int, unsigned *, int,
+                                                                        cudaStream_t);
+extern template cudaError_t launch_batch_refine_pc<cfloat, cdouble, true>(const BatchItemR<cfloat, cdouble> *,
+                                                                          const int *, int, unsigned *, int,
+                                                                          cudaStream_t);
+extern template int batch_refine_blocks_per_sm_pc<float, double, true>();
+extern template int batch_refine_blocks_per_sm_pc<cfloat, cdouble, true>();
+
 extern template cudaError_t launch_solve_pc<double, true>(const SysView<double> &, const SolveCtl &, int, cudaStream_t);
 extern template cudaError_t launch_solve_pc<cdouble, true>(const SysView<cdouble> &, const SolveCtl &, int,
                                                           cudaStream_t);

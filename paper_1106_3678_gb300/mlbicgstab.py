@@ -235,7 +235,7 @@ def mlbicgstab_create(A, AH=None, n: int = 4, q_seed: int = 0, Q=None,
     """Create a solver for CSR matrix ``A`` (see mlbicgstab_create in C).
     ``stream``: a torch.cuda.Stream, a raw cudaStream_t integer, or None.
     ``precond``: MLB_PRECOND_NONE, MLB_PRECOND_JACOBI (M = diag(A)) or
-    MLB_PRECOND_ILU0 (M = the ILU(0) factors of A; FP64 precision only)."""
+    MLB_PRECOND_ILU0 (M = the ILU(0) factors of A)."""
     lib = load()
     M = Matrix(A)
     MH = Matrix(AH) if AH is not None else None

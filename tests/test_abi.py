@@ -102,8 +102,11 @@ def test_invalid_arguments_are_rejected_before_gpu_work(lib):
     assert _raw_create(lib, A, precision=7)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, precond=5)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, precond=3)[0] == M.MLB_ERR_ARG
-    # ILU(0) runs in FP64 only
-    assert _raw_create(lib, A, precond=M.MLB_PRECOND_ILU0, precision=1)[0] == M.MLB_ERR_UNSUPPORTED
+    # refined mode: the reliable-update factor lies in (0, 1), the inner
+    # iteration cap is positive
+    assert _raw_create(lib, A, precision=1, inner_tol=0.0)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, precision=1, inner_tol=1.0)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, precision=1, inner_maxit=0)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, reserved0=1)[0] == M.MLB_ERR_ARG
     bad = W.CSR(A.row_ptr.copy(), A.col.copy(), A.val.copy(), A.n_rows)
     bad.col[3] = A.n_rows          # column out of range

@@ -167,10 +167,10 @@ def test_ilu_edge_cases():
     with pytest.raises(M.MlbError) as e:
         M.mlbicgstab_create(D, n=2, precond=ILU)
     assert e.value.code == M.MLB_ERR_ARG
-    # FP32-refined precision is not offered with ILU(0)
+    # the refined mode's FP32 factors are checked the same way
     with pytest.raises(M.MlbError) as e:
-        M.mlbicgstab_create(A, n=2, precond=ILU, precision=M.MLB_PREC_FP32_REFINED)
-    assert e.value.code == M.MLB_ERR_UNSUPPORTED
+        M.mlbicgstab_create(D, n=2, precond=ILU, precision=M.MLB_PREC_FP32_REFINED)
+    assert e.value.code == M.MLB_ERR_ARG
     # columns given out of order (and a repeated entry) are sorted and merged
     perm = np.concatenate([np.arange(A.row_ptr[r], A.row_ptr[r + 1])[::-1] for r in range(N)])
     S = W.CSR(row_ptr=A.row_ptr.copy(), col=A.col[perm].copy(), val=A.val[perm].copy(), n_rows=N)
