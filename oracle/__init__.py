@@ -20,6 +20,7 @@ Functions
     minv, minv_h        M^{-1} v and M^{-H} v
     solve               repeated calls from the current x until the true
                         residual meets tol (restart wrapper, not in the paper)
+    load_par            the multi-core build (pass as ``lib=``)
 """
 from __future__ import annotations
 
@@ -80,6 +81,34 @@ def load(path: str | None = None):
     if path is None:
         _LIB = lib
     return lib
+
+
+_LIB_PAR = None
+
+
+def load_par():
+    """The multi-core build of the oracle (OpenMP; inner products and norms
+    over fixed 1024-entry blocks, so results do not depend on the thread
+    count).  Pass it as ``lib=`` to any function here; ``par_threads``
+    sets its thread count."""
+    global _LIB_PAR
+    if _LIB_PAR is None:
+        _build.build()
+        lib = load(_build.OUT_PAR)
+        lib.orc_par_set_threads.restype = None
+        lib.orc_par_set_threads.argtypes = [C.c_int32]
+        lib.orc_par_max_threads.restype = C.c_int32
+        lib.orc_par_max_threads.argtypes = []
+        _LIB_PAR = lib
+    return _LIB_PAR
+
+
+def par_threads(t: int | None = None) -> int:
+    """Set (when t is given) and return the multi-core oracle's threads."""
+    lib = load_par()
+    if t is not None:
+        lib.orc_par_set_threads(int(t))
+    return int(lib.orc_par_max_threads())
 
 
 def _ptr(a):

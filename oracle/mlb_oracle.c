@@ -116,6 +116,19 @@ void orc_qgauss(uint64_t seed, int64_t N, int32_t n, int32_t is_complex,
     }
 }
 
+/* ---- multi-core build ----------------------------------------------------
+ * Compiled a second time with ORC_PAR and OpenMP (liborc_par.so): the
+ * same arithmetic, with elementwise loops shared among threads and inner
+ * products and norms taken over fixed 1024-entry blocks, so its results
+ * do not depend on the thread count (they differ from this sequential
+ * build in rounding order only).  Used to time the oracle on all host
+ * cores and to check long solves of large systems in reasonable time. */
+#ifdef ORC_PAR
+#include <omp.h>
+void orc_par_set_threads(int32_t t) { omp_set_num_threads(t > 0 ? t : 1); }
+int32_t orc_par_max_threads(void) { return (int32_t)omp_get_max_threads(); }
+#endif
+
 /* ---- the method, real FP64 ---------------------------------------------- */
 #define S double
 #define SFX(name) name##_d

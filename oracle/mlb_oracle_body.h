@@ -3,13 +3,16 @@
  * S = double (suffix _d) and once with S = double complex (suffix _z).
  * TEST INFRASTRUCTURE ONLY (see the header of mlb_oracle.c).
  *
- * Every vector operation is one plain sequential loop.  Inner products
+ * Every vector operation is one plain sequential loop (the multi-core
+ * build, ORC_PAR, shares elementwise loops among threads and takes inner
+ * products and norms over fixed blocks; see below).  Inner products
  * conjugate their left argument, u^H v = sum_i conj(u_i) v_i, as the paper's
  * ^H does; norms are sqrt(sum_i |v_i|^2).
  */
 
 /* ---- vector primitives (one Table 4.3 operation each) ------------------ */
 
+#ifndef ORC_PAR
 /* u^H v: one "dot product" of Table 4.3. */
 static S SFX(dot)(int64_t N, const S *u, const S *v, int64_t *ops)
 {
@@ -29,11 +32,60 @@ static double SFX(nrm2)(int64_t N, const S *v, int64_t *ops)
     ops[ORC_OP_NORM]++;
     return sqrt(s);
 }
+#else
+/* Multi-core build: the same sums taken over fixed blocks of ORC_BLOCK
+ * consecutive entries (each block summed in index order, then the block
+ * sums in block order), the blocks shared among threads.  The block
+ * partition does not depend on the thread count, so results are identical
+ * for every thread count; they differ from the sequential sums above only
+ * in rounding order. */
+#define ORC_BLOCK 1024
+static S SFX(dot)(int64_t N, const S *u, const S *v, int64_t *ops)
+{
+    const int64_t nb = (N + ORC_BLOCK - 1) / ORC_BLOCK;
+    S *part = (S *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(S));
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t i1 = (b + 1) * ORC_BLOCK < N ? (b + 1) * ORC_BLOCK : N;
+        S t = 0;
+        for (int64_t i = b * ORC_BLOCK; i < i1; ++i)
+            t += CONJ(u[i]) * v[i];
+        part[b] = t;
+    }
+    S s = 0;
+    for (int64_t b = 0; b < nb; ++b)
+        s += part[b];
+    free(part);
+    ops[ORC_OP_DOT]++;
+    return s;
+}
+
+static double SFX(nrm2)(int64_t N, const S *v, int64_t *ops)
+{
+    const int64_t nb = (N + ORC_BLOCK - 1) / ORC_BLOCK;
+    double *part = (double *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t i1 = (b + 1) * ORC_BLOCK < N ? (b + 1) * ORC_BLOCK : N;
+        double t = 0.0;
+        for (int64_t i = b * ORC_BLOCK; i < i1; ++i)
+            t += ABS2(v[i]);
+        part[b] = t;
+    }
+    double s = 0.0;
+    for (int64_t b = 0; b < nb; ++b)
+        s += part[b];
+    free(part);
+    ops[ORC_OP_NORM]++;
+    return sqrt(s);
+}
+#endif
 
 /* y = A x for CSR A: y_r = sum_k a_{r,col(k)} x_{col(k)} (row order). */
 static void SFX(csr_apply)(int64_t N, const int64_t *rp, const int32_t *ci,
                            const S *av, const S *x, S *y)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < N; ++r) {
         S s = 0;
         for (int64_t k = rp[r]; k < rp[r + 1]; ++k)
@@ -53,6 +105,7 @@ static void SFX(matvec)(int64_t N, const int64_t *rp, const int32_t *ci,
 /* y <- y + a x : one "saxpy". */
 static void SFX(axpy)(int64_t N, S a, const S *x, S *y, int64_t *ops)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i)
         y[i] = y[i] + a * x[i];
     ops[ORC_OP_SAXPY]++;
@@ -62,6 +115,7 @@ static void SFX(axpy)(int64_t N, S a, const S *x, S *y, int64_t *ops)
 static void SFX(xpay)(int64_t N, const S *x, S a, const S *y, S *out,
                       int64_t *ops)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i)
         out[i] = x[i] + a * y[i];
     ops[ORC_OP_SAXPY]++;
@@ -70,6 +124,7 @@ static void SFX(xpay)(int64_t N, const S *x, S a, const S *y, S *out,
 /* y <- a y : one "alpha v" of Table 4.3. */
 static void SFX(scal)(int64_t N, S a, S *y, int64_t *ops)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i)
         y[i] = a * y[i];
     ops[ORC_OP_SCALE]++;
@@ -79,6 +134,7 @@ static void SFX(scal)(int64_t N, S a, S *y, int64_t *ops)
  * written there) : counted as one "saxpy". */
 static void SFX(omega_corr)(int64_t N, const S *z, S omega, S *g, int64_t *ops)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i)
         g[i] = z[i] - g[i] / omega;
     ops[ORC_OP_SAXPY]++;
@@ -342,6 +398,7 @@ int SFX(orc_mlbicgstabt)(int64_t N, const int64_t *rp, const int32_t *ci,
 
     /* step 2: r_0 = b - A x_0 */
     SFX(matvec)(N, rp, ci, av, x, r, ops);
+#pragma omp parallel for schedule(static)
     for (int64_t t = 0; t < N; ++t)
         r[t] = b[t] - r[t];
     err = SFX(nrm2)(N, r, ops) / bnrm2;
