@@ -175,6 +175,12 @@ typedef struct {
                              its outputs written once */
     int64_t ops[5];       /* Table 4.3 operation counts of the last inner
                              call: matvec, dot, saxpy, scale (alpha v), norm */
+    double flops;         /* algorithmic floating-point operations of the
+                             solve kernel(s), real arithmetic: 2 per stored
+                             matrix entry per product (and per ILU(0) factor
+                             entry per M^{-1}), 2 per element per inner
+                             product, AXPY or norm, 1 per scaling; complex
+                             multiply-adds count 8 */
 } mlb_result;
 
 /* Facts about a handle. */

@@ -861,6 +861,7 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     res->err = d.err;
     res->true_relres = d.true_relres;
     res->bytes = d.bytes;
+    res->flops = d.flops;
     for (int q = 0; q < 5; ++q) res->ops[q] = d.ops[q];
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
@@ -1018,6 +1019,7 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
         res[s].err = d.err;
         res[s].true_relres = d.true_relres;
         res[s].bytes = d.bytes;
+        res[s].flops = d.flops;
         res[s].kernel_ms = ms;
         for (int q = 0; q < 5; ++q) res[s].ops[q] = d.ops[q];
         if (d.status != 0) rc = MLB_ERR_TIMEOUT;

@@ -54,6 +54,7 @@ struct DevResult {
     int64_t iter, spmv, outer;
     double err, true_relres, bytes;
     int64_t ops[5];
+    double flops;
 };
 
 enum { OP_MATVEC = 0, OP_DOT = 1, OP_SAXPY = 2, OP_SCALE = 3, OP_NORM = 4 };
@@ -63,6 +64,7 @@ struct Acct {
     int64_t ops[5];   // Table 4.3 categories of the current inner call
     int64_t spmv;     // all sparse products of the solve
     double bytes;     // algorithmic bytes of the solve
+    double flops;     // algorithmic floating-point operations of the solve
     // Scalars evaluated by thread 0 and read by every thread after a
     // __syncthreads: FP64 division and square root are costly on this GPU,
     // so they are not repeated by all threads.  Calls rotate through the
@@ -581,8 +583,23 @@ struct Engine {
         c_hi = s_hi * CPS;
     }
     __device__ void attach() { soff_load(gs.ring, sys.slice_ptr, s_lo, s_hi); }
+    // Counts one Table 4.3 operation and its algorithmic floating-point
+    // operations (real arithmetic): a product 2 per stored entry; an inner
+    // product, AXPY or norm 2 per element; a scaling 1 per element.
+    // Complex values: a multiply-add is 8 real operations, |v|^2 4, a
+    // scaling 6.
     __device__ __forceinline__ void op(int which, int cnt = 1) {
-        if (threadIdx.x == 0) acct->ops[which] += cnt;
+        if (threadIdx.x == 0) {
+            acct->ops[which] += cnt;
+            constexpr bool cx_ = is_cx<T>::value;
+            const double N = (double)sys.N;
+            double f;
+            if (which == OP_MATVEC) f = (cx_ ? 8.0 : 2.0) * (double)sys.nnz;
+            else if (which == OP_SCALE) f = (cx_ ? 6.0 : 1.0) * N;
+            else if (which == OP_NORM) f = (cx_ ? 4.0 : 2.0) * N;
+            else f = (cx_ ? 8.0 : 2.0) * N;
+            acct->flops += (double)cnt * f;
+        }
     }
 
     // Evaluate fn() in thread 0 only and give the value to every thread.
@@ -831,8 +848,10 @@ struct Engine {
             }
             if (!gs.wait()) return false;
         }
-        if (threadIdx.x == 0)   // factors and row data once, v read, out written and re-read
+        if (threadIdx.x == 0) {   // factors and row data once, v read, out written and re-read
             acct->bytes += (double)M.nnz * (sizeof(T) + 4) + (double)sys.N * (8 + 4 + 8 + 3 * sizeof(T));
+            acct->flops += (is_cx<T>::value ? 8.0 : 2.0) * (double)M.nnz;
+        }
         return true;
     }
 

@@ -97,6 +97,7 @@ struct Refiner {
         if (threadIdx.x == 0) {
             acct->bytes += (double)v.nnz * (sizeof(T64) + 4) + 4.0 * (double)(v.N + 1) +
                            3.0 * (double)v.N * sizeof(T64);
+            acct->flops += (DS == 2 ? 8.0 : 2.0) * (double)v.nnz + (DS == 2 ? 10.0 : 5.0) * (double)v.N;
             acct->spmv++;
         }
         return true;

@@ -67,6 +67,7 @@ __device__ void run_fp64_solve(Engine<T, PC> &E, GridSync &gs, const SolveCtl &c
         res->err = o.err;
         res->true_relres = true_rel;
         res->bytes = acct.bytes;
+        res->flops = acct.flops;
         for (int q = 0; q < 5; ++q) res->ops[q] = ops_last[q];
     }
 }
@@ -89,6 +90,7 @@ __device__ __forceinline__ void acct_reset(Acct &acct) {
         for (int q = 0; q < 5; ++q) acct.ops[q] = 0;
         acct.spmv = 0;
         acct.bytes = 0.0;
+        acct.flops = 0.0;
     }
     __syncthreads();
 }
@@ -267,6 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             res->err = o.err;
             res->true_relres = o.err;
             res->bytes = acct.bytes;
+            res->flops = acct.flops;
             for (int k = 0; k < 5; ++k) res->ops[k] = acct.ops[k];
         }
         __syncthreads();
@@ -347,6 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         res->err = o.err;
         res->true_relres = o.err;
         res->bytes = acct.bytes;
+        res->flops = acct.flops;
         for (int q = 0; q < 5; ++q) res->ops[q] = acct.ops[q];
     }
 }

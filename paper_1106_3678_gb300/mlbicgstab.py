@@ -56,7 +56,7 @@ class mlb_result(C.Structure):
                 ("spmv", C.c_int64), ("outer", C.c_int64),
                 ("err", C.c_double), ("true_relres", C.c_double),
                 ("kernel_ms", C.c_double), ("bytes", C.c_double),
-                ("ops", C.c_int64 * 5)]
+                ("ops", C.c_int64 * 5), ("flops", C.c_double)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "ops"}

@@ -52,10 +52,11 @@ def test_struct_layout_matches_c_compiler(tmp_path):
 int main(void) {{
   printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mlb_matrix), sizeof(mlb_options),
          sizeof(mlb_result), sizeof(mlb_info), sizeof(mlb_sequence_options), sizeof(mlb_tune_result));
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(mlb_options, stream),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(mlb_options, stream),
          offsetof(mlb_options, timeout_ns), offsetof(mlb_result, ops),
          offsetof(mlb_options, precond), offsetof(mlb_info, precond),
-         offsetof(mlb_info, n_active), offsetof(mlb_info, qd_kernel_ms));
+         offsetof(mlb_info, n_active), offsetof(mlb_info, qd_kernel_ms),
+         offsetof(mlb_result, flops));
   return 0;
 }}''')
     exe = tmp_path / "layout"
@@ -69,7 +70,8 @@ int main(void) {{
     assert [int(v) for v in offs.split()] == [
         M.mlb_options.stream.offset, M.mlb_options.timeout_ns.offset,
         M.mlb_result.ops.offset, M.mlb_options.precond.offset,
-        M.mlb_info.precond.offset, M.mlb_info.n_active.offset, M.mlb_info.qd_kernel_ms.offset]
+        M.mlb_info.precond.offset, M.mlb_info.n_active.offset, M.mlb_info.qd_kernel_ms.offset,
+        M.mlb_result.flops.offset]
 
 
 def test_strerror_and_defaults(lib):

@@ -25,3 +25,12 @@ def test_headline_conversion_count_is_set():
     # the reference arm converts its per-iteration time with this count
     assert bench.WORKLOADS[bench.DEFAULT]["iters"] > 0
     assert bench.NCU_DRAM_BYTES_PER_ITER is None or bench.NCU_DRAM_BYTES_PER_ITER > 0
+
+
+def test_pairs_name_known_workloads_and_converged_rule():
+    for name, base, key in bench.PAIRS:
+        assert name in bench.WORKLOADS and base in bench.WORKLOADS and key.startswith("speedup")
+    assert bench._converged({"flags": [0, 0], "true_relres": [1e-11, 9e-11]}, 1e-10) is True
+    assert bench._converged({"flags": [0, 1], "true_relres": [1e-11, 9e-11]}, 1e-10) is False
+    assert bench._converged({"flags": [0], "true_relres": [2e-10]}, 1e-10) is False
+    assert bench._converged({"flags": [0], "true_relres_max": 5e-11}, 1e-10) is True

@@ -78,3 +78,17 @@ def test_batch_sizes():
     assert 9e6 < Ns.sum() < 13e6
     dims = [m["dim"] for _, m in sys_]
     assert 180 < dims.count(2) < 330
+
+
+def test_iteration_window_is_a_prediction_interval():
+    from tests import spread
+    lo, hi = spread.window([100] * 17)
+    assert (lo, hi) == (99.0, 101.0)
+    c = [100, 104, 98, 101, 97, 103, 99, 100, 102, 96, 105, 100, 99, 101, 98, 100, 102]
+    lo, hi = spread.window(c)
+    m, s = np.mean(c), np.std(c, ddof=1)
+    assert np.isclose(hi - m, 4.015 * s * np.sqrt(1 + 1 / 17))
+    assert lo <= min(c) and hi >= max(c)
+    b = np.arange(5.0)
+    bb = spread.perturbed(b, 1)
+    assert np.count_nonzero(bb != b) == 1 and np.all(bb >= b)
