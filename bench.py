@@ -680,8 +680,11 @@ def run_ours(args, wl):
     by_name.setdefault(args.workload, {"workload": args.workload, "value": head_value, "converged": head_ok})
     for v in variants:
         if v["workload"] in ("cd3d128_n4_fp64_jacobi", "cd3d128_n4_fp64_ilu0"):
-            v["pairs"] = {"speedup_vs_unpreconditioned": v["value"] / head_value if v.get("converged") and head_ok
-                          else None}
+            ok = bool(v.get("converged")) and head_ok
+            v["pairs"] = {"speedup_vs_unpreconditioned": {
+                "against": args.workload, "speedup": v["value"] / head_value if ok else None,
+                "both_converged": ok, "iters": v.get("iters_per_solve"),
+                "iters_against": [r["iter"] for r in results]}}
     for name, base, key in PAIRS:
         v, bv = by_name.get(name), by_name.get(base)
         if v is None or bv is None or "value" not in v:

@@ -42,7 +42,7 @@ def par():
     return lib
 
 
-def _full(par, A, b, n, tol=1e-10, maxit=40000, AH=None, precond=M.MLB_PRECOND_NONE):
+def _full(par, A, b, n, tol=1e-10, maxit=40000, AH=None, precond=M.MLB_PRECOND_NONE, x_bound=1e-8):
     import torch
     cplx = np.iscomplexobj(A.val)
     dt = torch.complex128 if cplx else torch.float64
@@ -59,7 +59,8 @@ def _full(par, A, b, n, tol=1e-10, maxit=40000, AH=None, precond=M.MLB_PRECOND_N
     assert res.true_relres < tol
     assert O.true_relres(A, b, x, lib=par) < tol
     rel = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
-    assert rel <= 1e-8, (rel, res.iter, ref.iter)
+    bound = x_bound(x, ref) if callable(x_bound) else x_bound
+    assert rel <= bound, (rel, bound, res.iter, ref.iter)
     info = M.mlbicgstab_info(h)
     h.destroy()
     return res, ref, info
@@ -92,6 +93,27 @@ def test_full_solve_complex_helmholtz_64x64x16(par):
 
 
 def test_full_solve_reservoir_without_preconditioner(par):
-    """The 3x3-block reservoir family at a size where M = I converges."""
-    A = W.bsr3_to_csr(W.reservoir_bsr3(16, 16, 8))
-    _full(par, A, W.row_sums(A), 8)
+    """The 3x3-block reservoir family at a size where M = I converges
+    (12 x 12 x 6 cells, N = 2,592, about 8,000 iterations).  This family is
+    ill-conditioned (cond_2(A) ~ 2e6 here), so two solutions that both
+    meet tol = 1e-10 need not agree to 1e-8: the oracle's own solution is
+    ~2e-6 away from the exact one (x* = 1).  The bar is what the residuals
+    imply: A (x - x_or) = r_or - r, so
+        ||x - x_or|| <= ||A^{-1}||_2 (||r|| + ||r_or||),
+    with ||A^{-1}||_2 = 1 / sigma_min(A) from a dense SVD, and the 1e-8
+    bar wherever that bound is smaller."""
+    A = W.bsr3_to_csr(W.reservoir_bsr3(12, 12, 6))
+    b = W.row_sums(A)
+    N = A.n_rows
+    D = np.zeros((N, N))
+    for r in range(N):
+        k0, k1 = A.row_ptr[r], A.row_ptr[r + 1]
+        np.add.at(D[r], A.col[k0:k1], A.val[k0:k1])
+    inv_norm = 1.0 / np.linalg.svd(D, compute_uv=False)[-1]
+    bn = np.linalg.norm(b)
+
+    def bound(x, ref):
+        rr = (O.true_relres(A, b, x, lib=par) + ref.true_relres) * bn
+        return max(1e-8, 1.0001 * inv_norm * rr / np.linalg.norm(ref.x))
+
+    _full(par, A, b, 8, x_bound=bound)
