@@ -49,7 +49,9 @@ extern "C" {
 
 /* ---- value types ------------------------------------------------------- */
 #define MLB_F64 0   /* double */
+#define MLB_F32 1   /* float (the FP32 copies of a refined handle) */
 #define MLB_C128 2  /* complex double, interleaved (re, im) */
+#define MLB_C64 3   /* complex float, interleaved (re, im) */
 
 /* ---- precision modes --------------------------------------------------- */
 /* Preconditioner M of Algorithm 7.1 (right preconditioning). */
@@ -336,6 +338,28 @@ int mlbicgstab_autotune(mlb_handle *h, int32_t iters, int32_t use_cache,
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d);
 /* (MLB_ERR_UNSUPPORTED for a handle with a preconditioner: it stores
  * A M^{-1}, not A.) */
+
+/*
+ * Asynchronous form of mlbicgstab_spmv_qdot for pipelined callers: the same
+ * fused y = A x, d = Q^H y, enqueued on the handle's stream with the
+ * result left in device memory; the call returns without waiting.
+ *   value_type  MLB_F64 (MLB_C128 for complex handles): the handle's FP64
+ *               matrix and Q; x, y hold doubles (complex doubles).
+ *               MLB_F32 (MLB_C64): the FP32 copies a MLB_PREC_FP32_REFINED
+ *               handle keeps for its inner solve; x, y hold floats
+ *               (complex floats), products and per-thread sums are FP32,
+ *               sums across threads and CTAs FP64.  MLB_ERR_UNSUPPORTED
+ *               for an FP64 handle.
+ *   x, y        device arrays of N values of that type
+ *   d           device array of n_active * k + 1 doubles (k = 1 real,
+ *               2 complex): the inner products (complex as re, im), then a
+ *               status word, 1.0 if a wait inside the kernel gave up (d
+ *               and y are then invalid), else 0.0
+ * Calls on one handle share its scratch and must not overlap on the GPU
+ * (back-to-back calls on the handle's stream are ordered and fine).
+ * MLB_ERR_ARG for a pointer that is not device memory of the handle's GPU.
+ */
+int mlbicgstab_spmv_qdot_async(mlb_handle *h, int32_t value_type, const void *x, void *y, void *d);
 
 /*
  * Allocation-free variant of mlbicgstab_spmv_qdot: y = A x and d = Q^H y

@@ -1166,32 +1166,63 @@ int mlbicgstab_solve_sequence(mlb_handle *const *hs, int32_t count, const void *
     return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Enqueue the fused product on the handle's stream: values of type `vt`
+// (the FP64 data, or a refined handle's FP32 copies), d = device array of
+// n_active * DS doubles plus the status word.  ev0 is recorded directly
+// before the kernel when `timed`.
+int qd_enqueue(mlb_handle *h, int32_t vt, const void *x, void *y, double *d, bool timed) {
+    const bool narrow = vt == MLB_F32 || vt == MLB_C64;
+    const bool cplx = h->dtype == MLB_C128;
+    if (vt != (cplx ? MLB_C128 : MLB_F64) && vt != (cplx ? MLB_C64 : MLB_F32)) return MLB_ERR_ARG;
+    if (narrow && h->precision != MLB_PREC_FP32_REFINED) return MLB_ERR_UNSUPPORTED;
+    cudaStream_t st = h->stream;
+    cudaEvent_t ev = timed ? h->ev0 : nullptr;
+    // x is gathered from the caller's array (SELL padding columns are
+    // clamped below N); y goes to the caller's array and to the handle's
+    // padded buffer r, which the inner products stream back
+    const int grid = std::max(1, std::min(h->grid_want, h->grid_max));
+    // tiles of the product carry the fused columns of Q as epilogue vectors
+    const size_t vb = narrow ? h->esize / 2 : h->esize;
+    const int spt = std::min(slices_per_tile(h->maxw, vb, qd_fused_columns(h->n_active, cplx)), h->spt_cap);
+    cudaError_t e;
+    if (narrow && cplx)
+        e = launch_spmv_qdot_tiled<cfloat>(make_view32<cfloat>(h), spt, (const cfloat *)x, (cfloat *)h->r32,
+                                           (cfloat *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
+                                           st);
+    else if (narrow)
+        e = launch_spmv_qdot_tiled<float>(make_view32<float>(h), spt, (const float *)x, (float *)h->r32,
+                                          (float *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev, st);
+    else if (cplx)
+        e = launch_spmv_qdot_tiled<cdouble>(make_view<cdouble>(h), spt, (const cdouble *)x, (cdouble *)h->r,
+                                            (cdouble *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
+                                            st);
+    else
+        e = launch_spmv_qdot_tiled<double>(make_view<double>(h), spt, (const double *)x, (double *)h->r,
+                                           (double *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
+                                           st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    return MLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
     if (!h || !x || !y || !d) return MLB_ERR_ARG;
     if (h->precond != MLB_PRECOND_NONE) return MLB_ERR_UNSUPPORTED;
     MLB_CUDA(cudaSetDevice(h->device));
     if (!is_device_ptr(x, h->device) || !is_device_ptr(y, h->device)) return MLB_ERR_ARG;
     cudaStream_t st = h->stream;
-    cudaError_t e;
-    // x is gathered from the caller's array (SELL padding columns are
-    // clamped below N); y goes to the caller's array and to the handle's
-    // padded buffer r, which the inner products stream back
-    const int grid = std::max(1, std::min(h->grid_want, h->grid_max));
-    // tiles of the product carry the fused columns of Q as epilogue vectors
     const bool cplx = h->dtype == MLB_C128;
-    const int spt = std::min(slices_per_tile(h->maxw, h->esize, qd_fused_columns(h->n_active, cplx)), h->spt_cap);
-    if (cplx)
-        e = launch_spmv_qdot_tiled<cdouble>(make_view<cdouble>(h), spt, (const cdouble *)x, (cdouble *)h->r,
-                                            (cdouble *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket,
-                                            h->qd_out, h->ev0, st);
-    else
-        e = launch_spmv_qdot_tiled<double>(make_view<double>(h), spt, (const double *)x, (double *)h->r,
-                                           (double *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket,
-                                           h->qd_out, h->ev0, st);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return MLB_ERR_CUDA;
-    }
+    if (int rc = qd_enqueue(h, cplx ? MLB_C128 : MLB_F64, x, y, h->qd_out, true)) return rc;
     MLB_CUDA(cudaEventRecord(h->ev1, st));
     // d and the status flag behind it in one copy, through pinned memory
     const size_t nv = (size_t)h->n_active * (cplx ? 2 : 1);
@@ -1203,6 +1234,15 @@ int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
     if (h->qd_host[nv] != 0.0) return MLB_ERR_TIMEOUT;
     memcpy(d, h->qd_host, nv * 8);
     return MLB_OK;
+}
+
+int mlbicgstab_spmv_qdot_async(mlb_handle *h, int32_t value_type, const void *x, void *y, void *d) {
+    if (!h || !x || !y || !d) return MLB_ERR_ARG;
+    if (h->precond != MLB_PRECOND_NONE) return MLB_ERR_UNSUPPORTED;
+    MLB_CUDA(cudaSetDevice(h->device));
+    if (!is_device_ptr(x, h->device) || !is_device_ptr(y, h->device) || !is_device_ptr(d, h->device))
+        return MLB_ERR_ARG;
+    return qd_enqueue(h, value_type, x, y, (double *)d, false);
 }
 
 int mlbicgstab_selftest_barrier_timeout(int32_t grid, int64_t timeout_ns) {

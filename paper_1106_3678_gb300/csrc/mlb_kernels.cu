@@ -378,6 +378,12 @@ template cudaError_t launch_spmv_qdot_tiled<double>(const SysView<double> &, int
 template cudaError_t launch_spmv_qdot_tiled<cdouble>(const SysView<cdouble> &, int, const cdouble *, cdouble *,
                                                      cdouble *, double *, int, int *, unsigned *, double *,
                                                      cudaEvent_t, cudaStream_t);
+template cudaError_t launch_spmv_qdot_tiled<float>(const SysView<float> &, int, const float *, float *, float *,
+                                                   double *, int, int *, unsigned *, double *, cudaEvent_t,
+                                                   cudaStream_t);
+template cudaError_t launch_spmv_qdot_tiled<cfloat>(const SysView<cfloat> &, int, const cfloat *, cfloat *,
+                                                    cfloat *, double *, int, int *, unsigned *, double *,
+                                                    cudaEvent_t, cudaStream_t);
 template cudaError_t launch_refine<float, double>(const SysView<float> &, const RefView<double> &,
                                                   const SolveCtl &, const RefCtl &, int, cudaStream_t);
 template cudaError_t launch_refine<cfloat, cdouble>(const SysView<cfloat> &, const RefView<cdouble> &,

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmlbicgstab.so")
 
 MLB_OK, MLB_ERR_ARG, MLB_ERR_CUDA, MLB_ERR_OOM, MLB_ERR_TIMEOUT, MLB_ERR_UNSUPPORTED = range(6)
-MLB_F64, MLB_C128 = 0, 2
+MLB_F64, MLB_F32, MLB_C128, MLB_C64 = 0, 1, 2, 3
 MLB_PREC_FP64, MLB_PREC_FP32_REFINED = 0, 1
 MLB_PRECOND_NONE, MLB_PRECOND_JACOBI, MLB_PRECOND_ILU0 = 0, 1, 2
 
@@ -29,7 +29,7 @@ EXPORTS = (
     "mlbicgstab_info", "mlbicgstab_destroy", "mlbicgstab_strerror",
     "mlbicgstab_selftest_barrier_timeout", "mlbicgstab_spmv_qdot_noalloc",
     "mlbicgstab_set_n", "mlbicgstab_next_n", "mlbicgstab_solve_sequence",
-    "mlbicgstab_autotune",
+    "mlbicgstab_autotune", "mlbicgstab_spmv_qdot_async",
 )
 
 
@@ -118,6 +118,8 @@ def load(path: str | None = None):
                                            C.POINTER(mlb_result)]
     lib.mlbicgstab_spmv_qdot.restype = C.c_int
     lib.mlbicgstab_spmv_qdot.argtypes = [P, P, P, P]
+    lib.mlbicgstab_spmv_qdot_async.restype = C.c_int
+    lib.mlbicgstab_spmv_qdot_async.argtypes = [P, C.c_int32, P, P, P]
     lib.mlbicgstab_get_Q.restype = C.c_int
     lib.mlbicgstab_get_Q.argtypes = [P, P]
     lib.mlbicgstab_info.restype = C.c_int
@@ -363,6 +365,22 @@ def mlbicgstab_spmv_qdot(h: Handle, x, y) -> np.ndarray:
     _check(load().mlbicgstab_spmv_qdot(h.ptr, px, py, d.ctypes.data),
            "mlbicgstab_spmv_qdot")
     return d
+
+
+def mlbicgstab_spmv_qdot_async(h: Handle, x, y, d) -> None:
+    """Enqueue y = A x, d = Q^H y on the handle's stream (no wait).  x, y,
+    d are CUDA tensors: x, y float64/complex128 (the handle's FP64 data) or
+    float32/complex64 (a refined handle's FP32 copies); d float64 with
+    n_active * (2 if complex else 1) + 1 entries (the last one is the
+    status word)."""
+    import torch
+    ptrs = [_ptr(a) for a in (x, y, d)]
+    if not all(dv for _, dv in ptrs):
+        raise ValueError("x, y, d must be CUDA tensors")
+    vt = {torch.float64: MLB_F64, torch.float32: MLB_F32, torch.complex128: MLB_C128,
+          torch.complex64: MLB_C64}[x.dtype]
+    _check(load().mlbicgstab_spmv_qdot_async(h.ptr, vt, ptrs[0][0], ptrs[1][0], ptrs[2][0]),
+           "mlbicgstab_spmv_qdot_async")
 
 
 def mlbicgstab_spmv_qdot_noalloc(row_ptr, col_idx, values, x, Q, y, d,

@@ -164,6 +164,84 @@ def test_spmv_qdot_complex():
     _check_spmv_qdot(W.helmholtz3d_c(10, 9, 7), 6)
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n", [1, 4, 9])
+def test_spmv_qdot_async_fp64_equals_the_synchronous_call(n, cplx):
+    """The asynchronous entry point runs the same kernel: y and d equal the
+    synchronous call's bit for bit; d stays on the device with the status
+    word 0 behind it."""
+    import torch
+    A = W.helmholtz3d_c(9, 8, 7) if cplx else W.cd3d_lognormal(21)
+    dt = torch.complex128 if cplx else torch.float64
+    h = M.mlbicgstab_create(A, n=n, q_seed=5)
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(A.n_rows) + (1j * rng.standard_normal(A.n_rows) if cplx else 0)
+    xd = torch.tensor(x, dtype=dt, device="cuda")
+    y1, y2 = torch.empty_like(xd), torch.empty_like(xd)
+    d1 = M.mlbicgstab_spmv_qdot(h, xd, y1)
+    k = 2 if cplx else 1
+    dd = torch.full((n * k + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):   # back-to-back launches on the handle's stream
+        M.mlbicgstab_spmv_qdot_async(h, xd, y2, dd)
+    torch.cuda.synchronize()
+    d2 = dd.cpu().numpy()
+    assert d2[-1] == 0.0
+    d2 = d2[:-1].view(np.complex128) if cplx else d2[:-1]
+    np.testing.assert_array_equal(d2, d1)
+    assert torch.equal(y1, y2)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n", [1, 4, 16])
+def test_spmv_qdot_fp32_copies_of_a_refined_handle(n, cplx):
+    """FP32 product and FP32 per-thread inner products (FP64 across threads
+    and CTAs) against the oracle's FP64 product of the same FP32-rounded
+    values.  y: each row sums at most w FP32 products, within gamma32_w of
+    the exact sum of |a||x| (Higham, Thm 3.1, u = 2^-24), the oracle within
+    gamma64_w.  d: the propagated y difference plus gamma32_N |q|^T |y|."""
+    import torch
+    A = W.helmholtz3d_c(10, 9, 7) if cplx else W.cd3d_lognormal(23)
+    h = M.mlbicgstab_create(A, n=n, q_seed=2, precision=M.MLB_PREC_FP32_REFINED)
+    rng = np.random.default_rng(3 + n)
+    x = rng.standard_normal(A.n_rows) + (1j * rng.standard_normal(A.n_rows) if cplx else 0)
+    dt32, npt32 = (torch.complex64, np.complex64) if cplx else (torch.float32, np.float32)
+    x32 = x.astype(npt32)
+    xd = torch.tensor(x32, dtype=dt32, device="cuda")
+    yd = torch.empty_like(xd)
+    k = 2 if cplx else 1
+    dd = torch.zeros(n * k + 1, dtype=torch.float64, device="cuda")
+    M.mlbicgstab_spmv_qdot_async(h, xd, yd, dd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy().astype(np.complex128 if cplx else np.float64)
+    d = dd.cpu().numpy()
+    assert d[-1] == 0.0
+    d = d[:-1].view(np.complex128) if cplx else d[:-1]
+    A32 = W.CSR(A.row_ptr, A.col, A.val.astype(npt32).astype(A.val.dtype), A.n_rows)
+    xw = x32.astype(x.dtype)
+    yo = O.spmv(A32, xw)
+    w = int(np.max(np.diff(A.row_ptr))) + 1
+    u32 = 2.0 ** -24
+    g32 = lambda m: m * u32 / (1 - m * u32)
+    bound_y = (g32(w) + _gamma(w)) * _abs_spmv(A32, xw) * (4 if cplx else 1)
+    assert np.all(np.abs(y - yo) <= bound_y + 1e-300), np.max(np.abs(y - yo) - bound_y)
+    Q32 = M.mlbicgstab_get_Q(h).astype(npt32).astype(x.dtype)
+    do = Q32.conj().T @ y
+    bd = (np.abs(Q32).T @ bound_y) + g32(A.n_rows) * (4 if cplx else 1) * (np.abs(Q32).T @ np.abs(y))
+    assert np.all(np.abs(d - do) <= bd + np.abs(Q32).T @ np.abs(y - yo)), (d, do)
+
+
+def test_spmv_qdot_async_rejects_fp32_on_an_fp64_handle():
+    import torch
+    A = W.cd2d(16)
+    h = M.mlbicgstab_create(A, n=2)
+    x = torch.ones(A.n_rows, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    d = torch.empty(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(M.MlbError) as e:
+        M.mlbicgstab_spmv_qdot_async(h, x, y, d)
+    assert e.value.code == M.MLB_ERR_UNSUPPORTED
+
+
 def test_spmv_qdot_full_size_cd3d():
     """The 128^3 workload at full size, every row checked."""
     _check_spmv_qdot(W.cd3d_lognormal(128), 4)
