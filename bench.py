@@ -81,6 +81,15 @@ WORKLOADS = {
     "cd3d128_n4_refined_ilu0": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=1, precond=2),
     "reservoir_n8_refined_ilu0": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=1, precond=2),
     "batch512_n4_refined_ilu0": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=1, precond=2),
+    # ILU(0) in a multicolour order (precond 3): one level per colour in the
+    # triangular solves instead of one per wavefront; a different (weaker)
+    # preconditioner than the paper's natural-order ILU(0)
+    "cd3d128_n4_fp64_ilu0mc": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=0, precond=3),
+    "cd3d128_n4_refined_ilu0mc": dict(kind="cd3d", m=128, n=4, tol=1e-10, maxit=40000, precision=1, precond=3),
+    "reservoir_n8_fp64_ilu0mc": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=0, precond=3),
+    "reservoir_n8_refined_ilu0mc": dict(kind="reservoir", n=8, tol=1e-10, maxit=20000, precision=1, precond=3),
+    "batch512_n4_fp64_ilu0mc": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0, precond=3),
+    "helmholtz_n8_c128_ilu0mc": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=0, precond=3),
     # the fused product y = A x, d = Q^H y alone (mlbicgstab_spmv_qdot) on
     # the headline matrix, for n = 1, 4, 16 shadow vectors
     "spmv_qdot_cd3d128": dict(kind="spmv_qdot", m=128, n=4, ns=(1, 4, 16), calls=50),
@@ -98,16 +107,23 @@ DEFAULT = "cd3d128_n4_fp64"
 # captured again.
 NCU_DRAM_BYTES_PER_ITER = (136.82e9 + 34.61e9) / 300
 VARIANTS = ["spmv_qdot_cd3d128", "cd3d128_n1_fp64", "cd3d128_n8_fp64", "cd3d128_n16_fp64",
-            "cd3d128_n4_fp64_ilu0", "cd3d128_n4_refined_ilu0",
+            "cd3d128_n4_fp64_ilu0", "cd3d128_n4_refined_ilu0", "cd3d128_n4_fp64_ilu0mc", "cd3d128_n4_refined_ilu0mc",
             "reservoir_n8_fp64", "reservoir_n8_fp64_ilu0", "reservoir_n8_refined_ilu0",
-            "batch512_n4_fp64", "batch512_n4_fp64_ilu0", "batch512_n4_refined", "batch512_n4_refined_ilu0",
-            "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07", "helmholtz_n8_c64_refined",
+            "reservoir_n8_fp64_ilu0mc", "reservoir_n8_refined_ilu0mc",
+            "batch512_n4_fp64", "batch512_n4_fp64_ilu0", "batch512_n4_fp64_ilu0mc",
+            "batch512_n4_refined", "batch512_n4_refined_ilu0",
+            "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07", "helmholtz_n8_c128_ilu0mc", "helmholtz_n8_c64_refined",
             "sequence8_cd3d64", "tune_cd2d256"]
 # (variant, the variant it is compared with): refined against FP64 with the
 # same preconditioner, preconditioned against unpreconditioned, the omega
 # guard against kappa = 0.  A speedup is reported only when both sides
 # converged (every solve flag 0 with true relative residual below tol).
 PAIRS = [("cd3d128_n4_refined_ilu0", "cd3d128_n4_fp64_ilu0", "speedup_vs_fp64"),
+         ("cd3d128_n4_refined_ilu0mc", "cd3d128_n4_fp64_ilu0mc", "speedup_vs_fp64"),
+         ("reservoir_n8_refined_ilu0mc", "reservoir_n8_fp64_ilu0mc", "speedup_vs_fp64"),
+         ("reservoir_n8_fp64_ilu0mc", "reservoir_n8_fp64", "speedup_vs_unpreconditioned"),
+         ("batch512_n4_fp64_ilu0mc", "batch512_n4_fp64", "speedup_vs_unpreconditioned"),
+         ("helmholtz_n8_c128_ilu0mc", "helmholtz_n8_c128", "speedup_vs_unpreconditioned"),
          ("reservoir_n8_refined_ilu0", "reservoir_n8_fp64_ilu0", "speedup_vs_fp64"),
          ("batch512_n4_refined_ilu0", "batch512_n4_fp64_ilu0", "speedup_vs_fp64"),
          ("batch512_n4_refined", "batch512_n4_fp64", "speedup_vs_fp64"),
@@ -183,6 +199,8 @@ def _variant_desc(name, wl, systems):
         extra += ", Jacobi M=diag(A) (Algorithm 7.1)"
     if wl.get("precond", 0) == 2:
         extra += ", ILU(0) M=LU (Algorithm 7.1; level-scheduled triangular solves)"
+    if wl.get("precond", 0) == 3:
+        extra += ", multicolour ILU(0) M=P^T LU P (one triangular-solve level per colour)"
     return f"{what} (N={N:,}, nnz={nnz:,}), n={wl['n']}, {_prec_name(wl)}{extra}, tol {wl['tol']:g}"
 
 
@@ -442,7 +460,7 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
     steps = max(1, args.variant_steps)
     out = {"workload": name, "config": _variant_desc(name, vwl, systems),
            "precision": _prec_name(vwl), "n": vwl["n"], "unit": UNIT,
-           "kappa": vwl.get("kappa", 0.0), "precond": ["none", "jacobi", "ilu0"][vwl.get("precond", 0)]}
+           "kappa": vwl.get("kappa", 0.0), "precond": ["none", "jacobi", "ilu0", "ilu0_mc"][vwl.get("precond", 0)]}
     if vwl["kind"] == "batch":
         def once():
             for x in xs:
@@ -715,7 +733,7 @@ def run_ours(args, wl):
     by_name = {v["workload"]: v for v in variants}
     by_name.setdefault(args.workload, {"workload": args.workload, "value": head_value, "converged": head_ok})
     for v in variants:
-        if v["workload"] in ("cd3d128_n4_fp64_jacobi", "cd3d128_n4_fp64_ilu0"):
+        if v["workload"] in ("cd3d128_n4_fp64_jacobi", "cd3d128_n4_fp64_ilu0", "cd3d128_n4_fp64_ilu0mc"):
             ok = bool(v.get("converged")) and head_ok
             v["pairs"] = {"speedup_vs_unpreconditioned": {
                 "against": args.workload, "speedup": v["value"] / head_value if ok else None,

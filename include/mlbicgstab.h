@@ -58,6 +58,8 @@ extern "C" {
 #define MLB_PRECOND_NONE 0   /* M = I: Algorithm 4.1 */
 #define MLB_PRECOND_JACOBI 1 /* M = diag(A) (every diagonal entry nonzero) */
 #define MLB_PRECOND_ILU0 2   /* M = L U, the ILU(0) factors of A */
+#define MLB_PRECOND_ILU0_MC 3 /* M = P^T L U P, the ILU(0) factors of
+                                 P A P^T for a multicolour order P */
 
 #define MLB_PREC_FP64 0     /* matrix, vectors and arithmetic in FP64 */
 #define MLB_PREC_FP32_REFINED 1 /* inner ML(n)BiCGStab in FP32 (values,
@@ -151,7 +153,23 @@ typedef struct {
                              the kernel.  In refined mode the inner
                              FP32 solve applies FP32 copies of the
                              factors.  MLB_ERR_ARG when a row has no stored
-                             diagonal or a pivot is zero.  Handles with different
+                             diagonal or a pivot is zero.
+                             MLB_PRECOND_ILU0_MC: the same with A's rows
+                             and columns first reordered by colour (P A
+                             P^T; the order of mlbicgstab_get_perm): greedy
+                             colouring of A's symmetrised adjacency graph
+                             in natural order, colour classes in colour
+                             order.  The triangular solves then take one
+                             level per colour (2 for a 7-point stencil)
+                             instead of one per wavefront of the natural
+                             order (382 at 128^3), at the price of a
+                             weaker preconditioner (usually more
+                             iterations).  Not the paper's natural-order
+                             ILU(0).  The handle solves P A P^T y = P b
+                             and returns x = P^T y; b, x0, x, Q and
+                             mlbicgstab_get_Q stay in the caller's row
+                             order (drawn Q entries keep their original
+                             row index).  Handles with different
                              preconditioners may share one batch. */
     int32_t reserved0;    /* must be 0 */
 } mlb_options;
@@ -193,7 +211,9 @@ typedef struct {
     int64_t nnz_padded;   /* stored SELL-32 entries (>= nnz) */
     int64_t device_bytes; /* device memory held by the handle */
     int32_t n_active;     /* shadow vectors the next solve uses (<= n) */
-    int32_t reserved1;
+    int32_t ilu_levels;   /* levels of the forward triangular solve of an
+                             ILU(0) handle (one grid barrier each); 0
+                             otherwise */
     double qd_kernel_ms;  /* device time of the last mlbicgstab_spmv_qdot
                              (CUDA events around its launch on the handle's
                              stream); 0 before the first call */
@@ -409,6 +429,11 @@ int mlbicgstab_spmv_qdot_noalloc(int64_t nrows, int64_t nnz,
  * generator (§5 uses Matlab's randn).
  */
 int mlbicgstab_get_Q(const mlb_handle *h, void *host_out);
+
+/* Row order of the handle's system: new row r is the caller's row
+ * host_out[r] (N entries).  The multicolour order for MLB_PRECOND_ILU0_MC
+ * handles, the identity otherwise.  The paper has no counterpart. */
+int mlbicgstab_get_perm(const mlb_handle *h, int32_t *host_out);
 
 /* Fill `info` for a handle. */
 int mlbicgstab_info(const mlb_handle *h, mlb_info *info);

@@ -24,6 +24,11 @@ struct mlb_handle {
     int n_active = 4;   // shadow vectors the next solve uses (<= n)
     int precond = MLB_PRECOND_NONE;
     void *mdiag = nullptr;   // diagonal of M (Jacobi), device, N values
+    // multicolour ILU(0): the handle holds P A P^T; perm[new] = old row
+    std::vector<int32_t> perm_h;
+    int32_t *perm_d = nullptr;
+    void *pstage = nullptr;   // device staging vector for the reordering
+    int ncolors = 0;
     // ILU(0) factors and level sets (device; see IluHost)
     int64_t *ilu_rp = nullptr;
     int32_t *ilu_ci = nullptr, *ilu_dpos = nullptr;
@@ -214,6 +219,11 @@ void conj_transpose(const mlb_matrix *A, std::vector<int64_t> &rp, std::vector<i
     }
 }
 
+// The handle applies ILU(0) factors (natural or multicolour order).
+bool has_ilu(const mlb_handle *h) {
+    return h->precond == MLB_PRECOND_ILU0 || h->precond == MLB_PRECOND_ILU0_MC;
+}
+
 template <typename T>
 SysView<T> make_view(const mlb_handle *h) {
     SysView<T> v;
@@ -235,7 +245,7 @@ SysView<T> make_view(const mlb_handle *h) {
     v.b = (T *)h->b;
     v.n = h->n_active;
     v.ilu = IluView<T>{};
-    if (h->precond == MLB_PRECOND_ILU0) {
+    if (has_ilu(h)) {
         v.ilu.rp = h->ilu_rp;
         v.ilu.ci = h->ilu_ci;
         v.ilu.lu = (const T *)h->ilu_lu;
@@ -280,7 +290,7 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.b = (T32 *)h->b32;
     v.n = h->n_active;
     v.ilu = IluView<T32>{};
-    if (h->precond == MLB_PRECOND_ILU0) {
+    if (has_ilu(h)) {
         v.ilu.rp = h->ilu_rp;
         v.ilu.ci = h->ilu_ci;
         v.ilu.lu = (const T32 *)h->ilu_lu32;
@@ -346,6 +356,34 @@ bool is_device_ptr(const void *p, int dev) {
     return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
+// Inputs of a solve into the handle's b and x (the caller's row order, or
+// the multicolour order: b_B = P b, x_B = P x), and the solution back.
+int stage_in(mlb_handle *h, const void *b, const void *x, int32_t on_device, cudaStream_t st) {
+    const size_t nb = (size_t)h->N * h->esize;
+    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (h->perm_h.empty()) {
+        MLB_CUDA(cudaMemcpyAsync(h->b, b, nb, in, st));
+        MLB_CUDA(cudaMemcpyAsync(h->x, x, nb, in, st));
+        return MLB_OK;
+    }
+    MLB_CUDA(cudaMemcpyAsync(h->pstage, b, nb, in, st));
+    MLB_CUDA(launch_permute(h->pstage, h->b, h->perm_d, h->N, (int)h->esize, true, st));
+    MLB_CUDA(cudaMemcpyAsync(h->pstage, x, nb, in, st));
+    MLB_CUDA(launch_permute(h->pstage, h->x, h->perm_d, h->N, (int)h->esize, true, st));
+    return MLB_OK;
+}
+int stage_out(mlb_handle *h, void *x, int32_t on_device, cudaStream_t st) {
+    const size_t nb = (size_t)h->N * h->esize;
+    const cudaMemcpyKind outk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (h->perm_h.empty()) {
+        MLB_CUDA(cudaMemcpyAsync(x, h->x, nb, outk, st));
+        return MLB_OK;
+    }
+    MLB_CUDA(launch_permute(h->x, h->pstage, h->perm_d, h->N, (int)h->esize, false, st));
+    MLB_CUDA(cudaMemcpyAsync(x, h->pstage, nb, outk, st));
+    return MLB_OK;
+}
+
 // With a preconditioner the kernels iterate on y = M x (A M^{-1} y = b):
 // before a solve the caller's x_0 becomes y_0 = M x_0, afterwards the
 // result y becomes x = M^{-1} y, on the handle's buffer h->x.  Here for
@@ -404,9 +442,34 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     h->n = o->n;
     h->n_active = o->n;
     h->precond = o->precond;
+    // multicolour ILU(0): the handle holds B = P A P^T (and B^H = P A^H P^T),
+    // solves B y = P b and returns x = P^T y
+    std::vector<int64_t> brp, bhrp;
+    std::vector<int32_t> bci, bhci, iperm;
+    std::vector<char> bval, bhval;
+    mlb_matrix Bm, BHm;
+    if (o->precond == MLB_PRECOND_ILU0_MC) {
+        h->ncolors = mc_order(A, h->perm_h);
+        iperm.assign(A->nrows, 0);
+        for (int64_t r = 0; r < A->nrows; ++r) iperm[h->perm_h[r]] = (int32_t)r;
+        permute_csr(A, h->perm_h, iperm, h->esize, brp, bci, bval);
+        Bm = *A;
+        Bm.row_ptr = brp.data();
+        Bm.col_idx = bci.data();
+        Bm.values = bval.data();
+        A = &Bm;
+        if (AH) {
+            permute_csr(AH, h->perm_h, iperm, h->esize, bhrp, bhci, bhval);
+            BHm = *AH;
+            BHm.row_ptr = bhrp.data();
+            BHm.col_idx = bhci.data();
+            BHm.values = bhval.data();
+            AH = &BHm;
+        }
+    }
     // ILU(0): factors and level sets on the host (the handle keeps A itself)
     IluHost ih;
-    if (o->precond == MLB_PRECOND_ILU0) {
+    if (has_ilu(h)) {
         const int rci = ilu0_build(A, ih);
         if (rci) return rci;
     }
@@ -484,7 +547,7 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         if ((rc = dev_alloc(h, &h->mdiag, vb))) return rc;
         MLB_CUDA(cudaMemcpy(h->mdiag, jd.data(), (size_t)h->N * es, cudaMemcpyHostToDevice));
     }
-    if (h->precond == MLB_PRECOND_ILU0) {
+    if (has_ilu(h)) {
         const int64_t N = h->N;
         h->ilu_nnz = ih.nnz;
         h->ilu_nlev_l = ih.nlev_l;
@@ -524,11 +587,24 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         MLB_CUDA(cudaMemcpy(h->ilu_udiag, ih.udiag.data(), (size_t)N * es, cudaMemcpyHostToDevice));
     }
 
-    // shadow vectors
-    if (o->Q) {
+    // reordering (multicolour ILU(0)): the permutation and a staging vector
+    if (!h->perm_h.empty()) {
+        if ((rc = dev_alloc_t(h, &h->perm_d, (size_t)h->N * 4))) return rc;
+        if ((rc = dev_alloc(h, &h->pstage, vb))) return rc;
+        MLB_CUDA(cudaMemcpy(h->perm_d, h->perm_h.data(), (size_t)h->N * 4, cudaMemcpyHostToDevice));
+    }
+    // shadow vectors (given and drawn in the original row order)
+    if (o->Q && !h->perm_h.empty()) {
+        std::vector<char> qp((size_t)h->N * n * es);
+        const char *qs = (const char *)o->Q;
+        for (int m = 0; m < n; ++m)
+            for (int64_t r = 0; r < h->N; ++r)
+                memcpy(&qp[((size_t)m * h->N + r) * es], qs + ((size_t)m * h->N + h->perm_h[r]) * es, es);
+        MLB_CUDA(cudaMemcpy2D(h->Q, ld * es, qp.data(), h->N * es, h->N * es, n, cudaMemcpyHostToDevice));
+    } else if (o->Q) {
         MLB_CUDA(cudaMemcpy2DAsync(h->Q, ld * es, o->Q, h->N * es, h->N * es, n, cudaMemcpyHostToDevice, st));
     } else {
-        MLB_CUDA(launch_qgen(h->Q, cplx ? 1 : 0, h->N, ld, n, o->q_seed, st));
+        MLB_CUDA(launch_qgen(h->Q, cplx ? 1 : 0, h->N, ld, n, o->q_seed, st, h->perm_d));
     }
 
     // F = A^H Q(:, 0:n-2) (Algorithm 4.1, step 2)
@@ -581,7 +657,7 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         cudaFree(dav);
         if (e != cudaSuccess) return MLB_ERR_CUDA;
         // ILU(0): F = M^{-H} (A^H Q), column by column on the host
-        if (h->precond == MLB_PRECOND_ILU0) {
+        if (has_ilu(h)) {
             std::vector<char> col((size_t)h->N * es);
             for (int m = 0; m < n - 1; ++m) {
                 char *dcol = (char *)h->F + (size_t)m * ld * es;
@@ -617,7 +693,7 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         if (n > 1)
             MLB_CUDA(launch_narrow((const double *)h->F, (float *)h->F32, ld * (int64_t)(n - 1) * (int64_t)es / 8,
                                    st));
-        if (h->precond == MLB_PRECOND_ILU0) {
+        if (has_ilu(h)) {
             const int64_t N = h->N;
             const size_t ne = (size_t)kIluEll * N;
             if ((rc = dev_alloc(h, &h->ilu_lu32, (size_t)h->ilu_nnz * es / 2))) return rc;
@@ -729,7 +805,8 @@ int mlbicgstab_create(mlb_handle **out, const mlb_matrix *A, const mlb_matrix *A
     if (o.kappa < 0.0 || o.max_outer < 0 || o.timeout_ns <= 0) return MLB_ERR_ARG;
     if (o.precision == MLB_PREC_FP32_REFINED && (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.inner_maxit < 1))
         return MLB_ERR_ARG;
-    if ((o.precond != MLB_PRECOND_NONE && o.precond != MLB_PRECOND_JACOBI && o.precond != MLB_PRECOND_ILU0) ||
+    if ((o.precond != MLB_PRECOND_NONE && o.precond != MLB_PRECOND_JACOBI && o.precond != MLB_PRECOND_ILU0 &&
+         o.precond != MLB_PRECOND_ILU0_MC) ||
         o.reserved0 != 0)
         return MLB_ERR_ARG;
     int rc = validate_csr(A);
@@ -772,6 +849,7 @@ int mlbicgstab_info(const mlb_handle *h, mlb_info *info) {
     info->n = h->n;
     info->n_active = h->n_active;
     info->precond = h->precond;
+    info->ilu_levels = has_ilu(h) ? h->ilu_nlev_l : 0;
     info->dtype = h->dtype;
     info->precision = h->precision;
     info->grid = h->grid;
@@ -788,6 +866,22 @@ int mlbicgstab_get_Q(const mlb_handle *h, void *host_out) {
     MLB_CUDA(cudaMemcpy2DAsync(host_out, h->N * h->esize, h->Q, h->ld * h->esize, h->N * h->esize, h->n,
                                cudaMemcpyDeviceToHost, h->stream));
     MLB_CUDA(cudaStreamSynchronize(h->stream));
+    if (!h->perm_h.empty()) {   // back to the original row order
+        const size_t es = h->esize;
+        std::vector<char> tmp((size_t)h->N * es);
+        char *q = (char *)host_out;
+        for (int m = 0; m < h->n; ++m) {
+            char *col = q + (size_t)m * h->N * es;
+            memcpy(tmp.data(), col, tmp.size());
+            for (int64_t r = 0; r < h->N; ++r) memcpy(col + (size_t)h->perm_h[r] * es, &tmp[(size_t)r * es], es);
+        }
+    }
+    return MLB_OK;
+}
+
+int mlbicgstab_get_perm(const mlb_handle *h, int32_t *host_out) {
+    if (!h || !host_out) return MLB_ERR_ARG;
+    for (int64_t r = 0; r < h->N; ++r) host_out[r] = h->perm_h.empty() ? (int32_t)r : h->perm_h[r];
     return MLB_OK;
 }
 
@@ -812,8 +906,7 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
         }
         h->err_cap = hist_cap;
     }
-    MLB_CUDA(cudaMemcpyAsync(h->b, b, nb, in, st));
-    MLB_CUDA(cudaMemcpyAsync(h->x, x, nb, in, st));
+    if (int rcs = stage_in(h, b, x, on_device, st)) return rcs;
     if (int rcm = map_solution(h, false)) return rcm;   // y_0 = M x_0
     MLB_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(BarrierState), st));
     SolveCtl ctl;
@@ -847,7 +940,7 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     }
     MLB_CUDA(cudaEventRecord(h->ev1, st));
     if (int rcm = map_solution(h, true)) return rcm;    // x = M^{-1} y
-    MLB_CUDA(cudaMemcpyAsync(x, h->x, nb, outk, st));
+    if (int rcs = stage_out(h, x, on_device, st)) return rcs;
     MLB_CUDA(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
     MLB_CUDA(cudaStreamSynchronize(st));
     const DevResult &d = *h->hres;
@@ -960,9 +1053,7 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
     const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind outk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     for (int s = 0; s < count; ++s) {
-        const size_t nb = (size_t)hs[s]->N * hs[s]->esize;
-        MLB_CUDA(cudaMemcpyAsync(hs[s]->b, b[s], nb, in, st));
-        MLB_CUDA(cudaMemcpyAsync(hs[s]->x, x[s], nb, in, st));
+        if (int rcs = stage_in(hs[s], b[s], x[s], on_device, st)) return rcs;
         if (int rcm = map_solution(hs[s], false, st)) return rcm;
     }
     MLB_CUDA(cudaMemcpyAsync(dws, hws, off_res, cudaMemcpyHostToDevice, st));
@@ -973,7 +1064,7 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
     if (bps < 1) return MLB_ERR_CUDA;
     const int grid = std::min(count, sms * bps);
     bool any_ilu = false;
-    for (int q = 0; q < count; ++q) any_ilu = any_ilu || hs[q]->precond == MLB_PRECOND_ILU0;
+    for (int q = 0; q < count; ++q) any_ilu = any_ilu || has_ilu(hs[q]);
     const int *dorder = (const int *)(dws + off_order);
     unsigned *queue = (unsigned *)dws;
     const void *ditems = dws + off_items;
@@ -997,9 +1088,8 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
     }
     MLB_CUDA(cudaEventRecord(h0->ev1, st));
     for (int s = 0; s < count; ++s) {
-        const size_t nb = (size_t)hs[s]->N * hs[s]->esize;
         if (int rcm = map_solution(hs[s], true, st)) return rcm;
-        MLB_CUDA(cudaMemcpyAsync(x[s], hs[s]->x, nb, outk, st));
+        if (int rcs = stage_out(hs[s], x[s], on_device, st)) return rcs;
     }
     DevResult *hres = (DevResult *)(hws + off_res);
     MLB_CUDA(cudaMemcpyAsync(hres, dres, (size_t)count * sizeof(DevResult), cudaMemcpyDeviceToHost, st));

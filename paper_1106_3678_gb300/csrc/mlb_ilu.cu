@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstring>
 #include <utility>
 
 #include "mlb_internal.h"
@@ -160,6 +161,65 @@ void apply_h_t(const IluHost &f, V *v) {
 }
 
 }  // namespace
+
+int mc_order(const mlb_matrix *A, std::vector<int32_t> &perm) {
+    const int64_t N = A->nrows;
+    // transposed pattern (who lists column i), for the symmetrised graph
+    std::vector<int64_t> tp(N + 1, 0);
+    for (int64_t k = 0; k < A->nnz; ++k) tp[A->col_idx[k] + 1]++;
+    for (int64_t r = 0; r < N; ++r) tp[r + 1] += tp[r];
+    std::vector<int32_t> tr(A->nnz);
+    {
+        std::vector<int64_t> next(tp.begin(), tp.end() - 1);
+        for (int64_t r = 0; r < N; ++r)
+            for (int64_t k = A->row_ptr[r]; k < A->row_ptr[r + 1]; ++k) tr[next[A->col_idx[k]]++] = (int32_t)r;
+    }
+    std::vector<int32_t> color(N, -1);
+    std::vector<int64_t> seen;   // seen[c] == i: colour c is taken by a neighbour of row i
+    int ncolors = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        auto mark = [&](int64_t j) {
+            if (j != i && color[j] >= 0) {
+                if ((size_t)color[j] >= seen.size()) seen.resize(color[j] + 1, -1);
+                seen[color[j]] = i;
+            }
+        };
+        for (int64_t k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k) mark(A->col_idx[k]);
+        for (int64_t k = tp[i]; k < tp[i + 1]; ++k) mark(tr[k]);
+        int c = 0;
+        while ((size_t)c < seen.size() && seen[c] == i) ++c;
+        color[i] = c;
+        ncolors = std::max(ncolors, c + 1);
+    }
+    // colour by colour, natural order within a colour (a stable counting sort)
+    std::vector<int64_t> start(ncolors + 1, 0);
+    for (int64_t i = 0; i < N; ++i) start[color[i] + 1]++;
+    for (int c = 0; c < ncolors; ++c) start[c + 1] += start[c];
+    perm.assign(N, 0);
+    for (int64_t i = 0; i < N; ++i) perm[start[color[i]]++] = (int32_t)i;
+    return ncolors;
+}
+
+void permute_csr(const mlb_matrix *A, const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm,
+                 size_t es, std::vector<int64_t> &rp, std::vector<int32_t> &ci, std::vector<char> &val) {
+    const int64_t N = A->nrows;
+    rp.assign(N + 1, 0);
+    for (int64_t r = 0; r < N; ++r) {
+        const int64_t o = perm[r];
+        rp[r + 1] = rp[r] + (A->row_ptr[o + 1] - A->row_ptr[o]);
+    }
+    ci.assign(A->nnz, 0);
+    val.assign((size_t)A->nnz * es, 0);
+    const char *av = (const char *)A->values;
+    for (int64_t r = 0; r < N; ++r) {
+        const int64_t o = perm[r];
+        int64_t d = rp[r];
+        for (int64_t k = A->row_ptr[o]; k < A->row_ptr[o + 1]; ++k, ++d) {
+            ci[d] = iperm[A->col_idx[k]];
+            memcpy(&val[(size_t)d * es], av + (size_t)k * es, es);
+        }
+    }
+}
 
 int ilu0_build(const mlb_matrix *A, IluHost &out) {
     return A->dtype == MLB_C128 ? build_t<std::complex<double>>(A, out) : build_t<double>(A, out);

@@ -62,9 +62,11 @@ template <typename T32, typename T64>
 int batch_refine_blocks_per_sm();
 
 // Q (ld x n, column-major) from the counter-based SplitMix64 + Box-Muller
-// generator; rows N..ld-1 are left untouched (zero).
+// generator; rows N..ld-1 are left untouched (zero).  With `perm`, row r
+// receives the entries of original row perm[r] (Q of a multicolour-ordered
+// handle is the Q of the original row order, permuted).
 cudaError_t launch_qgen(void *Q, int is_complex, int64_t N, int64_t ld, int n,
-                        uint64_t seed, cudaStream_t st);
+                        uint64_t seed, cudaStream_t st, const int32_t *perm = nullptr);
 
 // F(:, s) = AH Q(:, s) for s < m, AH in CSR (values already conjugated).
 template <typename T>
@@ -122,6 +124,21 @@ struct IluHost {
 int ilu0_build(const mlb_matrix *A, IluHost &out);
 // v <- M^{-H} v for the N values at v (M = L U from `f`).
 void ilu0_apply_h(const IluHost &f, bool cplx, void *v);
+// Multicolour order of A (the multicolour ILU(0) preconditioner): greedy
+// colouring of the symmetrised adjacency graph in natural order (each row
+// takes the smallest colour no neighbour coloured before it has), rows
+// then listed colour by colour, natural order within a colour.
+// perm[new] = old.  Returns the number of colours.
+int mc_order(const mlb_matrix *A, std::vector<int32_t> &perm);
+// B = P A P^T: row r of B is row perm[r] of A with column c renamed
+// iperm[c] (entries of a row in A's order); es = bytes per value.
+void permute_csr(const mlb_matrix *A, const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm,
+                 size_t es, std::vector<int64_t> &rp, std::vector<int32_t> &ci, std::vector<char> &val);
+// Gather (to_perm: dst[r] = src[perm[r]]) or scatter (dst[perm[r]] =
+// src[r]) of N values of `es` bytes between the original and the
+// multicolour row order.
+cudaError_t launch_permute(const void *src, void *dst, const int32_t *perm, int64_t N, int es, bool to_perm,
+                           cudaStream_t st);
 
 // Failure-detection self-test of the grid barrier (see the C ABI).
 cudaError_t launch_barrier_selftest(int grid, BarrierState *bs,

@@ -93,11 +93,15 @@ __device__ __forceinline__ double normal_at(uint64_t seed, uint64_t t) {
     return rad * cos(ang);
 }
 
-__global__ void qgen_kernel(double *Q, int is_complex, int64_t N, int64_t ld, int n, uint64_t seed) {
+// Entry e = col * N + orow of the original order (orow = perm[row] for a
+// multicolour-ordered handle, else row) lands at (row, col).
+__global__ void qgen_kernel(double *Q, int is_complex, int64_t N, int64_t ld, int n, uint64_t seed,
+                            const int32_t *perm) {
     const int64_t total = N * (int64_t)n;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e % N, col = e / N;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t % N, col = t / N;
+        const int64_t e = col * N + (perm ? (int64_t)perm[row] : row);
         if (is_complex) {
             double *q = Q + 2 * (col * ld + row);
             q[0] = normal_at(seed, 2ull * e);
@@ -109,12 +113,33 @@ __global__ void qgen_kernel(double *Q, int is_complex, int64_t N, int64_t ld, in
 }
 
 cudaError_t launch_qgen(void *Q, int is_complex, int64_t N, int64_t ld, int n, uint64_t seed,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int32_t *perm) {
     int64_t total = N * (int64_t)n;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 65535 * 8) blocks = 65535 * 8;
     if (blocks < 1) blocks = 1;
-    qgen_kernel<<<blocks, 256, 0, st>>>((double *)Q, is_complex, N, ld, n, seed);
+    qgen_kernel<<<blocks, 256, 0, st>>>((double *)Q, is_complex, N, ld, n, seed, perm);
+    return cudaGetLastError();
+}
+
+// Row permutation of a vector (16-byte or 8-byte values as double pairs
+// or doubles): gather dst[r] = src[perm[r]] or scatter dst[perm[r]] = src[r].
+template <typename V>
+__global__ void permute_kernel(const V *src, V *dst, const int32_t *perm, int64_t N, int to_perm) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+        if (to_perm) dst[r] = src[perm[r]];
+        else dst[perm[r]] = src[r];
+    }
+}
+
+cudaError_t launch_permute(const void *src, void *dst, const int32_t *perm, int64_t N, int es, bool to_perm,
+                           cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
+    if (es == 16)
+        permute_kernel<double2><<<grid, 256, 0, st>>>((const double2 *)src, (double2 *)dst, perm, N, to_perm ? 1 : 0);
+    else
+        permute_kernel<double><<<grid, 256, 0, st>>>((const double *)src, (double *)dst, perm, N, to_perm ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmlbicgstab.so")
 MLB_OK, MLB_ERR_ARG, MLB_ERR_CUDA, MLB_ERR_OOM, MLB_ERR_TIMEOUT, MLB_ERR_UNSUPPORTED = range(6)
 MLB_F64, MLB_F32, MLB_C128, MLB_C64 = 0, 1, 2, 3
 MLB_PREC_FP64, MLB_PREC_FP32_REFINED = 0, 1
-MLB_PRECOND_NONE, MLB_PRECOND_JACOBI, MLB_PRECOND_ILU0 = 0, 1, 2
+MLB_PRECOND_NONE, MLB_PRECOND_JACOBI, MLB_PRECOND_ILU0, MLB_PRECOND_ILU0_MC = 0, 1, 2, 3
 
 # Every symbol the header declares (checked against the header by a test).
 EXPORTS = (
@@ -29,7 +29,7 @@ EXPORTS = (
     "mlbicgstab_info", "mlbicgstab_destroy", "mlbicgstab_strerror",
     "mlbicgstab_selftest_barrier_timeout", "mlbicgstab_spmv_qdot_noalloc",
     "mlbicgstab_set_n", "mlbicgstab_next_n", "mlbicgstab_solve_sequence",
-    "mlbicgstab_autotune", "mlbicgstab_spmv_qdot_async",
+    "mlbicgstab_autotune", "mlbicgstab_spmv_qdot_async", "mlbicgstab_get_perm",
 )
 
 
@@ -71,7 +71,7 @@ class mlb_info(C.Structure):
                 ("grid", C.c_int32), ("block", C.c_int32),
                 ("precond", C.c_int32), ("nnz_padded", C.c_int64),
                 ("device_bytes", C.c_int64), ("n_active", C.c_int32),
-                ("reserved1", C.c_int32), ("qd_kernel_ms", C.c_double)]
+                ("ilu_levels", C.c_int32), ("qd_kernel_ms", C.c_double)]
 
 
 class mlb_tune_result(C.Structure):
@@ -118,6 +118,8 @@ def load(path: str | None = None):
                                            C.POINTER(mlb_result)]
     lib.mlbicgstab_spmv_qdot.restype = C.c_int
     lib.mlbicgstab_spmv_qdot.argtypes = [P, P, P, P]
+    lib.mlbicgstab_get_perm.restype = C.c_int
+    lib.mlbicgstab_get_perm.argtypes = [P, P]
     lib.mlbicgstab_spmv_qdot_async.restype = C.c_int
     lib.mlbicgstab_spmv_qdot_async.argtypes = [P, C.c_int32, P, P, P]
     lib.mlbicgstab_get_Q.restype = C.c_int
@@ -236,8 +238,9 @@ def mlbicgstab_create(A, AH=None, n: int = 4, q_seed: int = 0, Q=None,
                       precond: int = MLB_PRECOND_NONE) -> Handle:
     """Create a solver for CSR matrix ``A`` (see mlbicgstab_create in C).
     ``stream``: a torch.cuda.Stream, a raw cudaStream_t integer, or None.
-    ``precond``: MLB_PRECOND_NONE, MLB_PRECOND_JACOBI (M = diag(A)) or
-    MLB_PRECOND_ILU0 (M = the ILU(0) factors of A)."""
+    ``precond``: MLB_PRECOND_NONE, MLB_PRECOND_JACOBI (M = diag(A)),
+    MLB_PRECOND_ILU0 (M = the ILU(0) factors of A) or MLB_PRECOND_ILU0_MC
+    (the ILU(0) factors of A in a multicolour order)."""
     lib = load()
     M = Matrix(A)
     MH = Matrix(AH) if AH is not None else None
@@ -408,6 +411,13 @@ def mlbicgstab_spmv_qdot_noalloc(row_ptr, col_idx, values, x, Q, y, d,
 def mlbicgstab_get_Q(h: Handle) -> np.ndarray:
     out = np.empty((h.N, h.n), dtype=h.dtype, order="F")
     _check(load().mlbicgstab_get_Q(h.ptr, out.ctypes.data), "mlbicgstab_get_Q")
+    return out
+
+
+def mlbicgstab_get_perm(h: Handle) -> np.ndarray:
+    """Row order of the handle's system (new row r = caller's row out[r])."""
+    out = np.empty(h.N, dtype=np.int32)
+    _check(load().mlbicgstab_get_perm(h.ptr, out.ctypes.data), "mlbicgstab_get_perm")
     return out
 
 

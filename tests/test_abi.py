@@ -103,7 +103,7 @@ def test_invalid_arguments_are_rejected_before_gpu_work(lib):
     assert _raw_create(lib, A, kappa=-1.0)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, precision=7)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, precond=5)[0] == M.MLB_ERR_ARG
-    assert _raw_create(lib, A, precond=3)[0] == M.MLB_ERR_ARG
+    assert _raw_create(lib, A, precond=4)[0] == M.MLB_ERR_ARG
     # refined mode: the reliable-update factor lies in (0, 1), the inner
     # iteration cap is positive
     assert _raw_create(lib, A, precision=1, inner_tol=0.0)[0] == M.MLB_ERR_ARG
