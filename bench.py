@@ -162,8 +162,9 @@ def _make_variant_inputs(wl):
         A = W.helmholtz3d_c()
         return [(A, W.conj_transpose(A), W.row_sums(A))]
     if kind == "reservoir":
-        A = W.bsr3_to_csr(W.reservoir_bsr3())
-        return [(A, None, W.row_sums(A))]
+        # passed in BSR(3) storage (3x3 blocks, one column index per block)
+        B = W.reservoir_bsr3()
+        return [(B, None, W.row_sums(W.bsr3_to_csr(B)))]
     if kind == "batch":
         return [(A, None, W.row_sums(A)) for A, _ in W.batch_cd(512, seed=5)]
     if kind == "tune":
@@ -186,7 +187,7 @@ def _variant_desc(name, wl, systems):
                 f"(N={N:,}, nnz={nnz:,}), n in {list(wl['ns'])}, x U[-1,1], fp64, {wl['calls']} calls each")
     what = {"cd3d": "3-D log-normal convection-diffusion 128^3",
             "helmholtz": "complex damped shifted Laplacian 256x256x64, A^H as separate CSR",
-            "reservoir": "3x3-block reservoir system 64x64x32 cells",
+            "reservoir": "3x3-block reservoir system 64x64x32 cells, BSR(3) input",
             "batch": "512 2-D/3-D convection-diffusion systems, N ~ logU[1e3,1e5], one launch",
             "tune": f"2-D 5-point convection-diffusion {wl.get('m', 0)}^2, default launch configuration vs autotuned",
             "sequence": (f"sequence of {wl.get('count', 0)} right-hand sides U[-1,1] (seeds 10..) on the 3-D "

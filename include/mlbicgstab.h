@@ -77,16 +77,28 @@ extern "C" {
                                    otherwise flag 1 with the solution of
                                    smallest true residual found. */
 
-/* A sparse matrix in host memory (CSR).  The library copies it; the
- * caller's arrays may be freed after mlbicgstab_create returns. */
+/* A sparse matrix in host memory: CSR, or BSR with 3x3 blocks.  The
+ * library copies it; the caller's arrays may be freed after
+ * mlbicgstab_create returns.
+ *   block = 0 or 1: CSR (row_ptr over the nrows rows, col_idx columns,
+ *   one value per entry).
+ *   block = 3: BSR(3), the storage of systems with 3 unknowns per cell
+ *   (e.g. reservoir models): nrows (a multiple of 3) scalar rows,
+ *   row_ptr over the nrows/3 block rows, nnz blocks, col_idx block
+ *   columns in [0, nrows/3), values 9 per block (row-major 3x3).  The
+ *   product of real-valued matrices then streams one column index per 3
+ *   values (a scalar CSR whose rows come in such triplets is stored the
+ *   same way).  Handles of such matrices are not accepted by
+ *   mlbicgstab_solve_batch or the fused-product entry points
+ *   (MLB_ERR_UNSUPPORTED). */
 typedef struct {
-    int64_t nrows;          /* N (square matrices only) */
-    int64_t nnz;            /* number of stored entries */
-    const int64_t *row_ptr; /* nrows + 1 entries */
-    const int32_t *col_idx; /* nnz entries */
-    const void *values;     /* nnz values of type `dtype` */
+    int64_t nrows;          /* N scalar rows (square matrices only) */
+    int64_t nnz;            /* stored entries (CSR) or blocks (BSR) */
+    const int64_t *row_ptr; /* nrows + 1 (CSR) or nrows/3 + 1 (BSR) */
+    const int32_t *col_idx; /* nnz (block) column indices */
+    const void *values;     /* nnz (CSR) or 9 nnz (BSR) values of `dtype` */
     int32_t dtype;          /* MLB_F64 or MLB_C128 */
-    int32_t reserved;       /* must be 0 */
+    int32_t block;          /* 0 or 1: CSR; 3: BSR with 3x3 blocks */
 } mlb_matrix;
 
 /* Options for mlbicgstab_create.  Zero-initialise, then set what you need;
@@ -217,6 +229,10 @@ typedef struct {
     double qd_kernel_ms;  /* device time of the last mlbicgstab_spmv_qdot
                              (CUDA events around its launch on the handle's
                              stream); 0 before the first call */
+    int32_t entry_values; /* values per stored matrix entry of the
+                             products: 1, or 3 (3x3-block rows with one
+                             column index per three values) */
+    int32_t reserved2;
 } mlb_info;
 
 /* Result of mlbicgstab_autotune. */

@@ -45,6 +45,7 @@ struct mlb_handle {
     int precision = MLB_PREC_FP64;
     int64_t N = 0, ld = 0, nnz = 0, nnz_pad = 0, nslices = 0;
     int64_t maxw = 0;   // widest SELL-32 slice (entries per row)
+    int ew = 1;         // values per stored entry: 1, or 3 (3x3-block rows, one column per three values)
     int device = 0;
     cudaStream_t stream = nullptr;
     int grid = 1;
@@ -127,14 +128,57 @@ int validate_csr(const mlb_matrix *A) {
     if (!A || A->nrows <= 0 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->values)))
         return MLB_ERR_ARG;
     if (A->dtype != MLB_F64 && A->dtype != MLB_C128) return MLB_ERR_ARG;
-    if (A->reserved != 0) return MLB_ERR_ARG;
+    if (A->block != 0 && A->block != 1 && A->block != 3) return MLB_ERR_ARG;
     if (A->nrows > (int64_t)INT32_MAX - 1024) return MLB_ERR_ARG;
-    if (A->row_ptr[0] != 0 || A->row_ptr[A->nrows] != A->nnz) return MLB_ERR_ARG;
-    for (int64_t r = 0; r < A->nrows; ++r)
+    const int64_t bs = A->block == 3 ? 3 : 1;
+    if (A->nrows % bs != 0) return MLB_ERR_ARG;
+    const int64_t nb = A->nrows / bs;   // (block) rows of row_ptr
+    if (A->row_ptr[0] != 0 || A->row_ptr[nb] != A->nnz) return MLB_ERR_ARG;
+    for (int64_t r = 0; r < nb; ++r)
         if (A->row_ptr[r + 1] < A->row_ptr[r]) return MLB_ERR_ARG;
     for (int64_t k = 0; k < A->nnz; ++k)
-        if (A->col_idx[k] < 0 || (int64_t)A->col_idx[k] >= A->nrows) return MLB_ERR_ARG;
+        if (A->col_idx[k] < 0 || (int64_t)A->col_idx[k] >= nb) return MLB_ERR_ARG;
     return MLB_OK;
+}
+
+// BSR with 3x3 blocks (block = 3) as scalar CSR: row 3R + a lists, block
+// by block in the given order, the three values of row a of each block
+// with columns 3C, 3C+1, 3C+2.
+void bsr3_expand(const mlb_matrix *A, size_t es, std::vector<int64_t> &rp, std::vector<int32_t> &ci,
+                 std::vector<char> &val) {
+    const int64_t nb = A->nrows / 3;
+    rp.assign(A->nrows + 1, 0);
+    for (int64_t R = 0; R < nb; ++R)
+        for (int a = 0; a < 3; ++a)
+            rp[3 * R + a + 1] = rp[3 * R + a] + 3 * (A->row_ptr[R + 1] - A->row_ptr[R]);
+    ci.assign(rp[A->nrows], 0);
+    val.assign((size_t)rp[A->nrows] * es, 0);
+    const char *av = (const char *)A->values;
+    for (int64_t R = 0; R < nb; ++R)
+        for (int a = 0; a < 3; ++a) {
+            int64_t d = rp[3 * R + a];
+            for (int64_t k = A->row_ptr[R]; k < A->row_ptr[R + 1]; ++k)
+                for (int j = 0; j < 3; ++j, ++d) {
+                    ci[d] = 3 * A->col_idx[k] + j;
+                    memcpy(&val[(size_t)d * es], av + ((size_t)k * 9 + a * 3 + j) * es, es);
+                }
+        }
+}
+
+// Every row's entries come in groups of three consecutive columns 3C,
+// 3C+1, 3C+2 (a matrix of 3x3 blocks, stored row by row): the products
+// can then keep one column index per three values.
+bool has_triplets(const mlb_matrix *A) {
+    if (A->nrows % 3 != 0) return false;
+    for (int64_t r = 0; r < A->nrows; ++r) {
+        const int64_t k0 = A->row_ptr[r], k1 = A->row_ptr[r + 1];
+        if ((k1 - k0) % 3 != 0) return false;
+        for (int64_t k = k0; k < k1; k += 3)
+            if (A->col_idx[k] % 3 != 0 || A->col_idx[k + 1] != A->col_idx[k] + 1 ||
+                A->col_idx[k + 2] != A->col_idx[k] + 2)
+                return false;
+    }
+    return true;
 }
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
@@ -142,8 +186,12 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 // CSR -> SELL-32 (slices of 32 consecutive rows, natural row order, entry k
 // of lane l at slice_ptr[s] + 32k + l; padding entries have value 0 and
 // column = the row itself, clamped to N-1).
+// ew = 3 (a matrix with has_triplets): each stored entry is three values
+// of one row of a 3x3 block and the block's first column; entry k of lane
+// l holds its values at 3 (slice_ptr[s] + 32k + l) .. + 2.  Padding entries
+// have value(s) 0 and a column whose entries (c .. c + ew - 1) exist.
 int64_t csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp, std::vector<int32_t> &col,
-                      std::vector<char> &val, size_t es) {
+                      std::vector<char> &val, size_t es, int ew) {
     const int64_t N = A->nrows, ns = ld / 32;
     sp.assign(ns + 1, 0);
     int64_t maxw = 0;
@@ -151,28 +199,29 @@ int64_t csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp,
         int64_t w = 0;
         for (int64_t l = 0; l < 32; ++l) {
             int64_t row = s * 32 + l;
-            if (row < N) w = std::max(w, A->row_ptr[row + 1] - A->row_ptr[row]);
+            if (row < N) w = std::max(w, (A->row_ptr[row + 1] - A->row_ptr[row]) / ew);
         }
         sp[s + 1] = sp[s] + 32 * w;
         maxw = std::max(maxw, w);
     }
     const int64_t tot = sp[ns];
     col.assign(tot, 0);
-    val.assign(tot * es, 0);
+    val.assign(tot * es * ew, 0);
     const char *av = (const char *)A->values;
     for (int64_t s = 0; s < ns; ++s) {
         const int64_t w = (sp[s + 1] - sp[s]) / 32;
         for (int64_t l = 0; l < 32; ++l) {
             const int64_t row = s * 32 + l;
-            const int64_t len = row < N ? A->row_ptr[row + 1] - A->row_ptr[row] : 0;
+            const int64_t len = row < N ? (A->row_ptr[row + 1] - A->row_ptr[row]) / ew : 0;
             for (int64_t k = 0; k < w; ++k) {
                 const int64_t dst = sp[s] + 32 * k + l;
                 if (k < len) {
-                    const int64_t src = A->row_ptr[row] + k;
+                    const int64_t src = A->row_ptr[row] + ew * k;
                     col[dst] = A->col_idx[src];
-                    memcpy(&val[dst * es], av + src * es, es);
+                    memcpy(&val[dst * es * ew], av + src * es, es * ew);
                 } else {
-                    col[dst] = (int32_t)std::min<int64_t>(row, N - 1);
+                    const int64_t r = std::min<int64_t>(row, N - 1);
+                    col[dst] = (int32_t)(ew == 3 ? r - r % 3 : r);
                 }
             }
         }
@@ -180,18 +229,19 @@ int64_t csr_to_sell32(const mlb_matrix *A, int64_t ld, std::vector<int64_t> &sp,
     return maxw;
 }
 
-// Slices per SpMV tile so that the widest tile (values of `vbytes` plus
-// 4-byte column indices) fits one shared-memory stage; 0 when one slice
-// alone does not fit (the SpMV then reads the matrix directly).
-int slices_per_tile(int64_t maxw, size_t vbytes, int nepi) {
-    const int64_t per_slice = maxw * 32 * (int64_t)(vbytes + 4) + (int64_t)nepi * 32 * (int64_t)vbytes;
+// Slices per SpMV tile so that the widest tile (entries of `ew` values of
+// `vbytes` plus a 4-byte column index, and `nepi` epilogue vectors) fits
+// one shared-memory stage; 0 when one slice alone does not fit (the SpMV
+// then reads the matrix directly).
+int slices_per_tile(int64_t maxw, size_t vbytes, int nepi, int ew = 1) {
+    const int64_t per_slice = maxw * 32 * (int64_t)(ew * vbytes + 4) + (int64_t)nepi * 32 * (int64_t)vbytes;
     if (per_slice <= 0) return kConsumerWarps;
     int64_t spt = kStageBytes / per_slice;
     if (spt > kConsumerWarps) spt = kConsumerWarps;
     return (int)spt;
 }
-void set_spt(int (&spt)[3], int64_t maxw, size_t vbytes, int cap) {
-    for (int e = 0; e < 3; ++e) spt[e] = std::min(slices_per_tile(maxw, vbytes, e), cap);
+void set_spt(int (&spt)[3], int64_t maxw, size_t vbytes, int cap, int ew) {
+    for (int e = 0; e < 3; ++e) spt[e] = std::min(slices_per_tile(maxw, vbytes, e, ew), cap);
 }
 
 // A^H in CSR by a stable counting sort over columns (values conjugated for
@@ -234,7 +284,8 @@ SysView<T> make_view(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T *)h->sval;
-    set_spt(v.spt, h->maxw, sizeof(T), h->spt_cap);
+    set_spt(v.spt, h->maxw, sizeof(T), h->spt_cap, h->ew);
+    v.ew = h->ew;
     v.Q = (const T *)h->Q;
     v.F = (const T *)h->F;
     v.G = (T *)h->G;
@@ -279,7 +330,8 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T32 *)h->sval32;
-    set_spt(v.spt, h->maxw, sizeof(T32), h->spt_cap);
+    set_spt(v.spt, h->maxw, sizeof(T32), h->spt_cap, h->ew);
+    v.ew = h->ew;
     v.Q = (const T32 *)h->Q32;
     v.F = (const T32 *)h->F32;
     v.G = (T32 *)h->G32;
@@ -324,7 +376,7 @@ RefView<T64> make_ref_view(const mlb_handle *h) {
     v.slice_ptr = h->slice_ptr;
     v.scol = h->scol;
     v.sval = (const T64 *)h->sval;
-    set_spt(v.spt, h->maxw, sizeof(T64), h->spt_cap);
+    set_spt(v.spt, h->maxw, sizeof(T64), h->spt_cap, h->ew);
     v.x = (T64 *)h->x;
     v.b = (const T64 *)h->b;
     v.r = (T64 *)h->r;
@@ -442,6 +494,32 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     h->n = o->n;
     h->n_active = o->n;
     h->precond = o->precond;
+    // BSR(3) input: the host-side steps (factors, orderings, A^H) work on
+    // the scalar CSR; the products keep one column per block row segment
+    std::vector<int64_t> xrp, xhrp;
+    std::vector<int32_t> xci, xhci;
+    std::vector<char> xval, xhval;
+    mlb_matrix Xm, XHm;
+    if (A->block == 3) {
+        bsr3_expand(A, h->esize, xrp, xci, xval);
+        Xm = *A;
+        Xm.block = 1;
+        Xm.nnz = xrp.back();
+        Xm.row_ptr = xrp.data();
+        Xm.col_idx = xci.data();
+        Xm.values = xval.data();
+        A = &Xm;
+    }
+    if (AH && AH->block == 3) {
+        bsr3_expand(AH, h->esize, xhrp, xhci, xhval);
+        XHm = *AH;
+        XHm.block = 1;
+        XHm.nnz = xhrp.back();
+        XHm.row_ptr = xhrp.data();
+        XHm.col_idx = xhci.data();
+        XHm.values = xhval.data();
+        AH = &XHm;
+    }
     // multicolour ILU(0): the handle holds B = P A P^T (and B^H = P A^H P^T),
     // solves B y = P b and returns x = P^T y
     std::vector<int64_t> brp, bhrp;
@@ -511,7 +589,8 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         std::vector<int64_t> sp;
         std::vector<int32_t> col;
         std::vector<char> val;
-        h->maxw = csr_to_sell32(A, ld, sp, col, val, es);
+        h->ew = (!cplx && has_triplets(A)) ? 3 : 1;
+        h->maxw = csr_to_sell32(A, ld, sp, col, val, es, h->ew);
         h->nnz_pad = sp.back();
         int rc;
         if ((rc = dev_alloc_t(h, &h->slice_ptr, sp.size() * 8))) return rc;
@@ -671,7 +750,7 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
     // refined mode: FP32 copies of the values, Q and F; FP32 work vectors
     if (refined) {
         const size_t vb32 = vb / 2;
-        if ((rc = dev_alloc(h, &h->sval32, (size_t)h->nnz_pad * es / 2))) return rc;
+        if ((rc = dev_alloc(h, &h->sval32, (size_t)h->nnz_pad * h->ew * es / 2))) return rc;
         if ((rc = dev_alloc(h, &h->Q32, vb32 * n))) return rc;
         if (n > 1 && (rc = dev_alloc(h, &h->F32, vb32 * (n - 1)))) return rc;
         if ((rc = dev_alloc(h, &h->G32, vb32 * n))) return rc;
@@ -688,7 +767,7 @@ int create_impl(mlb_handle *h, const mlb_matrix *A, const mlb_matrix *AH, const 
         MLB_CUDA(cudaMemsetAsync(h->r32, 0, vb32, st));
         MLB_CUDA(cudaMemsetAsync(h->z32, 0, vb32, st));
         MLB_CUDA(cudaMemsetAsync(h->b32, 0, vb32, st));
-        MLB_CUDA(launch_narrow((const double *)h->sval, (float *)h->sval32, h->nnz_pad * (int64_t)es / 8, st));
+        MLB_CUDA(launch_narrow((const double *)h->sval, (float *)h->sval32, h->nnz_pad * h->ew * (int64_t)es / 8, st));
         MLB_CUDA(launch_narrow((const double *)h->Q, (float *)h->Q32, ld * (int64_t)n * (int64_t)es / 8, st));
         if (n > 1)
             MLB_CUDA(launch_narrow((const double *)h->F, (float *)h->F32, ld * (int64_t)(n - 1) * (int64_t)es / 8,
@@ -849,6 +928,7 @@ int mlbicgstab_info(const mlb_handle *h, mlb_info *info) {
     info->n = h->n;
     info->n_active = h->n_active;
     info->precond = h->precond;
+    info->entry_values = h->ew;
     info->ilu_levels = has_ilu(h) ? h->ilu_nlev_l : 0;
     info->dtype = h->dtype;
     info->precision = h->precision;
@@ -979,6 +1059,7 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
         if (!h || !b[s] || !x[s] || !(tol[s] >= 0.0) || maxit[s] < 0) return MLB_ERR_ARG;
         if (h->dtype != h0->dtype || h->precision != h0->precision || h->device != h0->device)
             return MLB_ERR_ARG;
+        if (h->ew != 1) return MLB_ERR_UNSUPPORTED;   // the batch kernels take scalar storage
     }
     memset(res, 0, sizeof(mlb_result) * (size_t)count);
     MLB_CUDA(cudaSetDevice(h0->device));
@@ -1307,7 +1388,7 @@ extern "C" {
 
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
     if (!h || !x || !y || !d) return MLB_ERR_ARG;
-    if (h->precond != MLB_PRECOND_NONE) return MLB_ERR_UNSUPPORTED;
+    if (h->precond != MLB_PRECOND_NONE || h->ew != 1) return MLB_ERR_UNSUPPORTED;
     MLB_CUDA(cudaSetDevice(h->device));
     if (!is_device_ptr(x, h->device) || !is_device_ptr(y, h->device)) return MLB_ERR_ARG;
     cudaStream_t st = h->stream;
@@ -1328,7 +1409,7 @@ int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
 
 int mlbicgstab_spmv_qdot_async(mlb_handle *h, int32_t value_type, const void *x, void *y, void *d) {
     if (!h || !x || !y || !d) return MLB_ERR_ARG;
-    if (h->precond != MLB_PRECOND_NONE) return MLB_ERR_UNSUPPORTED;
+    if (h->precond != MLB_PRECOND_NONE || h->ew != 1) return MLB_ERR_UNSUPPORTED;
     MLB_CUDA(cudaSetDevice(h->device));
     if (!is_device_ptr(x, h->device) || !is_device_ptr(y, h->device) || !is_device_ptr(d, h->device))
         return MLB_ERR_ARG;

@@ -110,6 +110,7 @@ struct SysView {
     const int32_t *scol;        // column of entry (slice, k, lane) at off + 32k + lane
     const T *sval;
     int spt[3];                 // slices per SpMV tile with 0, 1, 2 epilogue vectors (<= 0: no tiles)
+    int ew;                     // 1: scalar entries; 3: 3x3-block entries (three values, one column)
     const T *Q;                 // ld x n
     const T *F;                 // ld x (n-1), F = A^H Q(:,0:n-2)
     T *G, *W;                   // ld x n rings
@@ -224,6 +225,37 @@ __device__ __forceinline__ T sell_slice_sum(const int32_t *cp, const T *vp, int 
     return sum;
 }
 
+// 3x3-block storage ("triplet" SELL-32): entry k of lane l holds the three
+// values of the lane's row in one 3x3 block, a_{row,c}, a_{row,c+1},
+// a_{row,c+2}, at vp[3 (32 k)] .. (lane-strided by 96), and the block's first
+// column c at cp[32 k]: one column index per three values.  The row sum is
+// taken value by value in column order, which is the order of the row's
+// scalar entries when the blocks are listed by block column.
+template <typename T>
+__device__ __forceinline__ T sell_slice_sum3(const int32_t *cp, const T *vp, int w, const T *xin) {
+    T sum{};
+    for (int k = 0; k < w; ++k) {
+        const int32_t c = __ldcs(cp + 32 * k);
+        const T v0 = ldcs_val(vp + 96 * k), v1 = ldcs_val(vp + 96 * k + 1), v2 = ldcs_val(vp + 96 * k + 2);
+        sum = efma(v0, xin[c], sum);
+        sum = efma(v1, xin[c + 1], sum);
+        sum = efma(v2, xin[c + 2], sum);
+    }
+    return sum;
+}
+template <typename T>
+__device__ __noinline__ T sell_slice_sum3_wide(const int32_t *cp, const T *vp, int w, const T *xin) {
+    T sum{};
+    for (int k = 0; k < w; ++k) {
+        const int32_t c = cp[32 * k];
+        const T x0 = xin[c], x1 = xin[c + 1], x2 = xin[c + 2];
+        sum = efma(vp[96 * k], x0, sum);
+        sum = efma(vp[96 * k + 1], x1, sum);
+        sum = efma(vp[96 * k + 2], x2, sum);
+    }
+    return sum;
+}
+
 // Row sum of a slice wider than the pipelined path takes, from a stage
 // (values at vp, column indices at cp, lane-strided by 32).  Out of line
 // so that its registers do not weigh on the pipelined loop.
@@ -261,13 +293,15 @@ __device__ __noinline__ T sell_slice_sum_wide(const int32_t *cp, const T *vp, in
 // just read), so the FP64 pipe and the memory system work at the same time
 // and the only global loads on a warp's critical path are the gathers.
 // The epilogue's stores are fenced for later bulk (async-proxy) reads.
-// Returns false when a tile wait timed out.
-template <int NE, typename T, typename Fin, typename AccArr>
+// EW = 3: the 3x3-block storage (see sell_slice_sum3); slice offsets and
+// widths then count blocks.  Returns false when a tile wait timed out.
+template <int NE, int EW = 1, typename T, typename Fin, typename AccArr>
 __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned &cseq, uint64_t timeout_ns,
                                           int64_t s_lo, int64_t s_hi, int spt, const int64_t *slice_ptr,
                                           const int32_t *scol, const T *sval, const T *xin,
                                           const T *const (&epi)[NE > 0 ? NE : 1], int lane, Fin fin,
                                           AccArr &acc) {
+    static_assert(EW == 1 || EW == 3, "scalar entries or 3x3 blocks");
     constexpr int kPipeW = 8;   // slices up to this width take the pipelined path
     constexpr int NEA = NE > 0 ? NE : 1;
     const int cw = threadIdx.x >> 5;
@@ -283,7 +317,10 @@ __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned 
                 T e[NEA];
 #pragma unroll
                 for (int i = 0; i < NE; ++i) e[i] = epi[i][row];
-                fin(row, sell_slice_sum(scol + o + lane, sval + o + lane, w, xin), e, acc);
+                if constexpr (EW == 3)
+                    fin(row, sell_slice_sum3(scol + o + lane, sval + 3 * (o + lane), w, xin), e, acc);
+                else
+                    fin(row, sell_slice_sum(scol + o + lane, sval + o + lane, w, xin), e, acc);
             }
         }
         fence_proxy_async_global();
@@ -294,7 +331,8 @@ __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned 
             const void *ep[NEA];
 #pragma unroll
             for (int i = 0; i < NE; ++i) ep[i] = epi[i];
-            ok = produce_sell(R, s_lo, s_hi, spt, off, sval, (int)sizeof(T), scol, ep, NE, pseq, timeout_ns);
+            ok = produce_sell(R, s_lo, s_hi, spt, off, sval, EW * (int)sizeof(T), (int)sizeof(T), scol, ep, NE, pseq,
+                              timeout_ns);
         }
         return ok;
     }
@@ -309,13 +347,14 @@ __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned 
     unsigned char *const rbuf = R->buf;
     const unsigned cs0 = cseq;
     auto stage_of = [&](const Job &j) { return rbuf + (size_t)j.st * kStageBytes; };
-    auto vals = [&](const Job &j) { return reinterpret_cast<const T *>(stage_of(j)) + j.o + lane; };
+    auto vals = [&](const Job &j) { return reinterpret_cast<const T *>(stage_of(j)) + EW * (j.o + lane); };
     auto cols = [&](const Job &j) {
-        return reinterpret_cast<const int32_t *>(stage_of(j) + (size_t)j.nv * sizeof(T)) + j.o + lane;
+        return reinterpret_cast<const int32_t *>(stage_of(j) + (size_t)j.nv * EW * sizeof(T)) + j.o + lane;
     };
     // epilogue entry i of this warp's row in the tile
     auto epv = [&](const Job &j, int i) {
-        return reinterpret_cast<const T *>(stage_of(j) + (size_t)j.nv * (sizeof(T) + 4))[(i * spt + cw) * 32 + lane];
+        return reinterpret_cast<const T *>(stage_of(j) + (size_t)j.nv * (EW * sizeof(T) + 4))[(i * spt + cw) * 32 +
+                                                                                             lane];
     };
     // wait for tile t and locate this warp's slice in it
     auto locate = [&](int t, Job &j) -> bool {
@@ -339,13 +378,17 @@ __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned 
     int done = 0;
     if (nt > 0) {
         Job ja, jb;
-        T xv[kPipeW];
+        T xv[kPipeW * EW];
         ok = locate(0, ja);
         if (ok && ja.w >= 0 && ja.w <= kPipeW) {
             const int32_t *cp = cols(ja);
 #pragma unroll
             for (int u = 0; u < kPipeW; ++u)
-                if (u < ja.w) xv[u] = xin[cp[32 * u]];
+                if (u < ja.w) {
+                    const int32_t c = cp[32 * u];
+#pragma unroll
+                    for (int q = 0; q < EW; ++q) xv[EW * u + q] = xin[c + q];
+                }
         }
         for (int t = 0; ok && t < nt; ++t) {
             const bool more = t + 1 < nt;
@@ -362,10 +405,20 @@ __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned 
             T sum{};
 #pragma unroll
             for (int u = 0; u < kPipeW; ++u) {
-                if (na && u < ja.w) sum = efma(va[32 * u], xv[u], sum);
-                if (nb && u < jb.w) xv[u] = xin[cb[32 * u]];
+                if (na && u < ja.w) {
+#pragma unroll
+                    for (int q = 0; q < EW; ++q) sum = efma(va[32 * EW * u + q], xv[EW * u + q], sum);
+                }
+                if (nb && u < jb.w) {
+                    const int32_t c = cb[32 * u];
+#pragma unroll
+                    for (int q = 0; q < EW; ++q) xv[EW * u + q] = xin[c + q];
+                }
             }
-            if (ja.w > kPipeW) sum = sell_slice_sum_wide(cols(ja), va, ja.w, xin);
+            if (ja.w > kPipeW) {
+                if constexpr (EW == 3) sum = sell_slice_sum3_wide(cols(ja), va, ja.w, xin);
+                else sum = sell_slice_sum_wide(cols(ja), va, ja.w, xin);
+            }
             if (ja.w >= 0) {
                 T e[NEA];
 #pragma unroll
@@ -555,8 +608,9 @@ struct NoHook {
 
 // PC: built with the ILU(0) preconditioner passes (ilu_pre and the
 // product passes' switch to M^{-1} of their input); without it none of
-// that code is reachable.
-template <typename T, bool PC = false>
+// that code is reachable.  EW: the matrix storage of the products (1:
+// scalar SELL-32; 3: 3x3 blocks, see sell_slice_sum3).
+template <typename T, bool PC = false, int EW = 1>
 struct Engine {
     using S = typename coef_of<T>::type;                      // FP64 coefficient
     using ACC = typename real_of<T>::type;                    // thread accumulator
@@ -635,10 +689,11 @@ struct Engine {
         if (threadIdx.x == 0) acct->bytes += (double)nvec * (double)sys.N * sizeof(T);
     }
     __device__ __forceinline__ void sbytes(int nextra) {
-        // SpMV: entries (value + column index), row_ptr-equivalent, x read
-        // once, y written once, plus `nextra` epilogue vectors.
+        // SpMV: entries (values, and a column index per stored entry of EW
+        // values), row_ptr-equivalent, x read once, y written once, plus
+        // `nextra` epilogue vectors.
         if (threadIdx.x == 0) {
-            acct->bytes += (double)sys.nnz * (sizeof(T) + 4) + 4.0 * (double)(sys.N + 1) +
+            acct->bytes += (double)sys.nnz * (sizeof(T) + 4.0 / EW) + 4.0 * (double)(sys.N + 1) +
                            (2.0 + nextra) * (double)sys.N * sizeof(T);
             acct->spmv++;
         }
@@ -701,7 +756,7 @@ struct Engine {
             if (sys.ilu.lu) xin = sys.ilu.t;
         }
         unsigned sq = gs.seq();   // issued (producer lane) or consumed (consumers) tiles
-        const bool okw = sell_spmv<NE>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
+        const bool okw = sell_spmv<NE, EW>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
                                        sys.scol, sys.sval, xin, epi, threadIdx.x & 31, fin, acc);
         gs.seq() = sq;
         if (!okw) gs.ring->failed = 1;

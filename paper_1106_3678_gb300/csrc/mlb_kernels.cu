@@ -1,4 +1,5 @@
 // Kernels of the ML(n)BiCGStab library (sm_103a).
+#include <algorithm>
 #include <new>
 
 #include "mlb_internal.h"
@@ -11,11 +12,20 @@ namespace mlb {
 // handles that have that preconditioner.
 template <typename T>
 cudaError_t launch_solve(const SysView<T> &sys, const SolveCtl &ctl, int grid, cudaStream_t st) {
+    if constexpr (!is_cx<T>::value) {
+        if (sys.ew == 3)
+            return sys.ilu.lu ? launch_solve_pc<T, true, 3>(sys, ctl, grid, st)
+                              : launch_solve_pc<T, false, 3>(sys, ctl, grid, st);
+    }
     return sys.ilu.lu ? launch_solve_pc<T, true>(sys, ctl, grid, st) : launch_solve_pc<T, false>(sys, ctl, grid, st);
 }
 template <typename T>
 int solve_blocks_per_sm() {
-    const int a = solve_blocks_per_sm_pc<T, false>(), b = solve_blocks_per_sm_pc<T, true>();
+    int a = solve_blocks_per_sm_pc<T, false>(), b = solve_blocks_per_sm_pc<T, true>();
+    if constexpr (!is_cx<T>::value) {
+        a = std::min(a, solve_blocks_per_sm_pc<T, false, 3>());
+        b = std::min(b, solve_blocks_per_sm_pc<T, true, 3>());
+    }
     return a < b ? a : b;
 }
 template <typename T>
@@ -35,12 +45,21 @@ int batch_blocks_per_sm() {
 template <typename T32, typename T64>
 cudaError_t launch_refine(const SysView<T32> &sys, const RefView<T64> &rv, const SolveCtl &ctl,
                           const RefCtl &rc, int grid, cudaStream_t st) {
+    if constexpr (!is_cx<T32>::value) {
+        if (sys.ew == 3)
+            return sys.ilu.lu ? launch_refine_pc<T32, T64, true, 3>(sys, rv, ctl, rc, grid, st)
+                              : launch_refine_pc<T32, T64, false, 3>(sys, rv, ctl, rc, grid, st);
+    }
     return sys.ilu.lu ? launch_refine_pc<T32, T64, true>(sys, rv, ctl, rc, grid, st)
                       : launch_refine_pc<T32, T64, false>(sys, rv, ctl, rc, grid, st);
 }
 template <typename T32, typename T64>
 int refine_blocks_per_sm() {
-    const int a = refine_blocks_per_sm_pc<T32, T64, false>(), b = refine_blocks_per_sm_pc<T32, T64, true>();
+    int a = refine_blocks_per_sm_pc<T32, T64, false>(), b = refine_blocks_per_sm_pc<T32, T64, true>();
+    if constexpr (!is_cx<T32>::value) {
+        a = std::min(a, refine_blocks_per_sm_pc<T32, T64, false, 3>());
+        b = std::min(b, refine_blocks_per_sm_pc<T32, T64, true, 3>());
+    }
     return a < b ? a : b;
 }
 template <typename T32, typename T64>

@@ -59,7 +59,7 @@ struct RefCtl {
     int64_t window;       // stagnation window of one inner call
 };
 
-template <typename T64, typename T32>
+template <typename T64, typename T32, int EW = 1>
 struct Refiner {
     using ACC = double;
     static constexpr int DS = dslots<T64>();
@@ -79,7 +79,7 @@ struct Refiner {
         const T64 *epi[1] = {v.b};
         T64 *const r = v.r;
         unsigned sq = gs.seq();   // issued (producer lane) or consumed (consumers) tiles
-        bool okt = sell_spmv<1>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, v.spt[1], v.slice_ptr, v.scol, v.sval,
+        bool okt = sell_spmv<1, EW>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, v.spt[1], v.slice_ptr, v.scol, v.sval,
                                 v.x, epi, threadIdx.x & 31,
                                 [=](int64_t row, T64 y, const T64 (&e)[1], double(&a)[2]) {
                                     T64 rv = subT(e[0], y);
@@ -95,7 +95,7 @@ struct Refiner {
         bb = acc[0];
         rr = acc[1];
         if (threadIdx.x == 0) {
-            acct->bytes += (double)v.nnz * (sizeof(T64) + 4) + 4.0 * (double)(v.N + 1) +
+            acct->bytes += (double)v.nnz * (sizeof(T64) + 4.0 / EW) + 4.0 * (double)(v.N + 1) +
                            3.0 * (double)v.N * sizeof(T64);
             acct->flops += (DS == 2 ? 8.0 : 2.0) * (double)v.nnz + (DS == 2 ? 10.0 : 5.0) * (double)v.N;
             acct->spmv++;
@@ -161,12 +161,12 @@ struct RefineOut {
 
 // Residual replacement of one inner call (see the file comment and
 // Engine::inner).  A per-thread object: every thread holds the same values.
-template <typename T32, typename T64, bool PC>
+template <typename T32, typename T64, bool PC, int EW = 1>
 struct RelUpdate {
     static constexpr bool kActive = true;
     using S = typename coef_of<T32>::type;
-    Engine<T32, PC> *E;
-    Refiner<T64, T32> *R;
+    Engine<T32, PC, EW> *E;
+    Refiner<T64, T32, EW> *R;
     double sigma;      // ||r|| at the start of the call: the inner system is A d = r / sigma
     double bn;         // ||b||
     double tol;        // target of the true relative residual
@@ -217,8 +217,8 @@ struct RelUpdate {
 // Outer refinement loop (see the file comment).  ctl.err_hist records the
 // true relative residual at the start of every inner call, and the final
 // one.
-template <typename T32, typename T64, bool PC>
-__device__ RefineOut refine_solve(Engine<T32, PC> &E, Refiner<T64, T32> &R, const SolveCtl &ctl,
+template <typename T32, typename T64, bool PC, int EW = 1>
+__device__ RefineOut refine_solve(Engine<T32, PC, EW> &E, Refiner<T64, T32, EW> &R, const SolveCtl &ctl,
                                   const RefCtl &rc) {
     RefineOut out{1, 0, 0, __longlong_as_double(0x7ff8000000000000LL)};
     double prev = 0.0;   // true residual at the start of the last inner call
@@ -265,7 +265,7 @@ __device__ RefineOut refine_solve(Engine<T32, PC> &E, Refiner<T64, T32> &R, cons
         int64_t budget = ctl.maxit - out.iter;
         if (budget > rc.inner_maxit) budget = rc.inner_maxit;
         const double rn = sqrt(rr);
-        RelUpdate<T32, T64, PC> hk{&E, &R, rn, bn, ctl.tol, rc.delta, rc.window, 0.0, INFINITY, 0, err, 0};
+        RelUpdate<T32, T64, PC, EW> hk{&E, &R, rn, bn, ctl.tol, rc.delta, rc.window, 0.0, INFINITY, 0, err, 0};
         auto o = E.inner(budget, false, ctl.tol * bn / rn, R.v.r, 1.0 / rn, &hk);
         if (!E.gs.ok) return out;
         out.iter += o.iter;

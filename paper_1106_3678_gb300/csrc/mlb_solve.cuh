@@ -21,12 +21,12 @@ namespace mlb {
 // residual did not (restart rule of this library), all iterations counted
 // against one maxit; then the true residual; the team's rank-0 CTA writes
 // the result record.
-template <typename T, bool PC>
-__device__ void run_fp64_solve(Engine<T, PC> &E, GridSync &gs, const SolveCtl &ctl, Acct &acct, DevResult *res) {
+template <typename T, bool PC, int EW>
+__device__ void run_fp64_solve(Engine<T, PC, EW> &E, GridSync &gs, const SolveCtl &ctl, Acct &acct, DevResult *res) {
     using S = typename coef_of<T>::type;
     int64_t total = 0;
     int outer = 0;
-    typename Engine<T, PC>::Out o{1, 0, 0, 0, 0.0};
+    typename Engine<T, PC, EW>::Out o{1, 0, 0, 0, 0.0};
     // ILU(0): the method iterates on y = M x (y_0 = M x_0; x = M^{-1} y at
     // the end, from the final residual pass, which forms M^{-1} y)
     if constexpr (PC) {
@@ -95,7 +95,7 @@ __device__ __forceinline__ void acct_reset(Acct &acct) {
     __syncthreads();
 }
 
-template <typename T, bool PC>
+template <typename T, bool PC, int EW = 1>
 __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, SolveCtl ctl) {
     using S = typename coef_of<T>::type;
     extern __shared__ unsigned char dsm[];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, Solv
     __shared__ SysView<T> s_sys;
     __shared__ SolveCtl s_ctl;
     __shared__ SharedSlot<GridSync> gs_slot;
-    __shared__ SharedSlot<Engine<T, PC>> e_slot;
+    __shared__ SharedSlot<Engine<T, PC, EW>> e_slot;
     __shared__ unsigned seqs[kThreads];
     ring_init(&ring, ring_buffer(dsm));
     seqs[threadIdx.x] = 0;
@@ -116,11 +116,11 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, Solv
         s_sys = sys;
         s_ctl = ctl;
         new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring, seqs);
-        new (e_slot.get()) Engine<T, PC>(s_sys, s_ctl, *gs_slot.get(), cbuf, btbuf, &acct);
+        new (e_slot.get()) Engine<T, PC, EW>(s_sys, s_ctl, *gs_slot.get(), cbuf, btbuf, &acct);
     }
     acct_reset(acct);   // includes the __syncthreads that publishes the objects
     GridSync &gs = *gs_slot.get();
-    Engine<T, PC> &E = *e_slot.get();
+    Engine<T, PC, EW> &E = *e_slot.get();
     E.attach();
     run_fp64_solve(E, gs, s_ctl, acct, s_ctl.res);
     __syncthreads();
@@ -192,24 +192,26 @@ int batch_blocks_per_sm_pc() {
     return nb;
 }
 
-template <typename T, bool PC>
+template <typename T, bool PC, int EW = 1>
 cudaError_t launch_solve_pc(const SysView<T> &sys, const SolveCtl &ctl, int grid, cudaStream_t st) {
     SysView<T> s = sys;
     SolveCtl c = ctl;
     void *args[] = {(void *)&s, (void *)&c};
-    cudaError_t e = allow_ring((const void *)solve_kernel<T, PC>);
+    cudaError_t e = allow_ring((const void *)solve_kernel<T, PC, EW>);
     if (e != cudaSuccess) return e;
     if (grid <= 1)
-        return cudaLaunchKernel((const void *)solve_kernel<T, PC>, dim3(1), dim3(kThreads), args, kRingBytes, st);
-    return cudaLaunchCooperativeKernel((const void *)solve_kernel<T, PC>, dim3(grid), dim3(kThreads), args,
+        return cudaLaunchKernel((const void *)solve_kernel<T, PC, EW>, dim3(1), dim3(kThreads), args, kRingBytes,
+                                st);
+    return cudaLaunchCooperativeKernel((const void *)solve_kernel<T, PC, EW>, dim3(grid), dim3(kThreads), args,
                                        kRingBytes, st);
 }
 
-template <typename T, bool PC>
+template <typename T, bool PC, int EW = 1>
 int solve_blocks_per_sm_pc() {
     int nb = 0;
-    if (allow_ring((const void *)solve_kernel<T, PC>) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<T, PC>, kThreads, kRingBytes) != cudaSuccess)
+    if (allow_ring((const void *)solve_kernel<T, PC, EW>) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<T, PC, EW>, kThreads, kRingBytes) !=
+            cudaSuccess)
         return 0;
     return nb;
 }
@@ -299,7 +301,7 @@ int batch_refine_blocks_per_sm_pc() {
 // ===========================================================================
 // FP32-inner / FP64-refined persistent solve kernel
 // ===========================================================================
-template <typename T32, typename T64, bool PC>
+template <typename T32, typename T64, bool PC, int EW = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     refine_kernel(SysView<T32> sys, RefView<T64> rv, SolveCtl ctl, RefCtl rc) {
     using S = typename coef_of<T32>::type;
@@ -315,8 +317,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ SolveCtl s_ctl;
     __shared__ RefCtl s_rc;
     __shared__ SharedSlot<GridSync> gs_slot;
-    __shared__ SharedSlot<Engine<T32, PC>> e_slot;
-    __shared__ SharedSlot<Refiner<T64, T32>> r_slot;
+    __shared__ SharedSlot<Engine<T32, PC, EW>> e_slot;
+    __shared__ SharedSlot<Refiner<T64, T32, EW>> r_slot;
     __shared__ unsigned seqs[kThreads];
     ring_init(&ring, ring_buffer(dsm));
     seqs[threadIdx.x] = 0;
@@ -326,15 +328,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         s_ctl = ctl;
         s_rc = rc;
         GridSync *g = new (gs_slot.get()) GridSync(ctl.bar, ctl.partials, red, &sflag, ctl.timeout_ns, &ring, seqs);
-        new (e_slot.get()) Engine<T32, PC>(s_sys, s_ctl, *g, cbuf, btbuf, &acct);
-        new (r_slot.get()) Refiner<T64, T32>(s_rv, *g, &acct);
+        new (e_slot.get()) Engine<T32, PC, EW>(s_sys, s_ctl, *g, cbuf, btbuf, &acct);
+        new (r_slot.get()) Refiner<T64, T32, EW>(s_rv, *g, &acct);
     }
     acct_reset(acct);   // includes the __syncthreads that publishes the objects
     GridSync &gs = *gs_slot.get();
-    Engine<T32, PC> &E = *e_slot.get();
-    Refiner<T64, T32> &R = *r_slot.get();
+    Engine<T32, PC, EW> &E = *e_slot.get();
+    Refiner<T64, T32, EW> &R = *r_slot.get();
     E.attach();
-    RefineOut o = refine_solve<T32, T64, PC>(E, R, s_ctl, s_rc);
+    RefineOut o = refine_solve<T32, T64, PC, EW>(E, R, s_ctl, s_rc);
     __syncthreads();
     ring_drain(&ring, seqs[kConsumers], seqs[0], ctl.timeout_ns);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <typename T32, typename T64, bool PC>
+template <typename T32, typename T64, bool PC, int EW = 1>
 cudaError_t launch_refine_pc(const SysView<T32> &sys, const RefView<T64> &rv, const SolveCtl &ctl,
                           const RefCtl &rc, int grid, cudaStream_t st) {
     SysView<T32> s = sys;
@@ -363,24 +365,40 @@ cudaError_t launch_refine_pc(const SysView<T32> &sys, const RefView<T64> &rv, co
     SolveCtl c = ctl;
     RefCtl q = rc;
     void *args[] = {(void *)&s, (void *)&r, (void *)&c, (void *)&q};
-    cudaError_t e = allow_ring((const void *)refine_kernel<T32, T64, PC>);
+    cudaError_t e = allow_ring((const void *)refine_kernel<T32, T64, PC, EW>);
     if (e != cudaSuccess) return e;
     if (grid <= 1)
-        return cudaLaunchKernel((const void *)refine_kernel<T32, T64, PC>, dim3(1), dim3(kThreads), args, kRingBytes,
+        return cudaLaunchKernel((const void *)refine_kernel<T32, T64, PC, EW>, dim3(1), dim3(kThreads), args, kRingBytes,
                                 st);
-    return cudaLaunchCooperativeKernel((const void *)refine_kernel<T32, T64, PC>, dim3(grid), dim3(kThreads),
+    return cudaLaunchCooperativeKernel((const void *)refine_kernel<T32, T64, PC, EW>, dim3(grid), dim3(kThreads),
                                        args, kRingBytes, st);
 }
 
-template <typename T32, typename T64, bool PC>
+template <typename T32, typename T64, bool PC, int EW = 1>
 int refine_blocks_per_sm_pc() {
     int nb = 0;
-    if (allow_ring((const void *)refine_kernel<T32, T64, PC>) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, refine_kernel<T32, T64, PC>, kThreads, kRingBytes) !=
+    if (allow_ring((const void *)refine_kernel<T32, T64, PC, EW>) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, refine_kernel<T32, T64, PC, EW>, kThreads, kRingBytes) !=
             cudaSuccess)
         return 0;
     return nb;
 }
+
+// 3x3-block storage (real values only), instantiated in mlb_kernels_bsr.cu.
+extern template cudaError_t launch_solve_pc<double, false, 3>(const SysView<double> &, const SolveCtl &, int,
+                                                              cudaStream_t);
+extern template cudaError_t launch_solve_pc<double, true, 3>(const SysView<double> &, const SolveCtl &, int,
+                                                             cudaStream_t);
+extern template int solve_blocks_per_sm_pc<double, false, 3>();
+extern template int solve_blocks_per_sm_pc<double, true, 3>();
+extern template cudaError_t launch_refine_pc<float, double, false, 3>(const SysView<float> &,
+                                                                      const RefView<double> &, const SolveCtl &,
+                                                                      const RefCtl &, int, cudaStream_t);
+extern template cudaError_t launch_refine_pc<float, double, true, 3>(const SysView<float> &,
+                                                                     const RefView<double> &, const SolveCtl &,
+                                                                     const RefCtl &, int, cudaStream_t);
+extern template int refine_blocks_per_sm_pc<float, double, false, 3>();
+extern template int refine_blocks_per_sm_pc<float, double, true, 3>();
 
 // Instantiated in mlb_kernels_ilu.cu.
 extern template cudaError_t launch_refine_pc<float, double, true>(const SysView<float> &, const RefView<double> &,

@@ -251,12 +251,13 @@ __device__ __forceinline__ bool consume(TileRing *R, const TilePass &P, unsigned
 }
 
 // SELL-32 tiles: `spt` consecutive slices [s0, s0+spt) of this CTA's slice
-// range.  A stage holds their values, then their column indices, then for
-// each of the `ne` epilogue vectors the 32*spt entries of the tile's rows
-// (those rows belong to this CTA).  The matrix is streamed once per
+// range.  A stage holds their values (vbytes per entry: one value, or the
+// three of a 3x3-block entry), then their column indices, then for each of
+// the `ne` epilogue vectors the 32*spt entries (ebytes each) of the tile's
+// rows (those rows belong to this CTA).  The matrix is streamed once per
 // product, so its copies carry an L2 evict-first hint.
 __device__ __forceinline__ bool produce_sell(TileRing *R, int64_t s_lo, int64_t s_hi, int spt,
-                                             const SliceOffsets &off, const void *sval, int vbytes,
+                                             const SliceOffsets &off, const void *sval, int vbytes, int ebytes,
                                              const int32_t *scol, const void *const *epi, int ne,
                                              unsigned &seq, uint64_t timeout_ns) {
     const uint64_t pol = l2_evict_first_policy();
@@ -268,7 +269,7 @@ __device__ __forceinline__ bool produce_sell(TileRing *R, int64_t s_lo, int64_t 
         const int64_t e0 = off(s0), e1 = off(s1);
         const unsigned nv = (unsigned)(e1 - e0);
         const unsigned bv = nv * (unsigned)vbytes, bc = nv * 4u;
-        const unsigned be = (unsigned)(s1 - s0) * 32u * (unsigned)vbytes;
+        const unsigned be = (unsigned)(s1 - s0) * 32u * (unsigned)ebytes;
         mbar_arrive_expect_tx(&R->full[s], bv + bc + be * (unsigned)ne);
         unsigned char *dst = R->buf + (size_t)s * kStageBytes;
         if (nv > 0) {
@@ -277,7 +278,7 @@ __device__ __forceinline__ bool produce_sell(TileRing *R, int64_t s_lo, int64_t 
         }
         unsigned char *de = dst + bv + bc;
         for (int i = 0; i < ne; ++i)
-            bulk_g2s(de + (size_t)i * spt * 32 * vbytes, (const unsigned char *)epi[i] + s0 * 32 * vbytes, be,
+            bulk_g2s(de + (size_t)i * spt * 32 * ebytes, (const unsigned char *)epi[i] + s0 * 32 * ebytes, be,
                      &R->full[s]);
     }
     return true;

@@ -37,7 +37,7 @@ class mlb_matrix(C.Structure):
     _fields_ = [("nrows", C.c_int64), ("nnz", C.c_int64),
                 ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
                 ("values", C.c_void_p), ("dtype", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("block", C.c_int32)]
 
 
 class mlb_options(C.Structure):
@@ -71,7 +71,8 @@ class mlb_info(C.Structure):
                 ("grid", C.c_int32), ("block", C.c_int32),
                 ("precond", C.c_int32), ("nnz_padded", C.c_int64),
                 ("device_bytes", C.c_int64), ("n_active", C.c_int32),
-                ("ilu_levels", C.c_int32), ("qd_kernel_ms", C.c_double)]
+                ("ilu_levels", C.c_int32), ("qd_kernel_ms", C.c_double),
+                ("entry_values", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class mlb_tune_result(C.Structure):
@@ -185,16 +186,21 @@ def _ptr(a):
 
 
 class Matrix:
-    """Keeps the host arrays of an mlb_matrix alive while it is used."""
+    """Keeps the host arrays of an mlb_matrix alive while it is used.  A
+    CSR matrix (row_ptr, col, val, n_rows), or a BSR matrix of 3x3 blocks
+    (val of shape (nblocks, 3, 3), row_ptr and col over block rows and
+    columns), passed with block = 3."""
 
     def __init__(self, A):
         cplx = np.iscomplexobj(A.val)
+        dt = np.complex128 if cplx else np.float64
         self.rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
         self.ci = np.ascontiguousarray(A.col, dtype=np.int32)
-        self.val = np.ascontiguousarray(A.val, dtype=np.complex128 if cplx else np.float64)
+        block = 3 if np.ndim(A.val) == 3 else 0
+        self.val = np.ascontiguousarray(np.asarray(A.val, dtype=dt).reshape(-1))
         self.c = mlb_matrix(int(A.n_rows), int(self.rp[-1]),
                             self.rp.ctypes.data, self.ci.ctypes.data,
-                            self.val.ctypes.data, MLB_C128 if cplx else MLB_F64, 0)
+                            self.val.ctypes.data, MLB_C128 if cplx else MLB_F64, block)
         self.dtype = self.val.dtype
 
 

@@ -66,6 +66,11 @@ class BSR3:
     def nblocks(self) -> int:
         return int(self.row_ptr[-1])
 
+    @property
+    def nnz(self) -> int:
+        """Scalar entries (9 per block)."""
+        return 9 * self.nblocks
+
 
 # ---------------------------------------------------------------------------
 # generic stencil assembly

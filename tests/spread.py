@@ -61,3 +61,18 @@ def oracle_window(A, b, Q, tol, maxit, kappa=0.0, restarts=False, lib=None):
             return O.mlbicgstabt(A, rhs, x0, Q, maxit, tol, kappa, lib=lib).iter
     counts = oracle_counts(one, b)
     return window(counts), counts
+
+
+def unique_prefix(A, b, Q, K, rel=1e-12, **kw):
+    """The oracle's residual history over K steps, and the last step k <= K
+    up to which that history does not depend on the order of the oracle's
+    sums (its sequential and fixed-block builds agree to `rel`): only that
+    prefix is determined by the method rather than by rounding.  On systems
+    whose early steps amplify rounding (a residual that jumps by orders of
+    magnitude), the prefix ends early."""
+    x0 = np.zeros_like(b)
+    ref = O.mlbicgstabt(A, b, x0, Q, K, 0.0, err_hist=True, **kw)
+    alt = O.mlbicgstabt(A, b, x0, Q, K, 0.0, err_hist=True, lib=O.load_par(), **kw)
+    agree = np.abs(alt.err_hist - ref.err_hist) <= rel * ref.err_hist
+    k = K if agree.all() else int(np.argmin(agree)) - 1
+    return ref, k

@@ -110,6 +110,19 @@ def test_invalid_arguments_are_rejected_before_gpu_work(lib):
     assert _raw_create(lib, A, precision=1, inner_tol=1.0)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, precision=1, inner_maxit=0)[0] == M.MLB_ERR_ARG
     assert _raw_create(lib, A, reserved0=1)[0] == M.MLB_ERR_ARG
+    # storage: CSR (block 0 or 1) or BSR(3); BSR needs nrows divisible by 3
+    # and block columns below nrows / 3
+    Mx = M.Matrix(A)
+    Mx.c.block = 2
+    assert lib.mlbicgstab_create(C.byref(C.c_void_p()), C.byref(Mx.c), None, None) == M.MLB_ERR_ARG
+    Bk = W.reservoir_bsr3(2, 2, 2)
+    Mb = M.Matrix(Bk)
+    assert Mb.c.block == 3 and Mb.c.nnz == Bk.nblocks
+    Mb.c.nrows = Bk.n_rows + 1
+    assert lib.mlbicgstab_create(C.byref(C.c_void_p()), C.byref(Mb.c), None, None) == M.MLB_ERR_ARG
+    Mb = M.Matrix(Bk)
+    Mb.ci[0] = Bk.n_cells
+    assert lib.mlbicgstab_create(C.byref(C.c_void_p()), C.byref(Mb.c), None, None) == M.MLB_ERR_ARG
     bad = W.CSR(A.row_ptr.copy(), A.col.copy(), A.val.copy(), A.n_rows)
     bad.col[3] = A.n_rows          # column out of range
     assert _raw_create(lib, bad)[0] == M.MLB_ERR_ARG
