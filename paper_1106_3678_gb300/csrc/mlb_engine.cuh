@@ -376,58 +376,67 @@ __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned 
     };
     auto row_of = [&](int t) { return (s_lo + (int64_t)t * spt + cw) * 32 + lane; };
     int done = 0;
-    if (nt > 0) {
-        Job ja, jb;
-        T xv[kPipeW * EW];
-        ok = locate(0, ja);
-        if (ok && ja.w >= 0 && ja.w <= kPipeW) {
-            const int32_t *cp = cols(ja);
+    // x gathers of slice j into xv (pipelined path: widths up to kPipeW)
+    auto gather = [&](const Job &j, T (&xv)[kPipeW * EW]) {
+        if (j.w >= 0 && j.w <= kPipeW) {
+            const int32_t *cp = cols(j);
 #pragma unroll
             for (int u = 0; u < kPipeW; ++u)
-                if (u < ja.w) {
+                if (u < j.w) {
                     const int32_t c = cp[32 * u];
 #pragma unroll
                     for (int q = 0; q < EW; ++q) xv[EW * u + q] = xin[c + q];
                 }
         }
+    };
+    // Tile t (slice jc, its x in xc): the FMAs, each followed by the gather
+    // of slice jn (tile t+1, when `more`) into the register it has just
+    // read; then the epilogue and the release of the stage.  (Gathering two
+    // tiles ahead measured slower: 228 against 206 us per iteration at 128^3.)
+    auto step = [&](int t, const Job &jc, T (&xc)[kPipeW * EW], const Job &jn, bool more) {
+        const bool na = jc.w >= 0 && jc.w <= kPipeW;
+        const bool nb = more && jn.w >= 0 && jn.w <= kPipeW;
+        const T *va = vals(jc);
+        const int32_t *cb = cols(jn);
+        T sum{};
+#pragma unroll
+        for (int u = 0; u < kPipeW; ++u) {
+            if (na && u < jc.w) {
+#pragma unroll
+                for (int q = 0; q < EW; ++q) sum = efma(va[32 * EW * u + q], xc[EW * u + q], sum);
+            }
+            if (nb && u < jn.w) {
+                const int32_t c = cb[32 * u];
+#pragma unroll
+                for (int q = 0; q < EW; ++q) xc[EW * u + q] = xin[c + q];
+            }
+        }
+        if (jc.w > kPipeW) {
+            if constexpr (EW == 3) sum = sell_slice_sum3_wide(cols(jc), va, jc.w, xin);
+            else sum = sell_slice_sum_wide(cols(jc), va, jc.w, xin);
+        }
+        if (jc.w >= 0) {
+            T e[NEA];
+#pragma unroll
+            for (int i = 0; i < NE; ++i) e[i] = epv(jc, i);
+            fin(row_of(t), sum, e, acc);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&R->empty[jc.st]);
+        ++done;
+    };
+    if (nt > 0) {
+        Job ja, jb;
+        T xv[kPipeW * EW];
+        ok = locate(0, ja);
+        if (ok) gather(ja, xv);
         for (int t = 0; ok && t < nt; ++t) {
             const bool more = t + 1 < nt;
             if (more && !locate(t + 1, jb)) {
                 ok = false;
                 break;
             }
-            // FMAs of tile t, each followed by the gather of tile t+1 that
-            // reuses its register
-            const bool na = ja.w >= 0 && ja.w <= kPipeW;
-            const bool nb = more && jb.w >= 0 && jb.w <= kPipeW;
-            const T *va = vals(ja);
-            const int32_t *cb = cols(jb);
-            T sum{};
-#pragma unroll
-            for (int u = 0; u < kPipeW; ++u) {
-                if (na && u < ja.w) {
-#pragma unroll
-                    for (int q = 0; q < EW; ++q) sum = efma(va[32 * EW * u + q], xv[EW * u + q], sum);
-                }
-                if (nb && u < jb.w) {
-                    const int32_t c = cb[32 * u];
-#pragma unroll
-                    for (int q = 0; q < EW; ++q) xv[EW * u + q] = xin[c + q];
-                }
-            }
-            if (ja.w > kPipeW) {
-                if constexpr (EW == 3) sum = sell_slice_sum3_wide(cols(ja), va, ja.w, xin);
-                else sum = sell_slice_sum_wide(cols(ja), va, ja.w, xin);
-            }
-            if (ja.w >= 0) {
-                T e[NEA];
-#pragma unroll
-                for (int i = 0; i < NE; ++i) e[i] = epv(ja, i);
-                fin(row_of(t), sum, e, acc);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&R->empty[ja.st]);
-            ++done;
+            step(t, ja, xv, jb, more);
             ja = jb;
         }
     }
@@ -739,10 +748,28 @@ struct Engine {
         if (gs.ring->failed) { gs.ok = false; return false; }
         return true;
     }
+    // Streaming pass with no inner product: the tiles, then only a team
+    // barrier (the next pass gathers what this one wrote), no reduction.
     template <typename Fn>
     __device__ __forceinline__ bool tpass(const TilePass &P, Fn fn) {
-        double none[1];
-        return tsum<1>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *) { fn(ch, st, k); }, none);
+        bool okw = true;
+        TileRing *const ring = gs.ring;
+        const uint64_t to = gs.timeout_ns;
+        if ((threadIdx.x >> 5) == kConsumerWarps) {
+            if ((threadIdx.x & 31) == 0) {
+                unsigned sq = gs.seq();
+                okw = produce(ring, P, sq, to);
+                gs.seq() = sq;
+            }
+        } else {
+            unsigned sq = gs.seq();
+            okw = consume(ring, P, sq, to, [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k); });
+            gs.seq() = sq;
+        }
+        if (!okw) gs.ring->failed = 1;
+        if (!sync()) return false;
+        if (gs.ring->failed) { gs.ok = false; return false; }
+        return true;
     }
 
     // SELL-32 SpMV pass over the owned slices (matrix tiles through the
