@@ -92,7 +92,10 @@ WORKLOADS = {
     "helmholtz_n8_c128_ilu0mc": dict(kind="helmholtz", n=8, tol=1e-10, maxit=40000, precision=0, precond=3),
     # the fused product y = A x, d = Q^H y alone (mlbicgstab_spmv_qdot) on
     # the headline matrix, for n = 1, 4, 16 shadow vectors
-    "spmv_qdot_cd3d128": dict(kind="spmv_qdot", m=128, n=4, ns=(1, 4, 16), calls=50),
+    "spmv_qdot_cd3d128": dict(kind="spmv_qdot", m=128, n=4, ns=(1, 4, 8, 16), calls=50),
+    # the batch after mlbicgstab_autotune_batch (tile cap per size class;
+    # tuning is setup, not timed), against batch512_n4_fp64 (default caps)
+    "batch512_n4_fp64_tuned": dict(kind="batch", n=4, tol=1e-10, maxit=20000, precision=0, tune=True),
 }
 for _n in (1, 8, 16):
     WORKLOADS[f"cd3d128_n{_n}_fp64"] = dict(kind="cd3d", m=128, n=_n, tol=1e-10, maxit=60000,
@@ -101,16 +104,16 @@ DEFAULT = "cd3d128_n4_fp64"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the solve
 # kernel on the headline workload, from one ncu capture of a 300-iteration
-# launch of the current kernel: 136.82 GB + 34.61 GB.  Traffic grows in
+# launch of the current kernel: 136.83 GB + 34.62 GB.  Traffic grows in
 # proportion to the iterations, so a full launch is scaled by its
 # iteration count.  Set to None whenever the kernel changes until it is
 # captured again.
-NCU_DRAM_BYTES_PER_ITER = None
+NCU_DRAM_BYTES_PER_ITER = (136.832543e9 + 34.620510e9) / 300
 VARIANTS = ["spmv_qdot_cd3d128", "cd3d128_n1_fp64", "cd3d128_n8_fp64", "cd3d128_n16_fp64",
             "cd3d128_n4_fp64_ilu0", "cd3d128_n4_refined_ilu0", "cd3d128_n4_fp64_ilu0mc", "cd3d128_n4_refined_ilu0mc",
             "reservoir_n8_fp64", "reservoir_n8_fp64_ilu0", "reservoir_n8_refined_ilu0",
             "reservoir_n8_fp64_ilu0mc", "reservoir_n8_refined_ilu0mc",
-            "batch512_n4_fp64", "batch512_n4_fp64_ilu0", "batch512_n4_fp64_ilu0mc",
+            "batch512_n4_fp64", "batch512_n4_fp64_tuned", "batch512_n4_fp64_ilu0", "batch512_n4_fp64_ilu0mc",
             "batch512_n4_refined", "batch512_n4_refined_ilu0",
             "helmholtz_n8_c128", "helmholtz_n8_c128_kappa07", "helmholtz_n8_c128_ilu0mc", "helmholtz_n8_c64_refined",
             "sequence8_cd3d64", "tune_cd2d256"]
@@ -118,7 +121,8 @@ VARIANTS = ["spmv_qdot_cd3d128", "cd3d128_n1_fp64", "cd3d128_n8_fp64", "cd3d128_
 # same preconditioner, preconditioned against unpreconditioned, the omega
 # guard against kappa = 0.  A speedup is reported only when both sides
 # converged (every solve flag 0 with true relative residual below tol).
-PAIRS = [("cd3d128_n4_refined_ilu0", "cd3d128_n4_fp64_ilu0", "speedup_vs_fp64"),
+PAIRS = [("batch512_n4_fp64_tuned", "batch512_n4_fp64", "speedup_vs_default"),
+         ("cd3d128_n4_refined_ilu0", "cd3d128_n4_fp64_ilu0", "speedup_vs_fp64"),
          ("cd3d128_n4_refined_ilu0mc", "cd3d128_n4_fp64_ilu0mc", "speedup_vs_fp64"),
          ("reservoir_n8_refined_ilu0mc", "reservoir_n8_fp64_ilu0mc", "speedup_vs_fp64"),
          ("reservoir_n8_fp64_ilu0mc", "reservoir_n8_fp64", "speedup_vs_unpreconditioned"),
@@ -202,6 +206,8 @@ def _variant_desc(name, wl, systems):
         extra += ", ILU(0) M=LU (Algorithm 7.1; level-scheduled triangular solves)"
     if wl.get("precond", 0) == 3:
         extra += ", multicolour ILU(0) M=P^T LU P (one triangular-solve level per colour)"
+    if wl.get("tune"):
+        extra += ", team size and per-class tile caps from mlbicgstab_autotune_batch (trials: A x = 1 to tol)"
     return f"{what} (N={N:,}, nnz={nnz:,}), n={wl['n']}, {_prec_name(wl)}{extra}, tol {wl['tol']:g}"
 
 
@@ -442,8 +448,9 @@ def _create(M, A, wl, stream):
 def _measure_variant(M, name, args, dev, stream, barrier, ws):
     import torch
     vwl = dict(WORKLOADS[name])
-    if args.maxit > 0:
-        vwl["maxit"] = args.maxit
+    vmax = args.variant_maxit if args.variant_maxit is not None else args.maxit
+    if vmax > 0:
+        vwl["maxit"] = vmax
     systems = _make_variant_inputs(vwl)
     if vwl["kind"] == "sequence":
         return _measure_sequence(M, name, vwl, systems, dev, stream, barrier, ws)
@@ -463,6 +470,13 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
            "precision": _prec_name(vwl), "n": vwl["n"], "unit": UNIT,
            "kappa": vwl.get("kappa", 0.0), "precond": ["none", "jacobi", "ilu0", "ilu0_mc"][vwl.get("precond", 0)]}
     if vwl["kind"] == "batch":
+        if vwl.get("tune"):
+            t0 = time.perf_counter()
+            tr = M.mlbicgstab_autotune_batch(hs, tol=vwl["tol"], maxit=vwl["maxit"], use_cache=False)
+            caps = [M.mlbicgstab_get_tuning(h)["batch_spt_cap"] for h in hs]
+            out["autotune"] = dict(tr, seconds=time.perf_counter() - t0,
+                                   caps={str(c): caps.count(c) for c in sorted(set(caps))})
+
         def once():
             for x in xs:
                 x.zero_()
@@ -483,7 +497,18 @@ def _measure_variant(M, name, args, dev, stream, barrier, ws):
             "not_converged": sum(1 for r in res if r.flag != 0 or not r.true_relres < vwl["tol"]),
             "iters_total": sum(r.iter for r in res), "iters_max": max(r.iter for r in res),
             "true_relres_max": max(r.true_relres for r in res),
+            "systems_by_ctas": {str(c): sum(1 for r in res if r.ctas == c) for c in sorted({r.ctas for r in res})},
         })
+        # the batch kernel's algorithmic bytes (every system's passes, as
+        # counted by the kernel) over the launch's device time
+        kb = sum(r.bytes for r in res)
+        kms = res[0].kernel_ms
+        peak, peak_kind = _load_peaks()
+        if kms > 0:
+            out["roofline"] = {"bound": "hbm", "achieved": kb / (kms * 1e-3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": kb / (kms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
+                               "algorithmic_bytes_per_launch": kb, "kernel_ms_per_launch": kms,
+                               "note": "systems smaller than L2 are served partly from L2"}
         # the same systems solved one by one with the plain FP64 path
         if vwl.get("precision", 0) == 0:
             for x in xs:
@@ -607,19 +632,37 @@ def _measure_spmv_qdot(M, name, vwl, systems, dev, stream, barrier, ws):
         barrier()
         k = float(np.mean(kms)) * 1e-3
         t64, ok64 = back_to_back(h, x, y, n)
+        # the autotuner's choice of fused columns (and tile cap), then the
+        # same back-to-back timing with it
+        tune64 = M.mlbicgstab_autotune(h, iters=10, use_cache=False)
+        t64t, ok64t = back_to_back(h, x, y, n)
         h.destroy()
         h32 = M.mlbicgstab_create(A, n=n, q_seed=0, stream=stream, precision=1)
         t32, ok32 = back_to_back(h32, x32, y32, n)
+        tune32 = M.mlbicgstab_autotune(h32, iters=10, use_cache=False)
+        t32t, ok32t = back_to_back(h32, x32, y32, n)
         h32.destroy()
         out["by_n"][str(n)] = {
             "fp64": {"kernel_us_sync_call": k * 1e6, "kernel_us_min_sync_call": min(kms) * 1e3,
                      "call_us": call * 1e6, "us_per_product_back_to_back": t64 * 1e6,
                      "algorithmic_bytes": byts, "achieved_gbs": byts / t64 / 1e9,
                      "frac_of_" + peak_kind + "_hbm": byts / t64 / 1e9 / peak,
-                     "achieved_gbs_sync_call": byts / k / 1e9, "status_ok": ok64},
+                     "achieved_gbs_sync_call": byts / k / 1e9, "status_ok": ok64,
+                     "fused_columns_default": _qd_rule(n, False),
+                     "tuned": {"fused_columns": tune64["qd_fused"], "spt_cap": tune64["spt_cap"],
+                               "tuner_us": tune64["qd_us"], "tuner_default_us": tune64["qd_default_us"],
+                               "us_per_product_back_to_back": t64t * 1e6,
+                               "frac_of_" + peak_kind + "_hbm": byts / t64t / 1e9 / peak,
+                               "status_ok": ok64t}},
             "fp32": {"us_per_product_back_to_back": t32 * 1e6, "algorithmic_bytes": byts32,
                      "achieved_gbs": byts32 / t32 / 1e9,
-                     "frac_of_" + peak_kind + "_hbm": byts32 / t32 / 1e9 / peak, "status_ok": ok32}}
+                     "frac_of_" + peak_kind + "_hbm": byts32 / t32 / 1e9 / peak, "status_ok": ok32,
+                     "fused_columns_default": _qd_rule(n, False, True),
+                     "tuned": {"fused_columns": tune32["qd_fused"], "spt_cap": tune32["spt_cap"],
+                               "tuner_us": tune32["qd_us"], "tuner_default_us": tune32["qd_default_us"],
+                               "us_per_product_back_to_back": t32t * 1e6,
+                               "frac_of_" + peak_kind + "_hbm": byts32 / t32t / 1e9 / peak,
+                               "status_ok": ok32t}}}
     main = out["by_n"][str(vwl["n"])]
     out["value"] = ws * 1e6 / main["fp64"]["us_per_product_back_to_back"]
     out["ms_per_step"] = main["fp64"]["us_per_product_back_to_back"] * 1e-3
@@ -629,6 +672,15 @@ def _measure_spmv_qdot(M, name, vwl, systems, dev, stream, barrier, ws):
     out["roofline_fp32"] = {"bound": "hbm", "achieved": main["fp32"]["achieved_gbs"], "peak": peak,
                             "unit": "GB/s", "frac": main["fp32"]["achieved_gbs"] / peak, "peak_kind": peak_kind}
     return out
+
+
+def _qd_rule(n, cplx, narrow=False):
+    """The library's built-in count of Q columns fused into the product."""
+    if n == 4 and not cplx:
+        return 4
+    if n > 4 and not cplx and not narrow:
+        return 1
+    return 2 if n >= 2 else 1
 
 
 def _measure_tune(M, name, vwl, systems, dev, stream, barrier, ws, args):
@@ -855,6 +907,8 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=1)
     ap.add_argument("--maxit", type=int, default=0,
                     help="override the iteration cap (short runs for profiling)")
+    ap.add_argument("--variant-maxit", type=int, default=None,
+                    help="iteration cap of the variants (default: --maxit; 0: each workload's own)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.maxit > 0:

@@ -213,6 +213,9 @@ typedef struct {
                              entry per M^{-1}), 2 per element per inner
                              product, AXPY or norm, 1 per scaling; complex
                              multiply-adds count 8 */
+    int32_t ctas;         /* CTAs that solved the system (the grid of a
+                             single solve; in a batch 1, or the team size) */
+    int32_t reserved;
 } mlb_result;
 
 /* Facts about a handle. */
@@ -243,7 +246,46 @@ typedef struct {
     double default_us_per_iter; /* the same before tuning */
     int32_t trials;       /* configurations timed (0 when from the cache) */
     int32_t from_cache;   /* 1: taken from the process-wide cache */
+    int32_t qd_fused;     /* columns of Q fused into the epilogue of the
+                             product of mlbicgstab_spmv_qdot chosen (1, 2
+                             or 4); 0 when the handle has no such product
+                             (a preconditioner, or 3x3-block storage) */
+    int32_t reserved;
+    double qd_us;         /* device time of one fused product with it */
+    double qd_default_us; /* the same with the built-in rule */
 } mlb_tune_result;
+
+/* Launch configuration of a handle: what the autotuners choose, readable
+ * and settable so that a choice can be kept across processes. */
+typedef struct {
+    int32_t grid;          /* CTAs of the persistent solve kernel, 1 to the
+                              largest co-resident grid */
+    int32_t spt_cap;       /* cap on 32-row slices per SpMV tile, 1..15 */
+    int32_t batch_spt_cap; /* the same inside mlbicgstab_solve_batch, 0..15
+                              (0: the product reads the matrix with plain
+                              loads), or -1: spt_cap */
+    int32_t batch_team;    /* CTAs per team for the large systems of a
+                              batch whose first handle this is, 1..8 (1: no
+                              teams); default 4 */
+    int32_t qd_fused;      /* columns of Q fused into the epilogue of
+                              mlbicgstab_spmv_qdot's product: 1, 2 or 4 (4
+                              real only), or 0: the built-in rule (4 for
+                              real n = 4; 1 for real FP64 values and
+                              n > 4; else 2, or 1 when n = 1); a choice
+                              above the active n falls back to the rule */
+} mlb_tuning;
+
+/* Result of mlbicgstab_autotune_batch. */
+typedef struct {
+    int32_t classes;      /* size classes of the batch (floor(log2 N)) */
+    int32_t trials;       /* batch launches timed (0 when all cached) */
+    int32_t from_cache;   /* classes whose choice came from the cache */
+    int32_t team;         /* CTAs per team chosen (batch_team of hs[0]) */
+    double default_ms;    /* device time of the whole trial batch (see
+                             mlbicgstab_autotune_batch) in one launch with
+                             the settings the handles had before */
+    double tuned_ms;      /* the same with the chosen settings */
+} mlb_batch_tune_result;
 
 /* Parameters of mlbicgstab_solve_sequence (automatic choice of n, §5). */
 typedef struct {
@@ -293,16 +335,26 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device,
 
 /*
  * Solve `count` independent systems, one handle each (created with the same
- * dtype, precision and device), in one persistent launch: each CTA takes
- * systems from a device queue, largest first (by N + nnz), and runs the
- * same method as mlbicgstab_solve (restarts and refinement included) with
- * CTA-wide barriers and shared-memory reductions.
+ * dtype, precision and device), in one persistent launch.  Estimated work
+ * of a system: (nnz + N) N^(1/3) (the per-iteration cost times the growth
+ * of iteration counts with N of discretised PDEs).  Systems of at least
+ * 2048 rows per team CTA whose estimate exceeds 1/10 of the average work
+ * per CTA (natural-order ILU(0) systems excepted: their triangular solves
+ * take one barrier per level) are solved by teams of hs[0]'s batch_team
+ * CTAs (mlb_tuning),
+ * largest first, with team barriers and reductions (the arithmetic of a
+ * single solve with grid = the team size); the other systems by one CTA
+ * each, largest first, with CTA-wide barriers and shared-memory
+ * reductions (the arithmetic of a single solve with grid = 1).  Each runs
+ * the same method as mlbicgstab_solve (restarts and refinement included).
  *   b[s], x[s]  per-system pointers as in mlbicgstab_solve (on_device
  *               applies to all).  tol[s], maxit[s] per system.
  *   res         `count` results; kernel_ms is the time of the whole launch.
  * The stream of hs[0] is used; hs[0] keeps a workspace (items, order,
  * results) that grows to the largest batch it has run.  No residual
  * history is recorded.  Handles must not be used by other calls meanwhile.
+ * Each system's SpMV tiles take its handle's batch cap on slices per tile
+ * (set by mlbicgstab_autotune_batch), else the handle's own cap.
  */
 int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count,
                            const void *const *b, void *const *x,
@@ -360,6 +412,43 @@ int mlbicgstab_solve_sequence(mlb_handle *const *hs, int32_t count,
  */
 int mlbicgstab_autotune(mlb_handle *h, int32_t iters, int32_t use_cache,
                         mlb_tune_result *out);
+/* mlbicgstab_autotune also chooses, for a handle whose A has a fused
+ * product (no preconditioner, scalar storage), how many columns of Q the
+ * product's epilogue carries: it times 20 calls of mlbicgstab_spmv_qdot's
+ * kernel (FP64, or the FP32 copies of a refined handle) for each of 1, 2
+ * and 4 columns (4 for real data only; never more than the active n) and
+ * keeps the fastest (qd_fused); later mlbicgstab_spmv_qdot and
+ * mlbicgstab_spmv_qdot_async calls use it while n_active allows it.
+ * Results change in rounding only (the sums' order follows the columns'
+ * passes).  Allocates and frees two device vectors of N values. */
+
+/*
+ * Batch autotuner (performance only).  Its trial batches solve A x = 1 from
+ * x = 0 for every system to `tol` (at most `maxit` iterations each): the
+ * iteration counts of real solves, whose spread decides how the work
+ * should be divided.  First the team size: the whole trial batch is run
+ * with batch_team 1, 2, 4 and 8 (set on every handle; a batch takes
+ * hs[0]'s), and the fastest kept.  Then the tile cap per size class
+ * (floor(log2 N), round(nnz/N)): a trial batch of the class's systems
+ * alone is run for each cap on slices per SpMV tile in {15, 12, 8, 4, 0}
+ * (0: the product reads the matrix with plain loads instead of through
+ * the tile ring), and the fastest set as the batch cap of the class's
+ * handles (single solves keep the handle's own cap).  Choices are cached
+ * for the process: the team size per (dtype, precision, preconditioner,
+ * count, floor(log2 of the total N)), the caps per (dtype, precision,
+ * preconditioner, class); use_cache = 1 takes cached choices without
+ * running them.  Reports the device time of the whole trial batch before
+ * and after.  The handles must satisfy mlbicgstab_solve_batch's rules;
+ * their device work buffers are overwritten; blocks until done;
+ * MLB_ERR_ARG for tol < 0, maxit outside [1, 10^7] or a bad list.
+ */
+int mlbicgstab_autotune_batch(mlb_handle *const *hs, int32_t count, double tol, int64_t maxit,
+                              int32_t use_cache, mlb_batch_tune_result *out);
+
+/* Read or set a handle's launch configuration (mlb_tuning).  Results
+ * change in rounding only.  MLB_ERR_ARG for a value outside its range. */
+int mlbicgstab_get_tuning(const mlb_handle *h, mlb_tuning *out);
+int mlbicgstab_set_tuning(mlb_handle *h, const mlb_tuning *t);
 
 /*
  * Fused hot operation: y = A x and d = Q^H y (all n shadow inner products,

@@ -52,6 +52,9 @@ struct mlb_handle {
     int grid_max = 1;       // largest co-resident grid of the solve kernel
     int grid_want = 1;      // CTAs that give every CTA at least 512 chunks
     int spt_cap = kConsumerWarps;   // cap on slices per SpMV tile (autotuner)
+    int batch_spt = -1;   // the same in batches (batch autotuner; -1: spt_cap)
+    int batch_team = 4;   // CTAs per team for a batch's large systems (1: none)
+    int qd_ne = 0;        // columns fused into the product's epilogue (autotuner; 0: built-in rule)
     uint64_t timeout_ns = 2000000000ull;
     double kappa = 0.0;
     int max_outer = 10;
@@ -267,6 +270,19 @@ void conj_transpose(const mlb_matrix *A, std::vector<int64_t> &rp, std::vector<i
             }
         }
     }
+}
+
+// Cap on slices per SpMV tile inside a batch: the batch autotuner's
+// choice, else the handle's own.
+int batch_cap(const mlb_handle *h) { return h->batch_spt >= 0 ? h->batch_spt : h->spt_cap; }
+
+// Columns of Q fused into the fused product's epilogue: the autotuner's
+// choice while the active n allows it, else the built-in rule for the
+// product's value type (narrow: the FP32 copies).
+int qd_ne_for(const mlb_handle *h, bool cplx, bool narrow) {
+    const int n = h->n_active, t = h->qd_ne;
+    if ((t == 1 || t == 2 || (t == 4 && !cplx)) && t <= n) return t;
+    return qd_fused_columns(n, cplx, narrow);
 }
 
 // The handle applies ILU(0) factors (natural or multicolour order).
@@ -1036,6 +1052,7 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     res->bytes = d.bytes;
     res->flops = d.flops;
     for (int q = 0; q < 5; ++q) res->ops[q] = d.ops[q];
+    res->ctas = d.ctas;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     res->kernel_ms = ms;
@@ -1068,11 +1085,51 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
     const bool cplx = h0->dtype == MLB_C128;
     const size_t item_bytes = refined ? (cplx ? sizeof(BatchItemR<cfloat, cdouble>) : sizeof(BatchItemR<float, double>))
                                       : (cplx ? sizeof(BatchItem<cdouble>) : sizeof(BatchItem<double>));
-    // workspace: [queue (256 B)] [order: count ints, padded] [items] [results]
-    const size_t off_order = 256;
-    const size_t off_items = off_order + ((size_t)count * 4 + 255) / 256 * 256;
-    const size_t off_res = off_items + ((size_t)count * item_bytes + 255) / 256 * 256;
-    const size_t need = off_res + (size_t)count * sizeof(DevResult);
+    int sms = 0;
+    MLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h0->device));
+    const int bps = refined ? (cplx ? batch_refine_blocks_per_sm<cfloat, cdouble>()
+                                    : batch_refine_blocks_per_sm<float, double>())
+                            : (cplx ? batch_blocks_per_sm<cdouble>() : batch_blocks_per_sm<double>());
+    if (bps < 1) return MLB_ERR_CUDA;
+    // Work plan: estimated work w = (nnz + N) N^(1/3); systems of at least
+    // kTeamMinRows rows per team CTA whose w exceeds kTeamShare of the
+    // average per CTA go to teams, the others to single CTAs; each list
+    // largest first (longest-processing-time order).  Natural-order ILU(0)
+    // systems stay on one CTA: their triangular solves take one barrier
+    // per level, which a team pays in global memory (measured: the 512-
+    // system ILU(0) batch 2.20 s with teams of 4, 1.96 s without).
+    const int slots = sms * bps;   // co-resident CTAs
+    const int team = std::max(1, std::min(h0->batch_team, slots));
+    std::vector<double> w(count);
+    double wsum = 0.0;
+    for (int s = 0; s < count; ++s) {
+        w[s] = (double)(hs[s]->nnz + hs[s]->N) * std::cbrt((double)hs[s]->N);
+        wsum += w[s];
+    }
+    std::vector<int> big, small;
+    for (int s = 0; s < count; ++s) {
+        const bool t = team > 1 && hs[s]->precond != MLB_PRECOND_ILU0 && hs[s]->N >= (int64_t)kTeamMinRows * team &&
+                       w[s] > kTeamShare * wsum / slots;
+        (t ? big : small).push_back(s);
+    }
+    auto by_work = [&](int a, int c) { return w[a] > w[c]; };
+    std::stable_sort(big.begin(), big.end(), by_work);
+    std::stable_sort(small.begin(), small.end(), by_work);
+    const int teams = std::min<int>((int)big.size(), slots / team);
+    const int grid = std::min(slots, teams * team + (int)small.size());
+    // workspace: [queue (256 B)] [order_big] [order_small] [team barriers]
+    // [team slots] [solve barriers] [results] (copied from the host:
+    // zeroes, results marked as not run) [items] [team partial sums]
+    auto up256 = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t off_big = 256;
+    const size_t off_small = off_big + up256(big.size() * 4 + 4);
+    const size_t off_tbar = off_small + up256(small.size() * 4 + 4);
+    const size_t off_titem = off_tbar + up256((size_t)teams * sizeof(BarrierState) + 16);
+    const size_t off_sbar = off_titem + up256((size_t)teams * 8 + 8);
+    const size_t off_res = off_sbar + up256(big.size() * sizeof(BarrierState) + 16);
+    const size_t off_items = off_res + up256((size_t)count * sizeof(DevResult));
+    const size_t off_spart = off_items + up256((size_t)count * item_bytes);
+    const size_t need = off_spart + big.size() * 2 * kMaxSums * (size_t)team * sizeof(double) + 256;
     if (need > h0->bws_bytes) {
         if (h0->bws) cudaFree(h0->bws);
         h0->bws = nullptr;
@@ -1096,13 +1153,16 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
     char *dws = (char *)h0->bws;
     char *hws = (char *)h0->bhost;
     DevResult *dres = (DevResult *)(dws + off_res);
-    // largest systems first (longest-processing-time order)
-    std::vector<int> order(count);
-    for (int s = 0; s < count; ++s) order[s] = s;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int c) { return hs[a]->nnz + hs[a]->N > hs[c]->nnz + hs[c]->N; });
     memset(hws, 0, off_items);
-    memcpy(hws + off_order, order.data(), (size_t)count * 4);
+    memcpy(hws + off_big, big.data(), big.size() * 4);
+    memcpy(hws + off_small, small.data(), small.size() * 4);
+    uint64_t max_timeout = 0;
+    for (int s = 0; s < count; ++s) {
+        DevResult *r0 = (DevResult *)(hws + off_res) + s;
+        r0->flag = 1;
+        r0->status = kStatusTimeout;   // a system no CTA took reports a failed wait
+        max_timeout = std::max<uint64_t>(max_timeout, hs[s]->timeout_ns);
+    }
     for (int s = 0; s < count; ++s) {
         const mlb_handle *h = hs[s];
         SolveCtl ctl;
@@ -1114,54 +1174,63 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
         ctl.res = dres + s;
         ctl.timeout_ns = h->timeout_ns;
         char *dst = hws + off_items + (size_t)s * item_bytes;
+        const int cap = batch_cap(h);
         if (refined) {
             const RefCtl rc = ref_ctl(h);
             if (cplx) {
                 BatchItemR<cfloat, cdouble> it{make_view32<cfloat>(h), make_ref_view<cdouble>(h), ctl, rc};
+                set_spt(it.sys.spt, h->maxw, sizeof(cfloat), cap, h->ew);
+                set_spt(it.rv.spt, h->maxw, sizeof(cdouble), cap, h->ew);
                 memcpy(dst, &it, sizeof(it));
             } else {
                 BatchItemR<float, double> it{make_view32<float>(h), make_ref_view<double>(h), ctl, rc};
+                set_spt(it.sys.spt, h->maxw, sizeof(float), cap, h->ew);
+                set_spt(it.rv.spt, h->maxw, sizeof(double), cap, h->ew);
                 memcpy(dst, &it, sizeof(it));
             }
         } else if (cplx) {
             BatchItem<cdouble> it{make_view<cdouble>(h), ctl};
+            set_spt(it.sys.spt, h->maxw, sizeof(cdouble), cap, h->ew);
             memcpy(dst, &it, sizeof(it));
         } else {
             BatchItem<double> it{make_view<double>(h), ctl};
+            set_spt(it.sys.spt, h->maxw, sizeof(double), cap, h->ew);
             memcpy(dst, &it, sizeof(it));
         }
     }
-    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const cudaMemcpyKind outk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    BatchPlan plan;
+    plan.order_big = (const int *)(dws + off_big);
+    plan.count_big = (int)big.size();
+    plan.order_small = (const int *)(dws + off_small);
+    plan.count_small = (int)small.size();
+    plan.team = team;
+    plan.teams = teams;
+    plan.queue = (unsigned *)dws;
+    plan.tbar = (BarrierState *)(dws + off_tbar);
+    plan.team_item = (int *)(dws + off_titem);
+    plan.sbar = (BarrierState *)(dws + off_sbar);
+    plan.spart = (double *)(dws + off_spart);
+    plan.timeout_ns = max_timeout;
     for (int s = 0; s < count; ++s) {
         if (int rcs = stage_in(hs[s], b[s], x[s], on_device, st)) return rcs;
         if (int rcm = map_solution(hs[s], false, st)) return rcm;
     }
-    MLB_CUDA(cudaMemcpyAsync(dws, hws, off_res, cudaMemcpyHostToDevice, st));
-    int sms = 0;
-    MLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h0->device));
-    int bps = refined ? (cplx ? batch_refine_blocks_per_sm<cfloat, cdouble>() : batch_refine_blocks_per_sm<float, double>())
-                      : (cplx ? batch_blocks_per_sm<cdouble>() : batch_blocks_per_sm<double>());
-    if (bps < 1) return MLB_ERR_CUDA;
-    const int grid = std::min(count, sms * bps);
+    MLB_CUDA(cudaMemcpyAsync(dws, hws, off_spart, cudaMemcpyHostToDevice, st));
     bool any_ilu = false;
     for (int q = 0; q < count; ++q) any_ilu = any_ilu || has_ilu(hs[q]);
-    const int *dorder = (const int *)(dws + off_order);
-    unsigned *queue = (unsigned *)dws;
     const void *ditems = dws + off_items;
     MLB_CUDA(cudaEventRecord(h0->ev0, st));
     cudaError_t e;
     if (refined) {
         if (cplx)
-            e = launch_batch_refine<cfloat, cdouble>((const BatchItemR<cfloat, cdouble> *)ditems, dorder, count, queue,
-                                                     grid, any_ilu, st);
+            e = launch_batch_refine<cfloat, cdouble>((const BatchItemR<cfloat, cdouble> *)ditems, plan, grid, any_ilu,
+                                                     st);
         else
-            e = launch_batch_refine<float, double>((const BatchItemR<float, double> *)ditems, dorder, count, queue,
-                                                   grid, any_ilu, st);
+            e = launch_batch_refine<float, double>((const BatchItemR<float, double> *)ditems, plan, grid, any_ilu, st);
     } else if (cplx) {
-        e = launch_batch<cdouble>((const BatchItem<cdouble> *)ditems, dorder, count, queue, grid, any_ilu, st);
+        e = launch_batch<cdouble>((const BatchItem<cdouble> *)ditems, plan, grid, any_ilu, st);
     } else {
-        e = launch_batch<double>((const BatchItem<double> *)ditems, dorder, count, queue, grid, any_ilu, st);
+        e = launch_batch<double>((const BatchItem<double> *)ditems, plan, grid, any_ilu, st);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1192,17 +1261,151 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
         res[s].bytes = d.bytes;
         res[s].flops = d.flops;
         res[s].kernel_ms = ms;
+        res[s].ctas = d.ctas;
         for (int q = 0; q < 5; ++q) res[s].ops[q] = d.ops[q];
         if (d.status != 0) rc = MLB_ERR_TIMEOUT;
     }
     return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Enqueue the fused product on the handle's stream: values of type `vt`
+// (the FP64 data, or a refined handle's FP32 copies), d = device array of
+// n_active * DS doubles plus the status word.  ev0 is recorded directly
+// before the kernel when `timed`.
+int qd_enqueue(mlb_handle *h, int32_t vt, const void *x, void *y, double *d, bool timed) {
+    const bool narrow = vt == MLB_F32 || vt == MLB_C64;
+    const bool cplx = h->dtype == MLB_C128;
+    if (vt != (cplx ? MLB_C128 : MLB_F64) && vt != (cplx ? MLB_C64 : MLB_F32)) return MLB_ERR_ARG;
+    if (narrow && h->precision != MLB_PREC_FP32_REFINED) return MLB_ERR_UNSUPPORTED;
+    cudaStream_t st = h->stream;
+    cudaEvent_t ev = timed ? h->ev0 : nullptr;
+    // x is gathered from the caller's array (SELL padding columns are
+    // clamped below N); y goes to the caller's array and to the handle's
+    // padded buffer r, which the inner products stream back
+    const int grid = std::max(1, std::min(h->grid_want, h->grid_max));
+    // tiles of the product carry the fused columns of Q as epilogue vectors
+    const size_t vb = narrow ? h->esize / 2 : h->esize;
+    const int ne = qd_ne_for(h, cplx, narrow);
+    const int spt = std::min(slices_per_tile(h->maxw, vb, ne), h->spt_cap);
+    cudaError_t e;
+    if (narrow && cplx)
+        e = launch_spmv_qdot_tiled<cfloat>(make_view32<cfloat>(h), ne, spt, (const cfloat *)x, (cfloat *)h->r32,
+                                           (cfloat *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
+                                           st);
+    else if (narrow)
+        e = launch_spmv_qdot_tiled<float>(make_view32<float>(h), ne, spt, (const float *)x, (float *)h->r32,
+                                          (float *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev, st);
+    else if (cplx)
+        e = launch_spmv_qdot_tiled<cdouble>(make_view<cdouble>(h), ne, spt, (const cdouble *)x, (cdouble *)h->r,
+                                            (cdouble *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
+                                            st);
+    else
+        e = launch_spmv_qdot_tiled<double>(make_view<double>(h), ne, spt, (const double *)x, (double *)h->r,
+                                           (double *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
+                                           st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MLB_ERR_CUDA;
+    }
+    return MLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 // Autotuner: CTA count and slices per SpMV tile, chosen by timing short
-// fixed-length solves on the handle's own matrix; the choice is cached per
-// (dtype, precision, preconditioner, floor(log2 N), round(nnz/N)).
+// fixed-length solves on the handle's own matrix, and the columns fused
+// into the fused product's epilogue, chosen by timing the product; the
+// choice is cached per (dtype, precision, preconditioner, floor(log2 N),
+// round(nnz/N), active n).
+struct TuneChoice {
+    int grid, spt, qd_ne;
+};
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int, int64_t>, std::pair<int, int>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int, int64_t, int>, TuneChoice> g_tune_cache;
+// batch autotuner: cap per (dtype, precision, preconditioner, floor(log2 N), round(nnz/N)),
+// team size per (dtype, precision, preconditioner, count, floor(log2 of the total N))
+static std::map<std::tuple<int, int, int, int, int64_t>, int> g_btune_cache;
+static std::map<std::tuple<int, int, int, int, int>, int> g_bteam_cache;
+
+static int log2_floor(int64_t v) {
+    int lg = 0;
+    for (; v > 1; v >>= 1) ++lg;
+    return lg;
+}
+static int64_t per_row(const mlb_handle *h) {
+    return (int64_t)((double)h->nnz / (double)std::max<int64_t>(h->N, 1) + 0.5);
+}
+
+// Mean device time of one fused product with `ne` columns fused: 20
+// back-to-back launches between two events on the handle's stream, after
+// one untimed launch.  x, y: device vectors of N values of type vt; the
+// results land in the handle's qd_out, whose status word is checked.
+static int time_qd(mlb_handle *h, int32_t vt, int ne, const void *x, void *y, double &us) {
+    const int keep = h->qd_ne;
+    h->qd_ne = ne;
+    cudaStream_t st = h->stream;
+    int rc = qd_enqueue(h, vt, x, y, h->qd_out, false);
+    if (rc == MLB_OK && cudaEventRecord(h->ev0, st) != cudaSuccess) rc = MLB_ERR_CUDA;
+    for (int k = 0; k < 20 && rc == MLB_OK; ++k) rc = qd_enqueue(h, vt, x, y, h->qd_out, false);
+    if (rc == MLB_OK && cudaEventRecord(h->ev1, st) != cudaSuccess) rc = MLB_ERR_CUDA;
+    h->qd_ne = keep;
+    if (rc != MLB_OK) return rc;
+    const size_t nv = (size_t)h->n_active * (h->dtype == MLB_C128 ? 2 : 1);
+    MLB_CUDA(cudaMemcpyAsync(h->qd_host, h->qd_out, (nv + 1) * 8, cudaMemcpyDeviceToHost, st));
+    MLB_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    MLB_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (h->qd_host[nv] != 0.0) return MLB_ERR_TIMEOUT;
+    us = 1e3 * (double)ms / 20.0;
+    return MLB_OK;
+}
+
+// Choose the fused column count of the handle's product (none when the
+// handle has no product).  Sets h->qd_ne and the result's qd fields.
+static int tune_qd(mlb_handle *h, mlb_tune_result *out) {
+    if (h->precond != MLB_PRECOND_NONE || h->ew != 1) return MLB_OK;
+    const bool cplx = h->dtype == MLB_C128;
+    const bool narrow = h->precision == MLB_PREC_FP32_REFINED;
+    const int32_t vt = cplx ? (narrow ? MLB_C64 : MLB_C128) : (narrow ? MLB_F32 : MLB_F64);
+    const size_t vb = narrow ? h->esize / 2 : h->esize;
+    void *x = nullptr, *y = nullptr;
+    if (cudaMalloc(&x, (size_t)h->N * vb) != cudaSuccess || cudaMalloc(&y, (size_t)h->N * vb) != cudaSuccess) {
+        cudaGetLastError();
+        if (x) cudaFree(x);
+        return MLB_ERR_OOM;
+    }
+    int rc = cudaMemsetAsync(x, 0, (size_t)h->N * vb, h->stream) == cudaSuccess ? MLB_OK : MLB_ERR_CUDA;
+    const int def = qd_fused_columns(h->n_active, cplx, narrow);
+    double def_us = 0.0, best_us = 0.0;
+    int best = def;
+    if (rc == MLB_OK) rc = time_qd(h, vt, def, x, y, def_us);
+    best_us = def_us;
+    for (int ne : {1, 2, 4}) {
+        if (rc != MLB_OK) break;
+        if (ne == def || ne > h->n_active || (cplx && ne > 2)) continue;
+        double us = 0.0;
+        rc = time_qd(h, vt, ne, x, y, us);
+        if (rc == MLB_OK && us < best_us) {
+            best_us = us;
+            best = ne;
+        }
+    }
+    cudaStreamSynchronize(h->stream);
+    cudaFree(x);
+    cudaFree(y);
+    if (rc != MLB_OK) return rc;
+    h->qd_ne = best;
+    out->qd_fused = best;
+    out->qd_us = best_us;
+    out->qd_default_us = def_us;
+    return MLB_OK;
+}
 
 // Device time per iteration of `iters` iterations of A x = 1 from x = 0
 // (tol 0, so exactly `iters` steps unless a breakdown ends it earlier);
@@ -1223,18 +1426,20 @@ static int time_config(mlb_handle *h, int32_t iters, std::vector<char> &bh, std:
 int mlbicgstab_autotune(mlb_handle *h, int32_t iters, int32_t use_cache, mlb_tune_result *out) {
     if (!h || !out || iters < 1 || iters > 100000 || (use_cache != 0 && use_cache != 1)) return MLB_ERR_ARG;
     memset(out, 0, sizeof(*out));
-    int lg = 0;
-    for (int64_t v = h->N; v > 1; v >>= 1) ++lg;
-    const auto key = std::make_tuple(h->dtype, h->precision, h->precond, lg,
-                                     (int64_t)((double)h->nnz / (double)std::max<int64_t>(h->N, 1) + 0.5));
+    MLB_CUDA(cudaSetDevice(h->device));
+    const auto key = std::make_tuple(h->dtype, h->precision, h->precond, log2_floor(h->N), per_row(h), h->n_active);
     if (use_cache) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            h->grid = std::max(1, std::min(it->second.first, h->grid_max));
-            h->spt_cap = std::max(1, std::min(it->second.second, (int)kConsumerWarps));
+            h->grid = std::max(1, std::min(it->second.grid, h->grid_max));
+            h->spt_cap = std::max(1, std::min(it->second.spt, (int)kConsumerWarps));
+            h->qd_ne = it->second.qd_ne;
             out->grid = h->grid;
             out->spt_cap = h->spt_cap;
+            out->qd_fused = h->precond == MLB_PRECOND_NONE && h->ew == 1
+                                ? qd_ne_for(h, h->dtype == MLB_C128, h->precision == MLB_PREC_FP32_REFINED)
+                                : 0;
             out->from_cache = 1;
             return MLB_OK;
         }
@@ -1280,15 +1485,176 @@ int mlbicgstab_autotune(mlb_handle *h, int32_t iters, int32_t use_cache, mlb_tun
         }
     h->grid = best_g;
     h->spt_cap = best_s;
+    rc = tune_qd(h, out);
+    if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {best_g, best_s};
+        g_tune_cache[key] = {best_g, best_s, h->qd_ne};
     }
     out->grid = best_g;
     out->spt_cap = best_s;
     out->us_per_iter = best_us;
     out->default_us_per_iter = def_us;
     out->trials = trials;
+    return MLB_OK;
+}
+
+int mlbicgstab_get_tuning(const mlb_handle *h, mlb_tuning *out) {
+    if (!h || !out) return MLB_ERR_ARG;
+    out->grid = h->grid;
+    out->spt_cap = h->spt_cap;
+    out->batch_spt_cap = h->batch_spt;
+    out->batch_team = h->batch_team;
+    out->qd_fused = h->qd_ne;
+    return MLB_OK;
+}
+
+int mlbicgstab_set_tuning(mlb_handle *h, const mlb_tuning *t) {
+    if (!h || !t) return MLB_ERR_ARG;
+    if (t->grid < 1 || t->grid > h->grid_max) return MLB_ERR_ARG;
+    if (t->spt_cap < 1 || t->spt_cap > (int)kConsumerWarps) return MLB_ERR_ARG;
+    if (t->batch_spt_cap < -1 || t->batch_spt_cap > (int)kConsumerWarps) return MLB_ERR_ARG;
+    if (t->batch_team < 1 || t->batch_team > kMaxBatchTeam) return MLB_ERR_ARG;
+    if (t->qd_fused != 0 && t->qd_fused != 1 && t->qd_fused != 2 && t->qd_fused != 4) return MLB_ERR_ARG;
+    if (t->qd_fused == 4 && h->dtype == MLB_C128) return MLB_ERR_ARG;
+    h->grid = t->grid;
+    h->spt_cap = t->spt_cap;
+    h->batch_spt = t->batch_spt_cap;
+    h->batch_team = t->batch_team;
+    h->qd_ne = t->qd_fused;
+    return MLB_OK;
+}
+
+// Device time of one trial batch over `sel`: A x = 1 from x = 0 to `tol`,
+// at most `maxit` iterations per system, host buffers.
+static int time_batch(const std::vector<mlb_handle *> &sel, double tol_, int64_t maxit, double &ms) {
+    const size_t cnt = sel.size();
+    std::vector<std::vector<char>> bh(cnt), xh(cnt);
+    std::vector<const void *> bp(cnt);
+    std::vector<void *> xp(cnt);
+    std::vector<double> tol(cnt, tol_);
+    std::vector<int64_t> its(cnt, maxit);
+    std::vector<mlb_result> res(cnt);
+    const double one = 1.0;
+    for (size_t s = 0; s < cnt; ++s) {
+        const mlb_handle *h = sel[s];
+        bh[s].assign((size_t)h->N * h->esize, 0);
+        xh[s].assign((size_t)h->N * h->esize, 0);
+        for (int64_t i = 0; i < h->N; ++i) memcpy(&bh[s][(size_t)i * h->esize], &one, sizeof(one));
+        bp[s] = bh[s].data();
+        xp[s] = xh[s].data();
+    }
+    const int rc = mlbicgstab_solve_batch(sel.data(), (int32_t)cnt, bp.data(), xp.data(), 0, tol.data(), its.data(),
+                                          res.data());
+    if (rc != MLB_OK) return rc;
+    ms = res[0].kernel_ms;
+    return MLB_OK;
+}
+
+int mlbicgstab_autotune_batch(mlb_handle *const *hs, int32_t count, double tol, int64_t maxit, int32_t use_cache,
+                              mlb_batch_tune_result *out) {
+    if (!hs || count <= 0 || !out || !(tol >= 0.0) || maxit < 1 || maxit > 10000000 ||
+        (use_cache != 0 && use_cache != 1))
+        return MLB_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    for (int32_t s = 0; s < count; ++s) {
+        const mlb_handle *h = hs[s];
+        if (!h || h->dtype != hs[0]->dtype || h->precision != hs[0]->precision || h->device != hs[0]->device)
+            return MLB_ERR_ARG;
+        for (int32_t t = 0; t < s; ++t)
+            if (hs[t] == h) return MLB_ERR_ARG;   // each system needs its own handle
+        if (h->ew != 1) return MLB_ERR_UNSUPPORTED;
+    }
+    std::vector<mlb_handle *> all(hs, hs + count);
+    int64_t ntot = 0;
+    for (mlb_handle *h : all) ntot += h->N;
+    // size classes in a fixed order
+    std::map<std::pair<int, int64_t>, std::vector<mlb_handle *>> classes;
+    for (mlb_handle *h : all) classes[{log2_floor(h->N), per_row(h)}].push_back(h);
+    out->classes = (int32_t)classes.size();
+    double ms = 0.0;
+    int trials = 0;
+    int rc = time_batch(all, tol, maxit, ms);
+    ++trials;
+    if (rc) return rc;
+    out->default_ms = ms;
+    // team size, on the whole trial batch
+    const mlb_handle *h0 = all[0];
+    const auto tkey = std::make_tuple(h0->dtype, h0->precision, h0->precond, (int)count, log2_floor(ntot));
+    int team = -1;
+    bool team_cached = false;
+    if (use_cache) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_bteam_cache.find(tkey);
+        if (it != g_bteam_cache.end()) {
+            team = it->second;
+            team_cached = true;
+        }
+    }
+    if (team < 0) {
+        std::vector<int> cand{all[0]->batch_team};
+        for (int c : {1, 2, 4, 8})
+            if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+        double best_ms = 1e300;
+        for (int c : cand) {
+            for (mlb_handle *h : all) h->batch_team = c;
+            double t = 0.0;
+            rc = time_batch(all, tol, maxit, t);
+            ++trials;
+            if (rc) return rc;
+            if (t < best_ms) {
+                best_ms = t;
+                team = c;
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_bteam_cache[tkey] = team;
+    }
+    for (mlb_handle *h : all) h->batch_team = team;
+    out->team = team;
+    // tile caps per size class
+    for (auto &kv : classes) {
+        std::vector<mlb_handle *> &sel = kv.second;
+        const mlb_handle *hc = sel[0];
+        const auto key = std::make_tuple(hc->dtype, hc->precision, hc->precond, kv.first.first, kv.first.second);
+        if (use_cache) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_btune_cache.find(key);
+            if (it != g_btune_cache.end()) {
+                for (mlb_handle *h : sel) h->batch_spt = it->second;
+                ++out->from_cache;
+                continue;
+            }
+        }
+        std::vector<int> caps{batch_cap(hc)};
+        for (int c : {(int)kConsumerWarps, 12, 8, 4, 0})
+            if (std::find(caps.begin(), caps.end(), c) == caps.end()) caps.push_back(c);
+        std::vector<int> keep;
+        for (mlb_handle *h : sel) keep.push_back(h->batch_spt);
+        int best = caps[0];
+        double best_ms = 1e300;
+        for (int c : caps) {
+            for (mlb_handle *h : sel) h->batch_spt = c;
+            double t = 0.0;
+            rc = time_batch(sel, tol, maxit, t);
+            ++trials;
+            if (rc != MLB_OK) {
+                for (size_t i = 0; i < sel.size(); ++i) sel[i]->batch_spt = keep[i];
+                return rc;
+            }
+            if (t < best_ms) {
+                best_ms = t;
+                best = c;
+            }
+        }
+        for (mlb_handle *h : sel) h->batch_spt = best;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_btune_cache[key] = best;
+    }
+    out->trials = team_cached && out->from_cache == out->classes ? 0 : trials;
+    rc = time_batch(all, tol, maxit, ms);
+    if (rc) return rc;
+    out->tuned_ms = ms;
     return MLB_OK;
 }
 
@@ -1337,54 +1703,6 @@ int mlbicgstab_solve_sequence(mlb_handle *const *hs, int32_t count, const void *
     return rc;
 }
 
-}  // extern "C"
-
-namespace {
-
-// Enqueue the fused product on the handle's stream: values of type `vt`
-// (the FP64 data, or a refined handle's FP32 copies), d = device array of
-// n_active * DS doubles plus the status word.  ev0 is recorded directly
-// before the kernel when `timed`.
-int qd_enqueue(mlb_handle *h, int32_t vt, const void *x, void *y, double *d, bool timed) {
-    const bool narrow = vt == MLB_F32 || vt == MLB_C64;
-    const bool cplx = h->dtype == MLB_C128;
-    if (vt != (cplx ? MLB_C128 : MLB_F64) && vt != (cplx ? MLB_C64 : MLB_F32)) return MLB_ERR_ARG;
-    if (narrow && h->precision != MLB_PREC_FP32_REFINED) return MLB_ERR_UNSUPPORTED;
-    cudaStream_t st = h->stream;
-    cudaEvent_t ev = timed ? h->ev0 : nullptr;
-    // x is gathered from the caller's array (SELL padding columns are
-    // clamped below N); y goes to the caller's array and to the handle's
-    // padded buffer r, which the inner products stream back
-    const int grid = std::max(1, std::min(h->grid_want, h->grid_max));
-    // tiles of the product carry the fused columns of Q as epilogue vectors
-    const size_t vb = narrow ? h->esize / 2 : h->esize;
-    const int spt = std::min(slices_per_tile(h->maxw, vb, qd_fused_columns(h->n_active, cplx)), h->spt_cap);
-    cudaError_t e;
-    if (narrow && cplx)
-        e = launch_spmv_qdot_tiled<cfloat>(make_view32<cfloat>(h), spt, (const cfloat *)x, (cfloat *)h->r32,
-                                           (cfloat *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
-                                           st);
-    else if (narrow)
-        e = launch_spmv_qdot_tiled<float>(make_view32<float>(h), spt, (const float *)x, (float *)h->r32,
-                                          (float *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev, st);
-    else if (cplx)
-        e = launch_spmv_qdot_tiled<cdouble>(make_view<cdouble>(h), spt, (const cdouble *)x, (cdouble *)h->r,
-                                            (cdouble *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
-                                            st);
-    else
-        e = launch_spmv_qdot_tiled<double>(make_view<double>(h), spt, (const double *)x, (double *)h->r,
-                                           (double *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
-                                           st);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return MLB_ERR_CUDA;
-    }
-    return MLB_OK;
-}
-
-}  // namespace
-
-extern "C" {
 
 int mlbicgstab_spmv_qdot(mlb_handle *h, const void *x, void *y, void *d) {
     if (!h || !x || !y || !d) return MLB_ERR_ARG;

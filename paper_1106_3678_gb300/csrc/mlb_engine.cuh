@@ -55,6 +55,7 @@ struct DevResult {
     double err, true_relres, bytes;
     int64_t ops[5];
     double flops;
+    int32_t ctas, pad;   // CTAs that solved the system
 };
 
 enum { OP_MATVEC = 0, OP_DOT = 1, OP_SAXPY = 2, OP_SCALE = 3, OP_NORM = 4 };
@@ -461,8 +462,9 @@ __device__ __forceinline__ typename coef_of<T>::type mk_coef(const double *v) {
 }
 
 // Synchronisation state of one CTA within the team of CTAs that solves one
-// system: the whole grid (a single solve), or the CTA alone (a batch, one
-// system per CTA).  Every CTA of a team passes the same sequence of
+// system: the whole grid (a single solve), a group of CTAs of a batch
+// launch (a large system of a batch), or the CTA alone (the other systems
+// of a batch).  Every CTA of a team passes the same sequence of
 // barriers and reductions, so `epoch` and the slots advance in lock step.
 // Several engines in one kernel share one GridSync.
 //
@@ -494,6 +496,12 @@ struct GridSync {
     __device__ GridSync(BarrierState *b, double *p, double *r, int *f, uint64_t to, TileRing *rg, unsigned *sq)
         : nblocks(gridDim.x), bid(blockIdx.x), bar(b), partials(p), red(r), sflag(f), timeout_ns(to), epoch(0),
           slot(0), ok(true), ring(rg), seqs(sq) {}
+    // Team = `nb` CTAs of a batch launch (rank `id`) with their own
+    // barrier state and partial sums ([2][kMaxSums][nb] doubles).
+    __device__ GridSync(BarrierState *b, double *p, unsigned nb, unsigned id, double *r, int *f, uint64_t to,
+                        TileRing *rg, unsigned *sq)
+        : nblocks(nb), bid(id), bar(b), partials(p), red(r), sflag(f), timeout_ns(to), epoch(0), slot(0), ok(true),
+          ring(rg), seqs(sq) {}
     // Team = this CTA alone.
     __device__ GridSync(double *r, int *f, uint64_t to, TileRing *rg, unsigned *sq)
         : nblocks(1), bid(0), bar(nullptr), partials(nullptr), red(r), sflag(f), timeout_ns(to), epoch(0), slot(0),

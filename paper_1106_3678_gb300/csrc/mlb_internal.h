@@ -48,14 +48,43 @@ struct BatchItemR {
     SolveCtl ctl;
     RefCtl rc;
 };
+// Batch work plan parameters: a system goes to a team when it has at
+// least kTeamMinRows rows per team CTA and its estimated work exceeds
+// kTeamShare of the average work per CTA; teams have at most kMaxBatchTeam
+// CTAs.
+constexpr int kTeamMinRows = 2048;
+constexpr double kTeamShare = 0.1;
+constexpr int kMaxBatchTeam = 8;
+
+// Work plan of a batch launch (device pointers into the batch workspace).
+// The first teams * team CTAs form `teams` teams of `team` consecutive CTAs;
+// each team takes the systems of order_big (a device queue, largest first)
+// one at a time and solves each with all its CTAs (team barriers and
+// reductions like a multi-CTA solve with grid = team).  Then every CTA,
+// and from the start every CTA outside the teams, takes the systems of
+// order_small (largest first) and solves each alone.  With teams the launch
+// is cooperative (all CTAs co-resident), so a team's CTAs all run.
+struct BatchPlan {
+    const int *order_big;    // item indices solved by teams
+    int count_big;
+    const int *order_small;  // item indices solved by one CTA
+    int count_small;
+    int team;                // CTAs per team
+    int teams;               // teams (0: none)
+    unsigned *queue;         // [0]: next of order_small, [1]: next of order_big (zeroed)
+    BarrierState *tbar;      // per team: barrier of the team's turns (zeroed)
+    int *team_item;          // per team: 2 slots, the turn's position in order_big
+    BarrierState *sbar;      // per position of order_big: the solve's barrier (zeroed)
+    double *spart;           // per position of order_big: 2 * kMaxSums * team doubles
+    uint64_t timeout_ns;     // limit of the waits between turns
+};
 // ilu: some item has an ILU(0) preconditioner (the kernel with those passes
 // then runs every item, each by its own view).
 template <typename T>
-cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
-                         bool ilu, cudaStream_t st);
+cudaError_t launch_batch(const BatchItem<T> *items, const BatchPlan &plan, int grid, bool ilu, cudaStream_t st);
 template <typename T32, typename T64>
-cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
-                                int grid, bool ilu, cudaStream_t st);
+cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const BatchPlan &plan, int grid, bool ilu,
+                                cudaStream_t st);
 template <typename T>
 int batch_blocks_per_sm();
 template <typename T32, typename T64>
@@ -77,8 +106,9 @@ cudaError_t launch_ahq(const int64_t *rp, const int32_t *ci, const T *av,
 // Fused y = A x, d = Q^H y.  `partials` holds grid * kQdMaxN * 2 doubles.
 constexpr int kQdMaxN = 64;
 // One CTA of kThreads per SM (grid <= the handle's grid_max),
-// dynamic shared memory kRingBytes.  The first qd_fused_columns(n, .) columns
-// of Q are epilogue vectors of the SELL product, whose tiles hold `spt`
+// dynamic shared memory kRingBytes.  The first `ne` columns (1, 2 or 4;
+// at most n, and at most 2 for complex values) of Q are epilogue vectors
+// of the SELL product, whose tiles hold `spt`
 // slices (sized for that many epilogue vectors); the others take tile
 // passes over y.  x: the caller's N values (SELL padding columns stay below
 // N); y: a padded scratch vector of ld values; yout: the caller's N values.
@@ -87,16 +117,23 @@ constexpr int kQdMaxN = 64;
 // at allocation); d (device) receives the n inner products (2n doubles for
 // complex) and then d[n * DS] = 1.0 if any CTA timed out, else 0.0.
 // ev (optional) is recorded on st directly before the kernel launch.
-// Fused columns: 4 only when that is all of them (real n = 4): four
+// Default fused columns: 4 only when that is all of them (real n = 4): four
 // epilogue vectors leave room for 12 slices per tile, so 3 of the 15
 // consumer warps idle in the product, which costs more than a later pass
-// over y for the remaining columns (measured at n = 8: 107 us fusing 4,
-// 95 us fusing 2); complex values take at most 2 (4 spill registers).
-inline int qd_fused_columns(int n, bool cplx) { return n == 4 && !cplx ? 4 : (n >= 2 ? 2 : 1); }
+// over y for the remaining columns; complex values take at most 2 (4
+// spill registers).  Real FP64 with n > 4 fuses 1: the product is bound by
+// FP64 issue, and the later passes over y overlap their DFMAs with the
+// loads better (128^3, n = 8: 86 us fusing 1, 92 us fusing 2, 107 us
+// fusing 4; n = 16: 119 against 126 us).
+inline int qd_fused_columns(int n, bool cplx, bool narrow) {
+    if (n == 4 && !cplx) return 4;
+    if (n > 4 && !cplx && !narrow) return 1;
+    return n >= 2 ? 2 : 1;
+}
 template <typename T>
-cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
-                                   int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
-                                   cudaStream_t st);
+cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int ne, int spt, const T *x, T *y, T *yout,
+                                   double *partials, int grid, int *status, unsigned *ticket, double *d,
+                                   cudaEvent_t ev, cudaStream_t st);
 
 // ILU(0) preconditioner, host side (mlb_ilu.cu).  Factors of A in A's
 // pattern (columns increasing within each row, repeated entries merged):

@@ -29,10 +29,8 @@ int solve_blocks_per_sm() {
     return a < b ? a : b;
 }
 template <typename T>
-cudaError_t launch_batch(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
-                         bool ilu, cudaStream_t st) {
-    return ilu ? launch_batch_pc<T, true>(items, order, count, queue, grid, st)
-               : launch_batch_pc<T, false>(items, order, count, queue, grid, st);
+cudaError_t launch_batch(const BatchItem<T> *items, const BatchPlan &plan, int grid, bool ilu, cudaStream_t st) {
+    return ilu ? launch_batch_pc<T, true>(items, plan, grid, st) : launch_batch_pc<T, false>(items, plan, grid, st);
 }
 template <typename T>
 int batch_blocks_per_sm() {
@@ -63,10 +61,10 @@ int refine_blocks_per_sm() {
     return a < b ? a : b;
 }
 template <typename T32, typename T64>
-cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
-                                int grid, bool ilu, cudaStream_t st) {
-    return ilu ? launch_batch_refine_pc<T32, T64, true>(items, order, count, queue, grid, st)
-               : launch_batch_refine_pc<T32, T64, false>(items, order, count, queue, grid, st);
+cudaError_t launch_batch_refine(const BatchItemR<T32, T64> *items, const BatchPlan &plan, int grid, bool ilu,
+                                cudaStream_t st) {
+    return ilu ? launch_batch_refine_pc<T32, T64, true>(items, plan, grid, st)
+               : launch_batch_refine_pc<T32, T64, false>(items, plan, grid, st);
 }
 template <typename T32, typename T64>
 int batch_refine_blocks_per_sm() {
@@ -361,11 +359,12 @@ static cudaError_t launch_qd_tiled_ne(const SysView<T> &sys, int spt, const T *x
 }
 
 template <typename T>
-cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
-                                   int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
-                                   cudaStream_t st) {
+cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int ne, int spt, const T *x, T *y, T *yout,
+                                   double *partials, int grid, int *status, unsigned *ticket, double *d,
+                                   cudaEvent_t ev, cudaStream_t st) {
     constexpr int DS = dslots<T>();
-    const int ne = qd_fused_columns(sys.n, DS == 2);
+    if (ne < 1 || ne > sys.n || (ne != 1 && ne != 2 && ne != 4) || (DS == 2 && ne > 2))
+        return cudaErrorInvalidValue;
     if constexpr (DS == 1) {
         if (ne == 4)
             return launch_qd_tiled_ne<T, 4>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
@@ -416,16 +415,16 @@ template cudaError_t launch_ahq<double>(const int64_t *, const int32_t *, const 
                                         const double *, double *, int, cudaStream_t);
 template cudaError_t launch_ahq<cdouble>(const int64_t *, const int32_t *, const cdouble *, int64_t, int64_t,
                                          const cdouble *, cdouble *, int, cudaStream_t);
-template cudaError_t launch_spmv_qdot_tiled<double>(const SysView<double> &, int, const double *, double *, double *,
-                                                    double *, int, int *, unsigned *, double *, cudaEvent_t,
-                                                    cudaStream_t);
-template cudaError_t launch_spmv_qdot_tiled<cdouble>(const SysView<cdouble> &, int, const cdouble *, cdouble *,
+template cudaError_t launch_spmv_qdot_tiled<double>(const SysView<double> &, int, int, const double *, double *,
+                                                    double *, double *, int, int *, unsigned *, double *,
+                                                    cudaEvent_t, cudaStream_t);
+template cudaError_t launch_spmv_qdot_tiled<cdouble>(const SysView<cdouble> &, int, int, const cdouble *, cdouble *,
                                                      cdouble *, double *, int, int *, unsigned *, double *,
                                                      cudaEvent_t, cudaStream_t);
-template cudaError_t launch_spmv_qdot_tiled<float>(const SysView<float> &, int, const float *, float *, float *,
-                                                   double *, int, int *, unsigned *, double *, cudaEvent_t,
-                                                   cudaStream_t);
-template cudaError_t launch_spmv_qdot_tiled<cfloat>(const SysView<cfloat> &, int, const cfloat *, cfloat *,
+template cudaError_t launch_spmv_qdot_tiled<float>(const SysView<float> &, int, int, const float *, float *,
+                                                   float *, double *, int, int *, unsigned *, double *,
+                                                   cudaEvent_t, cudaStream_t);
+template cudaError_t launch_spmv_qdot_tiled<cfloat>(const SysView<cfloat> &, int, int, const cfloat *, cfloat *,
                                                     cfloat *, double *, int, int *, unsigned *, double *,
                                                     cudaEvent_t, cudaStream_t);
 template cudaError_t launch_refine<float, double>(const SysView<float> &, const RefView<double> &,
@@ -434,14 +433,12 @@ template cudaError_t launch_refine<cfloat, cdouble>(const SysView<cfloat> &, con
                                                     const SolveCtl &, const RefCtl &, int, cudaStream_t);
 template int refine_blocks_per_sm<float, double>();
 template int refine_blocks_per_sm<cfloat, cdouble>();
-template cudaError_t launch_batch<double>(const BatchItem<double> *, const int *, int, unsigned *, int, bool,
-                                          cudaStream_t);
-template cudaError_t launch_batch<cdouble>(const BatchItem<cdouble> *, const int *, int, unsigned *, int, bool,
-                                           cudaStream_t);
-template cudaError_t launch_batch_refine<float, double>(const BatchItemR<float, double> *, const int *, int,
-                                                        unsigned *, int, bool, cudaStream_t);
-template cudaError_t launch_batch_refine<cfloat, cdouble>(const BatchItemR<cfloat, cdouble> *, const int *, int,
-                                                          unsigned *, int, bool, cudaStream_t);
+template cudaError_t launch_batch<double>(const BatchItem<double> *, const BatchPlan &, int, bool, cudaStream_t);
+template cudaError_t launch_batch<cdouble>(const BatchItem<cdouble> *, const BatchPlan &, int, bool, cudaStream_t);
+template cudaError_t launch_batch_refine<float, double>(const BatchItemR<float, double> *, const BatchPlan &, int,
+                                                        bool, cudaStream_t);
+template cudaError_t launch_batch_refine<cfloat, cdouble>(const BatchItemR<cfloat, cdouble> *, const BatchPlan &,
+                                                          int, bool, cudaStream_t);
 template int batch_blocks_per_sm<double>();
 template int batch_blocks_per_sm<cdouble>();
 template int batch_refine_blocks_per_sm<float, double>();

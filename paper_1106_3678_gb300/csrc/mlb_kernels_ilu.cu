@@ -7,9 +7,8 @@ namespace mlb {
 
 template cudaError_t launch_solve_pc<double, true>(const SysView<double> &, const SolveCtl &, int, cudaStream_t);
 template cudaError_t launch_solve_pc<cdouble, true>(const SysView<cdouble> &, const SolveCtl &, int, cudaStream_t);
-template cudaError_t launch_batch_pc<double, true>(const BatchItem<double> *, const int *, int, unsigned *, int,
-                                                   cudaStream_t);
-template cudaError_t launch_batch_pc<cdouble, true>(const BatchItem<cdouble> *, const int *, int, unsigned *, int,
+template cudaError_t launch_batch_pc<double, true>(const BatchItem<double> *, const BatchPlan &, int, cudaStream_t);
+template cudaError_t launch_batch_pc<cdouble, true>(const BatchItem<cdouble> *, const BatchPlan &, int,
                                                     cudaStream_t);
 template int solve_blocks_per_sm_pc<double, true>();
 template int solve_blocks_per_sm_pc<cdouble, true>();
@@ -21,11 +20,10 @@ template cudaError_t launch_refine_pc<cfloat, cdouble, true>(const SysView<cfloa
                                                              const SolveCtl &, const RefCtl &, int, cudaStream_t);
 template int refine_blocks_per_sm_pc<float, double, true>();
 template int refine_blocks_per_sm_pc<cfloat, cdouble, true>();
-template cudaError_t launch_batch_refine_pc<float, double, true>(const BatchItemR<float, double> *, const int *,
-                                                                 int, unsigned *, int, cudaStream_t);
+template cudaError_t launch_batch_refine_pc<float, double, true>(const BatchItemR<float, double> *,
+                                                                 const BatchPlan &, int, cudaStream_t);
 template cudaError_t launch_batch_refine_pc<cfloat, cdouble, true>(const BatchItemR<cfloat, cdouble> *,
-                                                                   const int *, int, unsigned *, int,
-                                                                   cudaStream_t);
+                                                                   const BatchPlan &, int, cudaStream_t);
 template int batch_refine_blocks_per_sm_pc<float, double, true>();
 template int batch_refine_blocks_per_sm_pc<cfloat, cdouble, true>();
 

@@ -69,6 +69,7 @@ __device__ void run_fp64_solve(Engine<T, PC, EW> &E, GridSync &gs, const SolveCt
         res->bytes = acct.bytes;
         res->flops = acct.flops;
         for (int q = 0; q < 5; ++q) res->ops[q] = ops_last[q];
+        res->ctas = (int32_t)gs.nblocks;
     }
 }
 
@@ -130,12 +131,51 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SysView<T> sys, Solv
 // ===========================================================================
 // batch: many independent systems in one persistent launch
 // ===========================================================================
-// Each CTA takes the next system from a device queue (systems ordered
-// largest first by the host) and solves it alone: the same method with
-// CTA-wide barriers and reductions in shared memory.
+// Work distribution of a batch launch (BatchPlan).  team_next: the team's
+// next position in order_big, agreed on by the team's CTAs: the rank-0 CTA
+// takes it from the queue into one of two slots (a slot is rewritten two
+// turns later, after every CTA of the team has passed the turn between),
+// and a team barrier publishes it.  -1 when order_big is exhausted or the
+// barrier failed.
+__device__ __forceinline__ int team_next(const BatchPlan &p, unsigned team, unsigned rank, unsigned &tepoch,
+                                         unsigned turn, int *sflag, int *s_next) {
+    int *slot = p.team_item + 2 * team + (turn & 1u);
+    if (rank == 0 && threadIdx.x == 0) *(volatile int *)slot = (int)atomicAdd(&p.queue[1], 1u);
+    if (!grid_barrier(p.tbar + team, tepoch, (unsigned)p.team, p.timeout_ns, sflag)) return -1;
+    if (threadIdx.x == 0) *s_next = ld_relaxed_i32(slot);
+    __syncthreads();
+    const int q = *s_next;
+    return q < p.count_big ? q : -1;
+}
+
+// Runs the plan: solve(item index, team size, rank, barrier, partials) for
+// each system this CTA takes (team size 1: this CTA alone).
+template <typename Solve>
+__device__ __forceinline__ void run_batch_plan(const BatchPlan &p, int *sflag, int *s_next, Solve solve) {
+    if (blockIdx.x < (unsigned)(p.teams * p.team)) {
+        const unsigned team = blockIdx.x / p.team, rank = blockIdx.x % p.team;
+        unsigned tepoch = 0;
+        for (unsigned turn = 0;; ++turn) {
+            const int q = team_next(p, team, rank, tepoch, turn, sflag, s_next);
+            if (q < 0) break;
+            solve(p.order_big[q], (unsigned)p.team, rank, p.sbar + q,
+                  p.spart + (size_t)q * 2 * kMaxSums * p.team);
+        }
+    }
+    for (;;) {
+        if (threadIdx.x == 0) *s_next = (int)atomicAdd(&p.queue[0], 1u);
+        __syncthreads();
+        const int q = *s_next;
+        if (q >= p.count_small) break;
+        solve(p.order_small[q], 1u, 0u, (BarrierState *)nullptr, (double *)nullptr);
+    }
+}
+
+// Each system is solved by the same method as a single solve: by a team
+// (the same arithmetic as a solve with grid = team) or by one CTA alone
+// with CTA-wide barriers and reductions in shared memory.
 template <typename T, bool PC>
-__global__ void __launch_bounds__(kThreads, 1)
-    batch_kernel(const BatchItem<T> *items, const int *order, int count, unsigned *queue) {
+__global__ void __launch_bounds__(kThreads, 1) batch_kernel(const BatchItem<T> *items, BatchPlan plan) {
     using S = typename coef_of<T>::type;
     extern __shared__ unsigned char dsm[];
     __shared__ TileRing ring;
@@ -151,17 +191,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ unsigned seqs[kThreads];   // tile counters, kept across systems
     ring_init(&ring, ring_buffer(dsm));
     seqs[threadIdx.x] = 0;
-    uint64_t timeout = 2000000000ull;
-    for (;;) {
-        if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        const int q = s_next;
-        if (q >= count) break;
-        if (threadIdx.x == 0) item = items[order[q]];
+    uint64_t timeout = plan.timeout_ns;
+    run_batch_plan(plan, &sflag, &s_next, [&](int idx, unsigned nb, unsigned rk, BarrierState *bar, double *part) {
+        if (threadIdx.x == 0) item = items[idx];
         acct_reset(acct);   // includes the __syncthreads that publishes `item`
         timeout = item.ctl.timeout_ns;
         if (threadIdx.x == 0) {
-            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
+            GridSync *g = nb > 1 ? new (gs_slot.get()) GridSync(bar, part, nb, rk, red, &sflag, timeout, &ring, seqs)
+                                 : new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
             new (e_slot.get()) Engine<T, PC>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
         }
         __syncthreads();
@@ -170,17 +207,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         E.attach();
         run_fp64_solve(E, gs, item.ctl, acct, item.ctl.res);
         __syncthreads();
-    }
+    });
     ring_drain(&ring, seqs[kConsumers], seqs[0], timeout);
 }
 
 template <typename T, bool PC>
-cudaError_t launch_batch_pc(const BatchItem<T> *items, const int *order, int count, unsigned *queue, int grid,
-                            cudaStream_t st) {
+cudaError_t launch_batch_pc(const BatchItem<T> *items, const BatchPlan &plan, int grid, cudaStream_t st) {
     cudaError_t e = allow_ring((const void *)batch_kernel<T, PC>);
     if (e != cudaSuccess) return e;
-    batch_kernel<T, PC><<<grid, kThreads, kRingBytes, st>>>(items, order, count, queue);
-    return cudaGetLastError();
+    const BatchItem<T> *it = items;
+    BatchPlan p = plan;
+    void *args[] = {(void *)&it, (void *)&p};
+    if (plan.teams > 0)
+        return cudaLaunchCooperativeKernel((const void *)batch_kernel<T, PC>, dim3(grid), dim3(kThreads), args,
+                                           kRingBytes, st);
+    return cudaLaunchKernel((const void *)batch_kernel<T, PC>, dim3(grid), dim3(kThreads), args, kRingBytes, st);
 }
 
 template <typename T, bool PC>
@@ -221,7 +262,7 @@ int solve_blocks_per_sm_pc() {
 // ===========================================================================
 template <typename T32, typename T64, bool PC>
 __global__ void __launch_bounds__(kThreads, 1)
-    batch_refine_kernel(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue) {
+    batch_refine_kernel(const BatchItemR<T32, T64> *items, BatchPlan plan) {
     using S = typename coef_of<T32>::type;
     extern __shared__ unsigned char dsm[];
     __shared__ TileRing ring;
@@ -238,17 +279,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ unsigned seqs[kThreads];   // tile counters, kept across systems
     ring_init(&ring, ring_buffer(dsm));
     seqs[threadIdx.x] = 0;
-    uint64_t timeout = 2000000000ull;
-    for (;;) {
-        if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        const int q = s_next;
-        if (q >= count) break;
-        if (threadIdx.x == 0) item = items[order[q]];
+    uint64_t timeout = plan.timeout_ns;
+    run_batch_plan(plan, &sflag, &s_next, [&](int idx, unsigned nb, unsigned rk, BarrierState *bar, double *part) {
+        if (threadIdx.x == 0) item = items[idx];
         acct_reset(acct);
         timeout = item.ctl.timeout_ns;
         if (threadIdx.x == 0) {
-            GridSync *g = new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
+            GridSync *g = nb > 1 ? new (gs_slot.get()) GridSync(bar, part, nb, rk, red, &sflag, timeout, &ring, seqs)
+                                 : new (gs_slot.get()) GridSync(red, &sflag, timeout, &ring, seqs);
             new (e_slot.get()) Engine<T32, PC>(item.sys, item.ctl, *g, cbuf, btbuf, &acct);
             new (r_slot.get()) Refiner<T64, T32>(item.rv, *g, &acct);
         }
@@ -259,12 +297,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         E.attach();
         RefineOut o = refine_solve<T32, T64, PC>(E, R, item.ctl, item.rc);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (gs.bid == 0 && threadIdx.x == 0) {
             DevResult *res = item.ctl.res;
             res->flag = o.flag;
             res->j = 0;
             res->i = 0;
-            res->status = gs.ok ? 0 : kStatusTimeout;
+            res->status = gs.ok ? 0 : (gs.bar ? ld_relaxed_i32(&gs.bar->status) : kStatusTimeout);
+            if (!gs.ok && res->status == 0) res->status = kStatusTimeout;
             res->iter = o.iter;
             res->spmv = acct.spmv;
             res->outer = o.outer;
@@ -273,19 +312,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             res->bytes = acct.bytes;
             res->flops = acct.flops;
             for (int k = 0; k < 5; ++k) res->ops[k] = acct.ops[k];
+            res->ctas = (int32_t)nb;
         }
         __syncthreads();
-    }
+    });
     ring_drain(&ring, seqs[kConsumers], seqs[0], timeout);
 }
 
 template <typename T32, typename T64, bool PC>
-cudaError_t launch_batch_refine_pc(const BatchItemR<T32, T64> *items, const int *order, int count, unsigned *queue,
-                                int grid, cudaStream_t st) {
+cudaError_t launch_batch_refine_pc(const BatchItemR<T32, T64> *items, const BatchPlan &plan, int grid,
+                                   cudaStream_t st) {
     cudaError_t e = allow_ring((const void *)batch_refine_kernel<T32, T64, PC>);
     if (e != cudaSuccess) return e;
-    batch_refine_kernel<T32, T64, PC><<<grid, kThreads, kRingBytes, st>>>(items, order, count, queue);
-    return cudaGetLastError();
+    const BatchItemR<T32, T64> *it = items;
+    BatchPlan p = plan;
+    void *args[] = {(void *)&it, (void *)&p};
+    if (plan.teams > 0)
+        return cudaLaunchCooperativeKernel((const void *)batch_refine_kernel<T32, T64, PC>, dim3(grid),
+                                           dim3(kThreads), args, kRingBytes, st);
+    return cudaLaunchKernel((const void *)batch_refine_kernel<T32, T64, PC>, dim3(grid), dim3(kThreads), args,
+                            kRingBytes, st);
 }
 
 template <typename T32, typename T64, bool PC>
@@ -354,6 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         res->bytes = acct.bytes;
         res->flops = acct.flops;
         for (int q = 0; q < 5; ++q) res->ops[q] = acct.ops[q];
+        res->ctas = (int32_t)gridDim.x;
     }
 }
 
@@ -410,21 +457,19 @@ extern template cudaError_t launch_refine_pc<cfloat, cdouble, true>(const SysVie
 extern template int refine_blocks_per_sm_pc<float, double, true>();
 extern template int refine_blocks_per_sm_pc<cfloat, cdouble, true>();
 extern template cudaError_t launch_batch_refine_pc<float, double, true>(const BatchItemR<float, double> *,
-                                                                        const int *, int, unsigned *, int,
-                                                                        cudaStream_t);
+                                                                        const BatchPlan &, int, cudaStream_t);
 extern template cudaError_t launch_batch_refine_pc<cfloat, cdouble, true>(const BatchItemR<cfloat, cdouble> *,
-                                                                          const int *, int, unsigned *, int,
-                                                                          cudaStream_t);
+                                                                          const BatchPlan &, int, cudaStream_t);
 extern template int batch_refine_blocks_per_sm_pc<float, double, true>();
 extern template int batch_refine_blocks_per_sm_pc<cfloat, cdouble, true>();
 
 extern template cudaError_t launch_solve_pc<double, true>(const SysView<double> &, const SolveCtl &, int, cudaStream_t);
 extern template cudaError_t launch_solve_pc<cdouble, true>(const SysView<cdouble> &, const SolveCtl &, int,
                                                           cudaStream_t);
-extern template cudaError_t launch_batch_pc<double, true>(const BatchItem<double> *, const int *, int, unsigned *,
-                                                         int, cudaStream_t);
-extern template cudaError_t launch_batch_pc<cdouble, true>(const BatchItem<cdouble> *, const int *, int,
-                                                          unsigned *, int, cudaStream_t);
+extern template cudaError_t launch_batch_pc<double, true>(const BatchItem<double> *, const BatchPlan &, int,
+                                                         cudaStream_t);
+extern template cudaError_t launch_batch_pc<cdouble, true>(const BatchItem<cdouble> *, const BatchPlan &, int,
+                                                          cudaStream_t);
 extern template int solve_blocks_per_sm_pc<double, true>();
 extern template int solve_blocks_per_sm_pc<cdouble, true>();
 extern template int batch_blocks_per_sm_pc<double, true>();

@@ -30,6 +30,7 @@ EXPORTS = (
     "mlbicgstab_selftest_barrier_timeout", "mlbicgstab_spmv_qdot_noalloc",
     "mlbicgstab_set_n", "mlbicgstab_next_n", "mlbicgstab_solve_sequence",
     "mlbicgstab_autotune", "mlbicgstab_spmv_qdot_async", "mlbicgstab_get_perm",
+    "mlbicgstab_autotune_batch", "mlbicgstab_get_tuning", "mlbicgstab_set_tuning",
 )
 
 
@@ -56,10 +57,11 @@ class mlb_result(C.Structure):
                 ("spmv", C.c_int64), ("outer", C.c_int64),
                 ("err", C.c_double), ("true_relres", C.c_double),
                 ("kernel_ms", C.c_double), ("bytes", C.c_double),
-                ("ops", C.c_int64 * 5), ("flops", C.c_double)]
+                ("ops", C.c_int64 * 5), ("flops", C.c_double),
+                ("ctas", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "ops"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("ops", "reserved")}
         d["ops"] = dict(zip(("matvec", "dot", "saxpy", "scale", "norm"),
                             [int(v) for v in self.ops]))
         return d
@@ -77,7 +79,19 @@ class mlb_info(C.Structure):
 
 class mlb_tune_result(C.Structure):
     _fields_ = [("grid", C.c_int32), ("spt_cap", C.c_int32), ("us_per_iter", C.c_double),
-                ("default_us_per_iter", C.c_double), ("trials", C.c_int32), ("from_cache", C.c_int32)]
+                ("default_us_per_iter", C.c_double), ("trials", C.c_int32), ("from_cache", C.c_int32),
+                ("qd_fused", C.c_int32), ("reserved", C.c_int32), ("qd_us", C.c_double),
+                ("qd_default_us", C.c_double)]
+
+
+class mlb_tuning(C.Structure):
+    _fields_ = [("grid", C.c_int32), ("spt_cap", C.c_int32), ("batch_spt_cap", C.c_int32),
+                ("batch_team", C.c_int32), ("qd_fused", C.c_int32)]
+
+
+class mlb_batch_tune_result(C.Structure):
+    _fields_ = [("classes", C.c_int32), ("trials", C.c_int32), ("from_cache", C.c_int32),
+                ("team", C.c_int32), ("default_ms", C.c_double), ("tuned_ms", C.c_double)]
 
 
 class mlb_sequence_options(C.Structure):
@@ -144,6 +158,13 @@ def load(path: str | None = None):
                                               C.POINTER(mlb_result), P]
     lib.mlbicgstab_autotune.restype = C.c_int
     lib.mlbicgstab_autotune.argtypes = [P, C.c_int32, C.c_int32, C.POINTER(mlb_tune_result)]
+    lib.mlbicgstab_get_tuning.restype = C.c_int
+    lib.mlbicgstab_get_tuning.argtypes = [P, C.POINTER(mlb_tuning)]
+    lib.mlbicgstab_set_tuning.restype = C.c_int
+    lib.mlbicgstab_set_tuning.argtypes = [P, C.POINTER(mlb_tuning)]
+    lib.mlbicgstab_autotune_batch.restype = C.c_int
+    lib.mlbicgstab_autotune_batch.argtypes = [P, C.c_int32, C.c_double, C.c_int64, C.c_int32,
+                                              C.POINTER(mlb_batch_tune_result)]
     lib.mlbicgstab_spmv_qdot_noalloc.restype = C.c_int
     lib.mlbicgstab_spmv_qdot_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, C.c_int32,
                                                  P, P, C.c_int64, C.c_int32, P, P, P]
@@ -356,10 +377,40 @@ def mlbicgstab_solve_sequence(hs, bs, xs, tols, maxits, n0: int, step: int, n_mi
 
 
 def mlbicgstab_autotune(h: Handle, iters: int = 20, use_cache: bool = True) -> dict:
-    """Choose the CTA count and SpMV tile size of a handle by timing."""
+    """Choose the CTA count and SpMV tile size of a handle, and the columns
+    fused into its product's epilogue, by timing."""
     r = mlb_tune_result()
     _check(load().mlbicgstab_autotune(h.ptr, int(iters), 1 if use_cache else 0, C.byref(r)),
            "mlbicgstab_autotune")
+    return {f: getattr(r, f) for f, _ in r._fields_ if f != "reserved"}
+
+
+def mlbicgstab_get_tuning(h: Handle) -> dict:
+    """The handle's launch configuration (grid, spt_cap, batch_spt_cap, qd_fused)."""
+    t = mlb_tuning()
+    _check(load().mlbicgstab_get_tuning(h.ptr, C.byref(t)), "mlbicgstab_get_tuning")
+    return {f: getattr(t, f) for f, _ in t._fields_}
+
+
+def mlbicgstab_set_tuning(h: Handle, **kw) -> None:
+    """Set fields of the handle's launch configuration (the others kept)."""
+    cur = mlbicgstab_get_tuning(h)
+    unknown = set(kw) - set(cur)
+    if unknown:
+        raise TypeError(f"unknown tuning fields {sorted(unknown)}")
+    cur.update(kw)
+    t = mlb_tuning(**{k: int(v) for k, v in cur.items()})
+    _check(load().mlbicgstab_set_tuning(h.ptr, C.byref(t)), "mlbicgstab_set_tuning")
+
+
+def mlbicgstab_autotune_batch(hs, tol: float = 1e-10, maxit: int = 20000, use_cache: bool = True) -> dict:
+    """Choose the batch's team size and the tile cap of each size class of
+    handles by timing trial batches (A x = 1 solved to tol)."""
+    count = len(hs)
+    ptrs = (C.c_void_p * count)(*[h.ptr for h in hs])
+    r = mlb_batch_tune_result()
+    _check(load().mlbicgstab_autotune_batch(ptrs, count, float(tol), int(maxit), 1 if use_cache else 0,
+                                            C.byref(r)), "mlbicgstab_autotune_batch")
     return {f: getattr(r, f) for f, _ in r._fields_}
 
 

@@ -50,13 +50,15 @@ def test_struct_layout_matches_c_compiler(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mlb_matrix), sizeof(mlb_options),
-         sizeof(mlb_result), sizeof(mlb_info), sizeof(mlb_sequence_options), sizeof(mlb_tune_result));
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(mlb_options, stream),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mlb_matrix), sizeof(mlb_options),
+         sizeof(mlb_result), sizeof(mlb_info), sizeof(mlb_sequence_options), sizeof(mlb_tune_result),
+         sizeof(mlb_batch_tune_result), sizeof(mlb_tuning));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(mlb_options, stream),
          offsetof(mlb_options, timeout_ns), offsetof(mlb_result, ops),
          offsetof(mlb_options, precond), offsetof(mlb_info, precond),
          offsetof(mlb_info, n_active), offsetof(mlb_info, qd_kernel_ms),
-         offsetof(mlb_result, flops));
+         offsetof(mlb_result, flops), offsetof(mlb_result, ctas), offsetof(mlb_tune_result, qd_us),
+         offsetof(mlb_batch_tune_result, tuned_ms));
   return 0;
 }}''')
     exe = tmp_path / "layout"
@@ -66,12 +68,13 @@ int main(void) {{
     assert [int(v) for v in sizes.split()] == [
         C.sizeof(M.mlb_matrix), C.sizeof(M.mlb_options),
         C.sizeof(M.mlb_result), C.sizeof(M.mlb_info), C.sizeof(M.mlb_sequence_options),
-        C.sizeof(M.mlb_tune_result)]
+        C.sizeof(M.mlb_tune_result), C.sizeof(M.mlb_batch_tune_result), C.sizeof(M.mlb_tuning)]
     assert [int(v) for v in offs.split()] == [
         M.mlb_options.stream.offset, M.mlb_options.timeout_ns.offset,
         M.mlb_result.ops.offset, M.mlb_options.precond.offset,
         M.mlb_info.precond.offset, M.mlb_info.n_active.offset, M.mlb_info.qd_kernel_ms.offset,
-        M.mlb_result.flops.offset]
+        M.mlb_result.flops.offset, M.mlb_result.ctas.offset, M.mlb_tune_result.qd_us.offset,
+        M.mlb_batch_tune_result.tuned_ms.offset]
 
 
 def test_strerror_and_defaults(lib):
@@ -202,3 +205,16 @@ def test_autotune_validates_before_gpu(lib):
     assert lib.mlbicgstab_autotune(None, 20, 1, C.byref(r)) == M.MLB_ERR_ARG
     assert lib.mlbicgstab_autotune(C.c_void_p(1), 0, 1, C.byref(r)) == M.MLB_ERR_ARG
     assert lib.mlbicgstab_autotune(C.c_void_p(1), 20, 2, C.byref(r)) == M.MLB_ERR_ARG
+    rb = M.mlb_batch_tune_result()
+    hs = (C.c_void_p * 1)(1)
+    assert lib.mlbicgstab_autotune_batch(None, 1, 1e-8, 20, 1, C.byref(rb)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune_batch(hs, 0, 1e-8, 20, 1, C.byref(rb)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune_batch(hs, 1, -1.0, 20, 1, C.byref(rb)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune_batch(hs, 1, float("nan"), 20, 1, C.byref(rb)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune_batch(hs, 1, 1e-8, 0, 1, C.byref(rb)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune_batch(hs, 1, 1e-8, 10000001, 1, C.byref(rb)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune_batch(hs, 1, 1e-8, 20, 2, C.byref(rb)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_autotune_batch(hs, 1, 1e-8, 20, 1, None) == M.MLB_ERR_ARG
+    t = M.mlb_tuning()
+    assert lib.mlbicgstab_get_tuning(None, C.byref(t)) == M.MLB_ERR_ARG
+    assert lib.mlbicgstab_set_tuning(None, C.byref(t)) == M.MLB_ERR_ARG

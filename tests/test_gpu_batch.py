@@ -99,3 +99,88 @@ def test_batch_of_small_passes_is_race_free_and_deterministic():
         assert meta_k == runs[0][1]
         for a, b in zip(xs_k, runs[0][0]):
             np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------------- teams of CTAs in a batch --
+
+def _check_batch_teams(systems, team, precision=M.MLB_PREC_FP64, precond=M.MLB_PRECOND_NONE, n=4,
+                       tol=1e-10, maxit=6000, oracle_every=1):
+    """Each system's batch result equals the single solve with grid = the
+    CTAs that solved it in the batch (team size, or 1), bit for bit, and
+    agrees with the oracle."""
+    hs = [M.mlbicgstab_create(A, n=n, q_seed=0, precision=precision, precond=precond) for A in systems]
+    M.mlbicgstab_set_tuning(hs[0], batch_team=team)
+    bs = [W.row_sums(A) for A in systems]
+    xs = [np.zeros(A.n_rows) for A in systems]
+    res = M.mlbicgstab_solve_batch(hs, bs, xs, [tol] * len(hs), [maxit] * len(hs))
+    ctas = [r.ctas for r in res]
+    assert set(ctas) <= {1, team}
+    for k, (A, b, r, x) in enumerate(zip(systems, bs, res, xs)):
+        assert r.status == 0 and r.flag == 0 and r.true_relres < tol, (k, r.as_dict())
+        h1 = M.mlbicgstab_create(A, n=n, q_seed=0, precision=precision, precond=precond, grid=r.ctas)
+        assert M.mlbicgstab_info(h1)["grid"] == r.ctas
+        x1 = np.zeros(A.n_rows)
+        r1, _ = M.mlbicgstab_solve(h1, b, x1, tol, maxit)
+        assert (r.iter, r.outer, r.flag) == (r1.iter, r1.outer, r1.flag), (k, r.ctas)
+        np.testing.assert_array_equal(x, x1)
+        h1.destroy()
+        if k % oracle_every == 0:
+            pc = {}
+            if precond == M.MLB_PRECOND_ILU0:
+                pc = dict(ilu=O.ilu0(A))
+            ref = O.solve(A, b, np.zeros(A.n_rows), O.q_gauss(0, A.n_rows, n), maxit, tol, **pc)
+            assert ref.flag == 0
+            assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x), k
+    for h in hs:
+        h.destroy()
+    return ctas
+
+
+@pytest.mark.parametrize("team", [2, 4, 8])
+def test_batch_teams_fp64(team):
+    systems = [A for A, _ in W.batch_cd(20, seed=45, n_min=500, n_max=40000)]
+    ctas = _check_batch_teams(systems, team, oracle_every=3)
+    assert ctas.count(team) >= 3 and ctas.count(1) >= 3
+
+
+def test_batch_without_teams_is_one_cta_per_system():
+    systems = [A for A, _ in W.batch_cd(8, seed=46, n_min=10000, n_max=30000)]
+    ctas = _check_batch_teams(systems, 1, oracle_every=4)
+    assert ctas == [1] * len(systems)
+
+
+def test_batch_more_large_systems_than_teams():
+    """Twice as many team systems as teams: teams take several systems in
+    turn (the slots of the turns alternate)."""
+    systems = [A for A, _ in W.batch_cd(40, seed=47, n_min=17000, n_max=20000)]
+    ctas = _check_batch_teams(systems, 8, maxit=4000, oracle_every=8)
+    assert ctas.count(8) == len(systems)   # 40 systems, 19 teams of 8 CTAs
+
+
+def test_batch_teams_refined_and_ilu0():
+    systems = [A for A, _ in W.batch_cd(10, seed=48, n_min=2000, n_max=30000)]
+    ctas = _check_batch_teams(systems, 4, precision=M.MLB_PREC_FP32_REFINED, oracle_every=3)
+    assert 4 in ctas
+    # natural-order ILU(0) systems stay on one CTA; the multicolour ones
+    # go to teams
+    ctas = _check_batch_teams(systems, 4, precond=M.MLB_PRECOND_ILU0, oracle_every=3)
+    assert set(ctas) == {1}
+    ctas = _check_batch_teams(systems, 4, precond=M.MLB_PRECOND_ILU0_MC, oracle_every=100)
+    assert 4 in ctas
+
+
+def test_batch_teams_complex():
+    systems = [W.helmholtz3d_c(m, m, 8, k=2.0) for m in (12, 20, 36, 40)]
+    hs = [M.mlbicgstab_create(A, n=4, q_seed=0, AH=W.conj_transpose(A)) for A in systems]
+    M.mlbicgstab_set_tuning(hs[0], batch_team=4)
+    bs = [W.row_sums(A) for A in systems]
+    xs = [np.zeros(A.n_rows, dtype=complex) for A in systems]
+    res = M.mlbicgstab_solve_batch(hs, bs, xs, [1e-10] * 4, [6000] * 4)
+    assert any(r.ctas == 4 for r in res)
+    for A, b, r, x in zip(systems, bs, res, xs):
+        assert r.status == 0 and r.flag == 0 and r.true_relres < 1e-10
+        h1 = M.mlbicgstab_create(A, n=4, q_seed=0, AH=W.conj_transpose(A), grid=r.ctas)
+        x1 = np.zeros(A.n_rows, dtype=complex)
+        r1, _ = M.mlbicgstab_solve(h1, b, x1, 1e-10, 6000)
+        assert r1.iter == r.iter
+        np.testing.assert_array_equal(x, x1)

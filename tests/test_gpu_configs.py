@@ -90,8 +90,11 @@ def test_batch_512_uneven_systems():
         ref = O.solve(A, b, np.zeros(A.n_rows), O.q_gauss(0, A.n_rows, 4), 20000, 1e-10)
         assert ref.flag == 0
         assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x), k
-        h1 = M.mlbicgstab_create(A, n=4, q_seed=0, grid=1)
+        # the same arithmetic as a single solve on as many CTAs as solved it
+        # in the batch (one, or a team for the large systems)
+        h1 = M.mlbicgstab_create(A, n=4, q_seed=0, grid=res[k].ctas)
         x1 = np.zeros(A.n_rows)
         r1, _ = M.mlbicgstab_solve(h1, b, x1, 1e-10, 20000)
         assert r1.iter == res[k].iter
         np.testing.assert_array_equal(x1, x)
+    assert {r.ctas for r in res} == {1, 4}
