@@ -38,6 +38,8 @@
 //     (A u)^H (A u) and (A u)^H u (step 38).
 #pragma once
 
+#include <type_traits>
+
 #include "mlb_device.cuh"
 #include "mlb_tiles.cuh"
 
@@ -995,7 +997,7 @@ struct Engine {
     // ------------------------------------------------------------------
 
     // r = b - A x, g_0 = r; sums ||b||^2, ||r||^2, q_1^H r.
-    __device__ __noinline__ bool ph_residual(double &bb, double &rr, S &qr, bool write_g0) {
+    __device__ __forceinline__ bool ph_residual_body(double &bb, double &rr, S &qr, bool write_g0) {
         constexpr int K = 2 + DS;
         ACC acc[K];
 #pragma unroll
@@ -1135,7 +1137,7 @@ struct Engine {
     }
 
     // w_slot = A g_slot; returns c = q_qcol^H w.
-    __device__ __noinline__ bool ph_spmv_c(int sl, int qcol, S &cval) {
+    __device__ __forceinline__ bool ph_spmv_c_body(int sl, int qcol, S &cval) {
         constexpr int K = DS;
         ACC acc[K];
 #pragma unroll
@@ -1157,7 +1159,7 @@ struct Engine {
     }
 
     // z = A u (u held in r); sums z^H z, z^H u.
-    __device__ __noinline__ bool ph_spmv_z(double &zz, S &zu) {
+    __device__ __forceinline__ bool ph_spmv_z_body(double &zz, S &zu) {
         constexpr int K = 1 + DS;
         ACC acc[K];
 #pragma unroll
@@ -1181,7 +1183,7 @@ struct Engine {
 
     // x += alpha g_sl, r -= alpha w_sl; sums ||r||^2, q_qcol^H r and
     // (when f0) f_1^H r.
-    __device__ __noinline__ bool ph_alpha(S alpha, int sl, int qcol, bool f0, double &rr, S &qr, S &fr) {
+    __device__ __forceinline__ bool ph_alpha_body(S alpha, int sl, int qcol, bool f0, double &rr, S &qr, S &fr) {
         constexpr int K = 1 + 2 * DS;
         const T a = to_t<T>(alpha), na = to_t<T>(-alpha);
         const bool hq = qcol >= 0;
@@ -1228,7 +1230,7 @@ struct Engine {
     }
 
     // x += omega u, r = u - omega z (u in r); sums ||r||^2, q_1^H r.
-    __device__ __noinline__ bool ph_omega(S omega, double &rr, S &qr) {
+    __device__ __forceinline__ bool ph_omega_body(S omega, double &rr, S &qr) {
         constexpr int K = 1 + DS;
         const T om = to_t<T>(omega), nom = to_t<T>(-omega);
         const T *in[4] = {sys.x, sys.r, sys.z, Qc(0)};
@@ -1262,7 +1264,7 @@ struct Engine {
     }
 
     // z_w = r + bt0 * w_sl (in place); sums q_qcol^H z_w.
-    __device__ __noinline__ bool ph_w_first(S bt0, int sl, int qcol, S &d) {
+    __device__ __forceinline__ bool ph_w_first_body(S bt0, int sl, int qcol, S &d) {
         constexpr int K = DS;
         const T b0 = to_t<T>(bt0);
         T *wp = Wc(sl);
@@ -1286,7 +1288,7 @@ struct Engine {
     }
 
     // z_w += bts * w_s (in place); sums q_qcol^H z_w.
-    __device__ __noinline__ bool ph_w_round(S bts, int s, int sl, int qcol, S &d) {
+    __device__ __forceinline__ bool ph_w_round_body(S bts, int s, int sl, int qcol, S &d) {
         constexpr int K = DS;
         const T bb = to_t<T>(bts);
         T *wp = Wc(sl);
@@ -1316,7 +1318,7 @@ struct Engine {
     //   g = bt[sl] g_sl;  g += bt[t] g_t for t = sl+1..n-1;  g = z_w - g/omega
     // sums f_1^H g when with_f.  The first kMaxInputs-4 columns g_t come
     // through the tile pipeline, any further ones by direct loads.
-    __device__ __noinline__ bool ph_w_last(bool first, int sl, S inv_omega, bool with_f, S &d) {
+    __device__ __forceinline__ bool ph_w_last_body(bool first, int sl, S inv_omega, bool with_f, S &d) {
         constexpr int K = DS;
         const int n = sys.n;
         const int last = n - 1;
@@ -1378,7 +1380,7 @@ struct Engine {
     }
 
     // g_sl += beta g_s; sums f_fcol^H g_sl when fcol >= 0 (else no sum).
-    __device__ __noinline__ bool ph_f_round(S beta, int s, int sl, int fcol, S &d) {
+    __device__ __forceinline__ bool ph_f_round_body(S beta, int s, int sl, int fcol, S &d) {
         const T bb = to_t<T>(beta);
         T *gp = Gc(sl);
         const T *in[3] = {gp, Gc(s), fcol >= 0 ? Fc(fcol) : nullptr};
@@ -1412,7 +1414,7 @@ struct Engine {
     }
 
     // Block 0: g_sl = r + beta g_0; sums f_fcol^H g_sl when fcol >= 0.
-    __device__ __noinline__ bool ph_g_j0(S beta, int sl, int fcol, S &d) {
+    __device__ __forceinline__ bool ph_g_j0_body(S beta, int sl, int fcol, S &d) {
         const T bb = to_t<T>(beta);
         T *gp = Gc(sl);
         const T *in[3] = {sys.r, Gc(0), fcol >= 0 ? Fc(fcol) : nullptr};
@@ -1452,6 +1454,30 @@ struct Engine {
         if (rec && ctl.err_hist && iter < ctl.hist_cap && gs.bid == 0 && threadIdx.x == 0)
             ctl.err_hist[iter] = err;
     }
+
+    // Each pass is inlined into the real FP64 engine (3 % less time per
+    // iteration at 128^3: no saves and restores of registers around the
+    // calls, whose stack sits in L2 beside the tile ring) and called out
+    // of line in the others (the FP32 engine runs 1 % faster so, and their
+    // kernels compile in a fraction of the time).
+    static constexpr bool kInlinePasses = std::is_same<T, double>::value;
+#define MLB_PASS(name, params, args)                                        \
+    __device__ __noinline__ bool name##_ool params { return name##_body args; } \
+    __device__ __forceinline__ bool name params {                            \
+        if constexpr (kInlinePasses) return name##_body args;                \
+        else return name##_ool args;                                         \
+    }
+    MLB_PASS(ph_residual, (double &bb, double &rr, S &qr, bool write_g0), (bb, rr, qr, write_g0))
+    MLB_PASS(ph_spmv_c, (int sl, int qcol, S &cval), (sl, qcol, cval))
+    MLB_PASS(ph_spmv_z, (double &zz, S &zu), (zz, zu))
+    MLB_PASS(ph_alpha, (S alpha, int sl, int qcol, bool f0, double &rr, S &qr, S &fr), (alpha, sl, qcol, f0, rr, qr, fr))
+    MLB_PASS(ph_omega, (S omega, double &rr, S &qr), (omega, rr, qr))
+    MLB_PASS(ph_w_first, (S bt0, int sl, int qcol, S &d), (bt0, sl, qcol, d))
+    MLB_PASS(ph_w_round, (S bts, int s, int sl, int qcol, S &d), (bts, s, sl, qcol, d))
+    MLB_PASS(ph_w_last, (bool first, int sl, S inv_omega, bool with_f, S &d), (first, sl, inv_omega, with_f, d))
+    MLB_PASS(ph_f_round, (S beta, int s, int sl, int fcol, S &d), (beta, s, sl, fcol, d))
+    MLB_PASS(ph_g_j0, (S beta, int sl, int fcol, S &d), (beta, sl, fcol, d))
+#undef MLB_PASS
 
     // ------------------------------------------------------------------
     // one call of the method (Algorithm 7.1, M = I) from the current x
