@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(HERE, "libmlbicgstab.so")
 HEADER = os.path.join(ROOT, "include", "mlbicgstab.h")
-SOURCES = ["mlb_kernels.cu", "mlb_kernels_ilu.cu", "mlb_kernels_bsr.cu", "mlb_api.cu", "mlb_noalloc.cu",
-           "mlb_ilu.cu"]
+SOURCES = ["mlb_kernels.cu", "mlb_kernels_ilu.cu", "mlb_kernels_cplx.cu", "mlb_kernels_bsr.cu", "mlb_api.cu",
+           "mlb_noalloc.cu", "mlb_ilu.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",

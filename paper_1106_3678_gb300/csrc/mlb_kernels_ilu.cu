@@ -1,19 +1,14 @@
-// Solve, batch and refined kernels with the ILU(0) preconditioner passes
-// (see mlb_solve.cuh), in a translation unit of their own so that they compile
-// in parallel with the rest of the library.
+// Real FP64 solve and batch kernels and the refined kernels with the ILU(0)
+// preconditioner passes (see mlb_solve.cuh), in a translation unit of their
+// own so that they compile in parallel with the rest of the library.
 #include "mlb_solve.cuh"
 
 namespace mlb {
 
 template cudaError_t launch_solve_pc<double, true>(const SysView<double> &, const SolveCtl &, int, cudaStream_t);
-template cudaError_t launch_solve_pc<cdouble, true>(const SysView<cdouble> &, const SolveCtl &, int, cudaStream_t);
 template cudaError_t launch_batch_pc<double, true>(const BatchItem<double> *, const BatchPlan &, int, cudaStream_t);
-template cudaError_t launch_batch_pc<cdouble, true>(const BatchItem<cdouble> *, const BatchPlan &, int,
-                                                    cudaStream_t);
 template int solve_blocks_per_sm_pc<double, true>();
-template int solve_blocks_per_sm_pc<cdouble, true>();
 template int batch_blocks_per_sm_pc<double, true>();
-template int batch_blocks_per_sm_pc<cdouble, true>();
 template cudaError_t launch_refine_pc<float, double, true>(const SysView<float> &, const RefView<double> &,
                                                            const SolveCtl &, const RefCtl &, int, cudaStream_t);
 template cudaError_t launch_refine_pc<cfloat, cdouble, true>(const SysView<cfloat> &, const RefView<cdouble> &,

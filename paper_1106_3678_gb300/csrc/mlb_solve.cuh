@@ -463,6 +463,14 @@ extern template cudaError_t launch_batch_refine_pc<cfloat, cdouble, true>(const 
 extern template int batch_refine_blocks_per_sm_pc<float, double, true>();
 extern template int batch_refine_blocks_per_sm_pc<cfloat, cdouble, true>();
 
+// Instantiated in mlb_kernels_cplx.cu.
+extern template cudaError_t launch_solve_pc<cdouble, false>(const SysView<cdouble> &, const SolveCtl &, int,
+                                                            cudaStream_t);
+extern template int solve_blocks_per_sm_pc<cdouble, false>();
+extern template cudaError_t launch_batch_pc<cdouble, false>(const BatchItem<cdouble> *, const BatchPlan &, int,
+                                                            cudaStream_t);
+extern template int batch_blocks_per_sm_pc<cdouble, false>();
+
 extern template cudaError_t launch_solve_pc<double, true>(const SysView<double> &, const SolveCtl &, int, cudaStream_t);
 extern template cudaError_t launch_solve_pc<cdouble, true>(const SysView<cdouble> &, const SolveCtl &, int,
                                                           cudaStream_t);
