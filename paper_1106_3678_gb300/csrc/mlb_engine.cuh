@@ -722,18 +722,29 @@ struct Engine {
     __device__ __forceinline__ bool reduce(double (&v)[K]) { return gs.template reduce<K>(v); }
     __device__ __forceinline__ bool sync() { return gs.sync(); }
 
-    __device__ __forceinline__ void tile_pass(TilePass &P, const T *const *in, int ni) {
-        P.ni = ni;
-        for (int i = 0; i < ni; ++i) P.in[i] = in[i];
-        P.tc = tile_chunks_for(ni);
-        P.c_lo = c_lo;
-        P.c_hi = c_hi;
+    // Inputs of a streaming pass: only the producer lane reads the list (it
+    // issues the copies); every thread derives the tile geometry from the
+    // count, so the consumers keep it in registers.
+    struct PassIn {
+        const T *const *in;
+        int ni;
+    };
+    __device__ __forceinline__ TileGeom geom(const PassIn &P) const {
+        return TileGeom{tile_chunks_for(P.ni), c_lo, c_hi};
+    }
+    // The producer lane's copy descriptor.
+    __device__ __forceinline__ void tile_pass(TilePass &D, const PassIn &P) const {
+        D.ni = P.ni;
+        for (int i = 0; i < P.ni; ++i) D.in[i] = P.in[i];
+        D.tc = tile_chunks_for(P.ni);
+        D.c_lo = c_lo;
+        D.c_hi = c_hi;
     }
 
     // Streaming pass through the tile pipeline: fn(chunk, stage, k, acc)
     // for every chunk of this CTA, then a team reduction of K sums.
     template <int K, typename Fn>
-    __device__ __forceinline__ bool tsum(const TilePass &P, Fn fn, double (&out)[K]) {
+    __device__ __forceinline__ bool tsum(const PassIn &P, Fn fn, double (&out)[K]) {
         ACC acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = ACC(0);
@@ -742,13 +753,15 @@ struct Engine {
         const uint64_t to = gs.timeout_ns;
         if ((threadIdx.x >> 5) == kConsumerWarps) {
             if ((threadIdx.x & 31) == 0) {
+                TilePass D;
+                tile_pass(D, P);
                 unsigned sq = gs.seq();
-                okw = produce(ring, P, sq, to);
+                okw = produce(ring, D, sq, to);
                 gs.seq() = sq;
             }
         } else {
             unsigned sq = gs.seq();
-            okw = consume(ring, P, sq, to, [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k, acc); });
+            okw = consume(ring, geom(P), sq, to, [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k, acc); });
             gs.seq() = sq;
         }
         if (!okw) gs.ring->failed = 1;
@@ -761,19 +774,21 @@ struct Engine {
     // Streaming pass with no inner product: the tiles, then only a team
     // barrier (the next pass gathers what this one wrote), no reduction.
     template <typename Fn>
-    __device__ __forceinline__ bool tpass(const TilePass &P, Fn fn) {
+    __device__ __forceinline__ bool tpass(const PassIn &P, Fn fn) {
         bool okw = true;
         TileRing *const ring = gs.ring;
         const uint64_t to = gs.timeout_ns;
         if ((threadIdx.x >> 5) == kConsumerWarps) {
             if ((threadIdx.x & 31) == 0) {
+                TilePass D;
+                tile_pass(D, P);
                 unsigned sq = gs.seq();
-                okw = produce(ring, P, sq, to);
+                okw = produce(ring, D, sq, to);
                 gs.seq() = sq;
             }
         } else {
             unsigned sq = gs.seq();
-            okw = consume(ring, P, sq, to, [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k); });
+            okw = consume(ring, geom(P), sq, to, [&](int64_t ch, const unsigned char *st, int k) { fn(ch, st, k); });
             gs.seq() = sq;
         }
         if (!okw) gs.ring->failed = 1;
@@ -1194,9 +1209,8 @@ struct Engine {
         const int iq = 4, iff = hq ? 5 : 4;
         T *const xo = sys.x;
         T *const ro = sys.r;
-        TilePass P;
-        tile_pass(P, in, ni);
-        const int tc = P.tc;
+        const PassIn P{in, ni};
+        const int tc = tile_chunks_for(P.ni);
         double v[K];
         bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
             Pack<T> xx = lds<T>(st, tc, 0, k), gg = lds<T>(st, tc, 1, k), rv = lds<T>(st, tc, 2, k),
@@ -1236,9 +1250,8 @@ struct Engine {
         const T *in[4] = {sys.x, sys.r, sys.z, Qc(0)};
         T *const xo = sys.x;
         T *const ro = sys.r;
-        TilePass P;
-        tile_pass(P, in, 4);
-        const int tc = P.tc;
+        const PassIn P{in, 4};
+        const int tc = tile_chunks_for(P.ni);
         double v[K];
         bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
             Pack<T> xx = lds<T>(st, tc, 0, k), uu = lds<T>(st, tc, 1, k), zz = lds<T>(st, tc, 2, k),
@@ -1269,9 +1282,8 @@ struct Engine {
         const T b0 = to_t<T>(bt0);
         T *wp = Wc(sl);
         const T *in[3] = {sys.r, wp, Qc(qcol)};
-        TilePass P;
-        tile_pass(P, in, 3);
-        const int tc = P.tc;
+        const PassIn P{in, 3};
+        const int tc = tile_chunks_for(P.ni);
         double v[K];
         bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
             Pack<T> rv = lds<T>(st, tc, 0, k), ww = lds<T>(st, tc, 1, k), qq = lds<T>(st, tc, 2, k);
@@ -1293,9 +1305,8 @@ struct Engine {
         const T bb = to_t<T>(bts);
         T *wp = Wc(sl);
         const T *in[3] = {wp, Wc(s), Qc(qcol)};
-        TilePass P;
-        tile_pass(P, in, 3);
-        const int tc = P.tc;
+        const PassIn P{in, 3};
+        const int tc = tile_chunks_for(P.ni);
         double v[K];
         bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
             Pack<T> zw = lds<T>(st, tc, 0, k), w2 = lds<T>(st, tc, 1, k), qq = lds<T>(st, tc, 2, k);
@@ -1342,9 +1353,8 @@ struct Engine {
         const T *const Gb = sys.G;
         const int64_t ldv = sys.ld;
         const S *const btl = bt;
-        TilePass P;
-        tile_pass(P, in, ni);
-        const int tc = P.tc;
+        const PassIn P{in, ni};
+        const int tc = tile_chunks_for(P.ni);
         double v[K];
         bool okk = tsum<K>(P, [&](int64_t ch, const unsigned char *st, int k, ACC *acc) {
             Pack<T> zw = lds<T>(st, tc, 0, k), g = lds<T>(st, tc, 1, k), o = lds<T>(st, tc, 2, k);
@@ -1384,9 +1394,8 @@ struct Engine {
         const T bb = to_t<T>(beta);
         T *gp = Gc(sl);
         const T *in[3] = {gp, Gc(s), fcol >= 0 ? Fc(fcol) : nullptr};
-        TilePass P;
-        tile_pass(P, in, fcol >= 0 ? 3 : 2);
-        const int tc = P.tc;
+        const PassIn P{in, fcol >= 0 ? 3 : 2};
+        const int tc = tile_chunks_for(P.ni);
         if (fcol < 0) {
             bool okk = tpass(P, [&](int64_t ch, const unsigned char *st, int k) {
                 Pack<T> g = lds<T>(st, tc, 0, k), g2 = lds<T>(st, tc, 1, k);
@@ -1418,9 +1427,8 @@ struct Engine {
         const T bb = to_t<T>(beta);
         T *gp = Gc(sl);
         const T *in[3] = {sys.r, Gc(0), fcol >= 0 ? Fc(fcol) : nullptr};
-        TilePass P;
-        tile_pass(P, in, fcol >= 0 ? 3 : 2);
-        const int tc = P.tc;
+        const PassIn P{in, fcol >= 0 ? 3 : 2};
+        const int tc = tile_chunks_for(P.ni);
         if (fcol < 0) {
             bool okk = tpass(P, [&](int64_t ch, const unsigned char *st, int k) {
                 Pack<T> rv = lds<T>(st, tc, 0, k), g2 = lds<T>(st, tc, 1, k), g;

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if ((threadIdx.x >> 5) == kConsumerWarps) {
             if ((threadIdx.x & 31) == 0) ok = produce(&ring, P, sq, to);
         } else {
-            ok = consume(&ring, P, sq, to, [&](int64_t, const unsigned char *st, int k) {
+            ok = consume(&ring, TileGeom{tc, c_lo, c_hi}, sq, to, [&](int64_t, const unsigned char *st, int k) {
                 const Pack<T> yy = lds<T>(st, tc, 0, k);
 #pragma unroll
                 for (int m = 0; m < G; ++m) {

@@ -180,6 +180,13 @@ struct TilePass {
     __device__ __forceinline__ int ntiles() const { return (int)((c_hi - c_lo + tc - 1) / tc); }
 };
 
+// Geometry of a streaming pass as the consumers see it: chunks per tile
+// and the CTA's chunk range.
+struct TileGeom {
+    int tc;
+    int64_t c_lo, c_hi;
+};
+
 __device__ __forceinline__ int tile_chunks_for(int ni) {
     int tc = kStageBytes / (16 * ni);
     if (tc > kTileChunks) tc = kTileChunks;
@@ -220,13 +227,10 @@ __device__ __forceinline__ bool produce(TileRing *R, const TilePass &P, unsigned
 // for each chunk k of the tile owned by this thread (chunk k is read from
 // stage + i*tc*16 + k*16 for input i), then release the stage.
 template <typename Fn>
-__device__ __forceinline__ bool consume(TileRing *R, const TilePass &P, unsigned &seq, uint64_t timeout_ns, Fn fn) {
-    // Everything the loop needs is copied into registers first: the
-    // consumers' generic stores could alias the pass descriptor, so reading
-    // it inside the loop would reload it from memory after every store.
-    const int nt = P.ntiles();
-    const int tc = P.tc;
-    const int64_t c_lo = P.c_lo, c_hi = P.c_hi;
+__device__ __forceinline__ bool consume(TileRing *R, const TileGeom g, unsigned &seq, uint64_t timeout_ns, Fn fn) {
+    const int tc = g.tc;
+    const int64_t c_lo = g.c_lo, c_hi = g.c_hi;
+    const int nt = (int)((c_hi - c_lo + tc - 1) / tc);
     unsigned char *const buf = R->buf;
     unsigned sq = seq;
     const int tid = threadIdx.x;   // < kConsumers
