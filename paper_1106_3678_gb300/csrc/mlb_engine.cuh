@@ -66,8 +66,11 @@ enum { OP_MATVEC = 0, OP_DOT = 1, OP_SAXPY = 2, OP_SCALE = 3, OP_NORM = 4 };
 struct Acct {
     int64_t ops[5];   // Table 4.3 categories of the current inner call
     int64_t spmv;     // all sparse products of the solve
-    double bytes;     // algorithmic bytes of the solve
-    double flops;     // algorithmic floating-point operations of the solve
+    // Algorithmic bytes and floating-point operations of the solve, kept
+    // in integer arithmetic: thread 0 adds to them in every pass, on the
+    // pass's critical path, where FP64 adds would cost ~60 cycles each.
+    int64_t bytes;
+    int64_t flops;
     // Scalars evaluated by thread 0 and read by every thread after a
     // __syncthreads: FP64 division and square root are costly on this GPU,
     // so they are not repeated by all threads.  Calls rotate through the
@@ -665,13 +668,13 @@ struct Engine {
         if (threadIdx.x == 0) {
             acct->ops[which] += cnt;
             constexpr bool cx_ = is_cx<T>::value;
-            const double N = (double)sys.N;
-            double f;
-            if (which == OP_MATVEC) f = (cx_ ? 8.0 : 2.0) * (double)sys.nnz;
-            else if (which == OP_SCALE) f = (cx_ ? 6.0 : 1.0) * N;
-            else if (which == OP_NORM) f = (cx_ ? 4.0 : 2.0) * N;
-            else f = (cx_ ? 8.0 : 2.0) * N;
-            acct->flops += (double)cnt * f;
+            const int64_t N = sys.N;
+            int64_t f;
+            if (which == OP_MATVEC) f = (cx_ ? 8 : 2) * sys.nnz;
+            else if (which == OP_SCALE) f = (cx_ ? 6 : 1) * N;
+            else if (which == OP_NORM) f = (cx_ ? 4 : 2) * N;
+            else f = (cx_ ? 8 : 2) * N;
+            acct->flops += cnt * f;
         }
     }
 
@@ -705,15 +708,15 @@ struct Engine {
     __device__ __forceinline__ T *Wc(int k) const { return sys.W + (int64_t)k * sys.ld; }
 
     __device__ __forceinline__ void vbytes(int nvec) {
-        if (threadIdx.x == 0) acct->bytes += (double)nvec * (double)sys.N * sizeof(T);
+        if (threadIdx.x == 0) acct->bytes += nvec * sys.N * (int64_t)sizeof(T);
     }
     __device__ __forceinline__ void sbytes(int nextra) {
         // SpMV: entries (values, and a column index per stored entry of EW
         // values), row_ptr-equivalent, x read once, y written once, plus
         // `nextra` epilogue vectors.
         if (threadIdx.x == 0) {
-            acct->bytes += (double)sys.nnz * (sizeof(T) + 4.0 / EW) + 4.0 * (double)(sys.N + 1) +
-                           (2.0 + nextra) * (double)sys.N * sizeof(T);
+            acct->bytes += sys.nnz * (int64_t)sizeof(T) + sys.nnz / EW * 4 + 4 * (sys.N + 1) +
+                           (2 + nextra) * sys.N * (int64_t)sizeof(T);
             acct->spmv++;
         }
     }
@@ -956,8 +959,8 @@ struct Engine {
             if (!gs.wait()) return false;
         }
         if (threadIdx.x == 0) {   // factors and row data once, v read, out written and re-read
-            acct->bytes += (double)M.nnz * (sizeof(T) + 4) + (double)sys.N * (8 + 4 + 8 + 3 * sizeof(T));
-            acct->flops += (is_cx<T>::value ? 8.0 : 2.0) * (double)M.nnz;
+            acct->bytes += M.nnz * (int64_t)(sizeof(T) + 4) + sys.N * (int64_t)(8 + 4 + 8 + 3 * sizeof(T));
+            acct->flops += (is_cx<T>::value ? 8 : 2) * M.nnz;
         }
         return true;
     }
@@ -1093,7 +1096,7 @@ struct Engine {
         bb = v[0];
         rr = v[1];
         qr = mk_coef<T>(v + 2);
-        if (threadIdx.x == 0) acct->bytes += (double)sys.N * (sizeof(TW) + 5.0 * sizeof(T));
+        if (threadIdx.x == 0) acct->bytes += sys.N * (int64_t)(sizeof(TW) + 5 * sizeof(T));
         return true;
     }
 
@@ -1147,7 +1150,7 @@ struct Engine {
         qr = mk_coef<T>(v + 1);
         fr = mk_coef<T>(v + 1 + DS);
         if (threadIdx.x == 0)
-            acct->bytes += (double)sys.N * (sizeof(TW) + (1.0 + (qv ? 1 : 0) + (fv ? 1 : 0)) * sizeof(T));
+            acct->bytes += sys.N * (int64_t)(sizeof(TW) + (1 + (qv ? 1 : 0) + (fv ? 1 : 0)) * sizeof(T));
         return true;
     }
 

@@ -95,9 +95,9 @@ struct Refiner {
         bb = acc[0];
         rr = acc[1];
         if (threadIdx.x == 0) {
-            acct->bytes += (double)v.nnz * (sizeof(T64) + 4.0 / EW) + 4.0 * (double)(v.N + 1) +
-                           3.0 * (double)v.N * sizeof(T64);
-            acct->flops += (DS == 2 ? 8.0 : 2.0) * (double)v.nnz + (DS == 2 ? 10.0 : 5.0) * (double)v.N;
+            acct->bytes += v.nnz * (int64_t)sizeof(T64) + v.nnz / EW * 4 + 4 * (v.N + 1) +
+                           3 * v.N * (int64_t)sizeof(T64);
+            acct->flops += (DS == 2 ? 8 : 2) * v.nnz + (DS == 2 ? 10 : 5) * v.N;
             acct->spmv++;
         }
         return true;
@@ -130,7 +130,7 @@ struct Refiner {
         }
         fence_proxy_async_global();
         if (threadIdx.x == 0)
-            acct->bytes += (double)v.N * (2.0 * sizeof(T64) + (zero ? 2.0 : 1.0) * sizeof(T32));
+            acct->bytes += v.N * (int64_t)(2 * sizeof(T64) + (zero ? 2 : 1) * sizeof(T32));
         return gs.sync();
     }
 
@@ -142,7 +142,7 @@ struct Refiner {
         uint4 *dst = reinterpret_cast<uint4 *>(save ? v.xbest : v.x);
         const uint4 *src = reinterpret_cast<const uint4 *>(save ? v.x : v.xbest);
         for (int64_t ch = c_start; ch < c_hi; ch += kConsumers) dst[ch] = src[ch];
-        if (threadIdx.x == 0) acct->bytes += 2.0 * (double)v.N * sizeof(T64);
+        if (threadIdx.x == 0) acct->bytes += 2 * v.N * (int64_t)sizeof(T64);
         return gs.sync();
     }
 

@@ -66,8 +66,8 @@ __device__ void run_fp64_solve(Engine<T, PC, EW> &E, GridSync &gs, const SolveCt
         res->outer = outer;
         res->err = o.err;
         res->true_relres = true_rel;
-        res->bytes = acct.bytes;
-        res->flops = acct.flops;
+        res->bytes = (double)acct.bytes;
+        res->flops = (double)acct.flops;
         for (int q = 0; q < 5; ++q) res->ops[q] = ops_last[q];
         res->ctas = (int32_t)gs.nblocks;
     }
@@ -90,8 +90,8 @@ __device__ __forceinline__ void acct_reset(Acct &acct) {
     if (threadIdx.x == 0) {
         for (int q = 0; q < 5; ++q) acct.ops[q] = 0;
         acct.spmv = 0;
-        acct.bytes = 0.0;
-        acct.flops = 0.0;
+        acct.bytes = 0;
+        acct.flops = 0;
     }
     __syncthreads();
 }
@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             res->outer = o.outer;
             res->err = o.err;
             res->true_relres = o.err;
-            res->bytes = acct.bytes;
-            res->flops = acct.flops;
+            res->bytes = (double)acct.bytes;
+            res->flops = (double)acct.flops;
             for (int k = 0; k < 5; ++k) res->ops[k] = acct.ops[k];
             res->ctas = (int32_t)nb;
         }
@@ -397,8 +397,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         res->outer = o.outer;
         res->err = o.err;
         res->true_relres = o.err;
-        res->bytes = acct.bytes;
-        res->flops = acct.flops;
+        res->bytes = (double)acct.bytes;
+        res->flops = (double)acct.flops;
         for (int q = 0; q < 5; ++q) res->ops[q] = acct.ops[q];
         res->ctas = (int32_t)gridDim.x;
     }
