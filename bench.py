@@ -108,7 +108,7 @@ DEFAULT = "cd3d128_n4_fp64"
 # proportion to the iterations, so a full launch is scaled by its
 # iteration count.  Set to None whenever the kernel changes until it is
 # captured again.
-NCU_DRAM_BYTES_PER_ITER = (136.330260e9 + 31.289359e9) / 300
+NCU_DRAM_BYTES_PER_ITER = None
 VARIANTS = ["spmv_qdot_cd3d128", "cd3d128_n1_fp64", "cd3d128_n8_fp64", "cd3d128_n16_fp64",
             "cd3d128_n4_fp64_ilu0", "cd3d128_n4_refined_ilu0", "cd3d128_n4_fp64_ilu0mc", "cd3d128_n4_refined_ilu0mc",
             "reservoir_n8_fp64", "reservoir_n8_fp64_ilu0", "reservoir_n8_refined_ilu0",

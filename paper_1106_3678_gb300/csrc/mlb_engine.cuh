@@ -1466,28 +1466,34 @@ struct Engine {
             ctl.err_hist[iter] = err;
     }
 
-    // Each pass is inlined into the FP64 engines (4 % less time per
-    // iteration for real 128^3 and complex 256x256x64 systems: no saves and
-    // restores of registers around the calls, whose stack sits in L2 beside
-    // the tile ring) and called out of line in the FP32 ones (they run 1 %
-    // faster so, and their kernels compile in a fraction of the time).
-    static constexpr bool kInlinePasses = std::is_same<T, double>::value || std::is_same<T, cdouble>::value;
-#define MLB_PASS(name, params, args)                                        \
+    // The streaming passes are inlined into the FP64 engines without the
+    // ILU(0) passes: no saves and restores of registers around the calls,
+    // whose stack sits in L2 beside the tile ring.  The SELL product passes
+    // stay out of line in the real engine (inlined, their register demand
+    // spreads over the whole loop: n = 1 took 223 instead of 193 us per
+    // iteration at 128^3) but are inlined in the complex one (1 % faster).
+    // All passes of the FP32 engines stay out of line (1 % faster so, and
+    // their kernels compile in a fraction of the time), and so do those of
+    // the ILU(0) engines (inlining cost the natural-order solve 4 %).
+    static constexpr bool kInlinePasses =
+        (std::is_same<T, double>::value || std::is_same<T, cdouble>::value) && !PC;
+    static constexpr bool kInlineProducts = std::is_same<T, cdouble>::value && !PC;
+#define MLB_PASS(name, inl, params, args)                                   \
     __device__ __noinline__ bool name##_ool params { return name##_body args; } \
     __device__ __forceinline__ bool name params {                            \
-        if constexpr (kInlinePasses) return name##_body args;                \
+        if constexpr (inl) return name##_body args;                          \
         else return name##_ool args;                                         \
     }
-    MLB_PASS(ph_residual, (double &bb, double &rr, S &qr, bool write_g0), (bb, rr, qr, write_g0))
-    MLB_PASS(ph_spmv_c, (int sl, int qcol, S &cval), (sl, qcol, cval))
-    MLB_PASS(ph_spmv_z, (double &zz, S &zu), (zz, zu))
-    MLB_PASS(ph_alpha, (S alpha, int sl, int qcol, bool f0, double &rr, S &qr, S &fr), (alpha, sl, qcol, f0, rr, qr, fr))
-    MLB_PASS(ph_omega, (S omega, double &rr, S &qr), (omega, rr, qr))
-    MLB_PASS(ph_w_first, (S bt0, int sl, int qcol, S &d), (bt0, sl, qcol, d))
-    MLB_PASS(ph_w_round, (S bts, int s, int sl, int qcol, S &d), (bts, s, sl, qcol, d))
-    MLB_PASS(ph_w_last, (bool first, int sl, S inv_omega, bool with_f, S &d), (first, sl, inv_omega, with_f, d))
-    MLB_PASS(ph_f_round, (S beta, int s, int sl, int fcol, S &d), (beta, s, sl, fcol, d))
-    MLB_PASS(ph_g_j0, (S beta, int sl, int fcol, S &d), (beta, sl, fcol, d))
+    MLB_PASS(ph_residual, kInlineProducts, (double &bb, double &rr, S &qr, bool write_g0), (bb, rr, qr, write_g0))
+    MLB_PASS(ph_spmv_c, kInlineProducts, (int sl, int qcol, S &cval), (sl, qcol, cval))
+    MLB_PASS(ph_spmv_z, kInlineProducts, (double &zz, S &zu), (zz, zu))
+    MLB_PASS(ph_alpha, kInlinePasses, (S alpha, int sl, int qcol, bool f0, double &rr, S &qr, S &fr), (alpha, sl, qcol, f0, rr, qr, fr))
+    MLB_PASS(ph_omega, kInlinePasses, (S omega, double &rr, S &qr), (omega, rr, qr))
+    MLB_PASS(ph_w_first, kInlinePasses, (S bt0, int sl, int qcol, S &d), (bt0, sl, qcol, d))
+    MLB_PASS(ph_w_round, kInlinePasses, (S bts, int s, int sl, int qcol, S &d), (bts, s, sl, qcol, d))
+    MLB_PASS(ph_w_last, kInlinePasses, (bool first, int sl, S inv_omega, bool with_f, S &d), (first, sl, inv_omega, with_f, d))
+    MLB_PASS(ph_f_round, kInlinePasses, (S beta, int s, int sl, int fcol, S &d), (beta, s, sl, fcol, d))
+    MLB_PASS(ph_g_j0, kInlinePasses, (S beta, int sl, int fcol, S &d), (beta, sl, fcol, d))
 #undef MLB_PASS
 
     // ------------------------------------------------------------------
