@@ -1466,17 +1466,17 @@ struct Engine {
             ctl.err_hist[iter] = err;
     }
 
-    // The streaming passes are inlined into the FP64 engines without the
-    // ILU(0) passes: no saves and restores of registers around the calls,
-    // whose stack sits in L2 beside the tile ring.  The SELL product passes
-    // stay out of line in the real engine (inlined, their register demand
-    // spreads over the whole loop: n = 1 took 223 instead of 193 us per
-    // iteration at 128^3) but are inlined in the complex one (1 % faster).
-    // All passes of the FP32 engines stay out of line (1 % faster so, and
-    // their kernels compile in a fraction of the time), and so do those of
-    // the ILU(0) engines (inlining cost the natural-order solve 4 %).
-    static constexpr bool kInlinePasses =
-        (std::is_same<T, double>::value || std::is_same<T, cdouble>::value) && !PC;
+    // The streaming passes are inlined into the FP64 engines: no saves and
+    // restores of registers around the calls, whose stack sits in L2
+    // beside the tile ring.  The SELL product passes stay out of line in
+    // the real engines (inlined, their register demand spreads over the
+    // whole loop: n = 1 took 223 instead of 193 us per iteration at 128^3,
+    // and the natural-order ILU(0) solve 4 % longer) but are inlined in the
+    // complex one without ILU(0) (1 % faster).  The FP32 engines call every
+    // pass out of line (their kernels then compile in a fraction of the
+    // time; inlining gained 2 % only where the refined mode does not
+    // converge without a preconditioner).
+    static constexpr bool kInlinePasses = std::is_same<T, double>::value || std::is_same<T, cdouble>::value;
     static constexpr bool kInlineProducts = std::is_same<T, cdouble>::value && !PC;
 #define MLB_PASS(name, inl, params, args)                                   \
     __device__ __noinline__ bool name##_ool params { return name##_body args; } \
