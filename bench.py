@@ -104,11 +104,11 @@ DEFAULT = "cd3d128_n4_fp64"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the solve
 # kernel on the headline workload, from one ncu capture of a 300-iteration
-# launch of the current kernel: 136.33 GB + 31.29 GB.  Traffic grows in
+# launch of the current kernel: 136.46 GB + 30.39 GB.  Traffic grows in
 # proportion to the iterations, so a full launch is scaled by its
 # iteration count.  Set to None whenever the kernel changes until it is
 # captured again.
-NCU_DRAM_BYTES_PER_ITER = None
+NCU_DRAM_BYTES_PER_ITER = (136.456225e9 + 30.393382e9) / 300
 VARIANTS = ["spmv_qdot_cd3d128", "cd3d128_n1_fp64", "cd3d128_n8_fp64", "cd3d128_n16_fp64",
             "cd3d128_n4_fp64_ilu0", "cd3d128_n4_refined_ilu0", "cd3d128_n4_fp64_ilu0mc", "cd3d128_n4_refined_ilu0mc",
             "reservoir_n8_fp64", "reservoir_n8_fp64_ilu0", "reservoir_n8_refined_ilu0",
