@@ -989,9 +989,6 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     MLB_CUDA(cudaSetDevice(h->device));
     if (on_device && (!is_device_ptr(b, h->device) || !is_device_ptr(x, h->device))) return MLB_ERR_ARG;
     cudaStream_t st = h->stream;
-    const size_t nb = (size_t)h->N * h->esize;
-    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const cudaMemcpyKind outk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (err_hist && hist_cap > h->err_cap) {
         if (h->err_hist) cudaFree(h->err_hist);
         h->err_hist = nullptr;
