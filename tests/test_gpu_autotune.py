@@ -110,6 +110,23 @@ def test_every_fused_column_count_matches_oracle(n, cplx):
     h.destroy()
 
 
+@pytest.mark.parametrize("n,cplx", [(8, False), (4, False), (3, True)])
+def test_every_fused_column_count_fp32_copies(n, cplx):
+    """The same for the FP32 product on a refined handle's copies."""
+    from tests.test_gpu_parity import fp32_product_vs_oracle
+    A = W.helmholtz3d_c(10, 9, 7) if cplx else W.cd3d_lognormal(23)
+    h = M.mlbicgstab_create(A, n=n, q_seed=2, precision=M.MLB_PREC_FP32_REFINED)
+    for ne in (1, 2, 4):
+        if ne > n or (cplx and ne > 2):
+            continue
+        M.mlbicgstab_set_tuning(h, qd_fused=ne)
+        fp32_product_vs_oracle(h, A, n, cplx, 10 + ne)
+    r = M.mlbicgstab_autotune(h, iters=5, use_cache=False)
+    assert r["qd_fused"] in (1, 2, 4) and r["qd_us"] <= r["qd_default_us"]
+    fp32_product_vs_oracle(h, A, n, cplx, 20)
+    h.destroy()
+
+
 def test_fused_column_choice_above_active_n_falls_back():
     A = W.cd3d_lognormal(16)
     h = M.mlbicgstab_create(A, n=8, q_seed=0)

@@ -199,10 +199,16 @@ def test_spmv_qdot_fp32_copies_of_a_refined_handle(n, cplx):
     values.  y: each row sums at most w FP32 products, within gamma32_w of
     the exact sum of |a||x| (Higham, Thm 3.1, u = 2^-24), the oracle within
     gamma64_w.  d: the propagated y difference plus gamma32_N |q|^T |y|."""
-    import torch
     A = W.helmholtz3d_c(10, 9, 7) if cplx else W.cd3d_lognormal(23)
     h = M.mlbicgstab_create(A, n=n, q_seed=2, precision=M.MLB_PREC_FP32_REFINED)
-    rng = np.random.default_rng(3 + n)
+    fp32_product_vs_oracle(h, A, n, cplx, 3 + n)
+
+
+def fp32_product_vs_oracle(h, A, n, cplx, seed):
+    """The FP32 fused product of a refined handle against the oracle's
+    product of the FP32-rounded values, at the bounds described above."""
+    import torch
+    rng = np.random.default_rng(seed)
     x = rng.standard_normal(A.n_rows) + (1j * rng.standard_normal(A.n_rows) if cplx else 0)
     dt32, npt32 = (torch.complex64, np.complex64) if cplx else (torch.float32, np.float32)
     x32 = x.astype(npt32)
