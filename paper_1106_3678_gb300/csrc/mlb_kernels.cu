@@ -250,10 +250,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     using ACC = typename real_of<T>::type;
     extern __shared__ unsigned char dsm[];
     __shared__ TileRing ring;
+    // Programmatic dependent launch: the next product on the stream may be
+    // scheduled as soon as every CTA of this one runs.  Its producer warp
+    // streams only constant data (A and Q) into its own shared memory, so
+    // it starts at once; every other thread waits for this grid to
+    // complete before touching x, y, d or the shared partial sums, ticket
+    // and status words (and the producer lane's later accesses follow the
+    // consumers' through the CTA barriers).  The next product's set-up and
+    // first tiles so overlap this one's tail.
+    asm volatile("griddepcontrol.launch_dependents;");
     ring_init(&ring, ring_buffer(dsm));
     int64_t s_lo, s_hi;
     own_range(sys.nslices, gridDim.x, blockIdx.x, s_lo, s_hi);
-    soff_load(&ring, sys.slice_ptr, s_lo, s_hi);
+    soff_load(&ring, sys.slice_ptr, s_lo, s_hi);   // constant data
+    if ((threadIdx.x >> 5) != kConsumerWarps) asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint64_t to = 2000000000ull;
     const int n = sys.n;
     double *const scratch = reinterpret_cast<double *>(ring.buf);   // the stages, free between passes
@@ -353,9 +363,18 @@ static cudaError_t launch_qd_tiled_ne(const SysView<T> &sys, int spt, const T *x
     cudaError_t e = allow_ring((const void *)spmv_qdot_tiled_kernel<T, NE>);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev, st);
     if (e != cudaSuccess) return e;
-    spmv_qdot_tiled_kernel<T, NE>
-        <<<grid, kThreads, kRingBytes, st>>>(sys, spt, x, y, yout, partials, status, ticket, d);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kRingBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, spmv_qdot_tiled_kernel<T, NE>, sys, spt, x, y, yout, partials, status, ticket,
+                              d);
 }
 
 template <typename T>
