@@ -1290,18 +1290,18 @@ int qd_enqueue(mlb_handle *h, int32_t vt, const void *x, void *y, double *d, boo
     const int spt = std::min(slices_per_tile(h->maxw, vb, ne), h->spt_cap);
     cudaError_t e;
     if (narrow && cplx)
-        e = launch_spmv_qdot_tiled<cfloat>(make_view32<cfloat>(h), ne, spt, (const cfloat *)x, (cfloat *)h->r32,
+        e = launch_spmv_qdot_tiled<cfloat>(make_view32<cfloat>(h), ne, h->maxw, spt, (const cfloat *)x, (cfloat *)h->r32,
                                            (cfloat *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
                                            st);
     else if (narrow)
-        e = launch_spmv_qdot_tiled<float>(make_view32<float>(h), ne, spt, (const float *)x, (float *)h->r32,
+        e = launch_spmv_qdot_tiled<float>(make_view32<float>(h), ne, h->maxw, spt, (const float *)x, (float *)h->r32,
                                           (float *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev, st);
     else if (cplx)
-        e = launch_spmv_qdot_tiled<cdouble>(make_view<cdouble>(h), ne, spt, (const cdouble *)x, (cdouble *)h->r,
+        e = launch_spmv_qdot_tiled<cdouble>(make_view<cdouble>(h), ne, h->maxw, spt, (const cdouble *)x, (cdouble *)h->r,
                                             (cdouble *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
                                             st);
     else
-        e = launch_spmv_qdot_tiled<double>(make_view<double>(h), ne, spt, (const double *)x, (double *)h->r,
+        e = launch_spmv_qdot_tiled<double>(make_view<double>(h), ne, h->maxw, spt, (const double *)x, (double *)h->r,
                                            (double *)y, h->qd_partials, grid, h->qd_status, h->qd_ticket, d, ev,
                                            st);
     if (e != cudaSuccess) {

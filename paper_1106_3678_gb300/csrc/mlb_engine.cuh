@@ -300,15 +300,17 @@ __device__ __noinline__ T sell_slice_sum_wide(const int32_t *cp, const T *vp, in
 // and the only global loads on a warp's critical path are the gathers.
 // The epilogue's stores are fenced for later bulk (async-proxy) reads.
 // EW = 3: the 3x3-block storage (see sell_slice_sum3); slice offsets and
-// widths then count blocks.  Returns false when a tile wait timed out.
-template <int NE, int EW = 1, typename T, typename Fin, typename AccArr>
+// widths then count blocks.  Slices up to PW entries wide take the
+// pipelined path (PW registers of gathered x per thread), wider ones a
+// direct loop.  Returns false when a tile wait timed out.
+template <int NE, int EW = 1, int PW = 8, typename T, typename Fin, typename AccArr>
 __device__ __forceinline__ bool sell_spmv(TileRing *R, unsigned &pseq, unsigned &cseq, uint64_t timeout_ns,
                                           int64_t s_lo, int64_t s_hi, int spt, const int64_t *slice_ptr,
                                           const int32_t *scol, const T *sval, const T *xin,
                                           const T *const (&epi)[NE > 0 ? NE : 1], int lane, Fin fin,
                                           AccArr &acc) {
     static_assert(EW == 1 || EW == 3, "scalar entries or 3x3 blocks");
-    constexpr int kPipeW = 8;   // slices up to this width take the pipelined path
+    constexpr int kPipeW = PW;
     constexpr int NEA = NE > 0 ? NE : 1;
     const int cw = threadIdx.x >> 5;
     const SliceOffsets off(R, slice_ptr, s_lo, s_hi);

@@ -130,9 +130,11 @@ inline int qd_fused_columns(int n, bool cplx, bool narrow) {
     if (n > 4 && !cplx && !narrow) return 1;
     return n >= 2 ? 2 : 1;
 }
+// maxw: the widest slice (entries per row), which selects the pipelined
+// width of the product.
 template <typename T>
-cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int ne, int spt, const T *x, T *y, T *yout,
-                                   double *partials, int grid, int *status, unsigned *ticket, double *d,
+cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int ne, int64_t maxw, int spt, const T *x, T *y,
+                                   T *yout, double *partials, int grid, int *status, unsigned *ticket, double *d,
                                    cudaEvent_t ev, cudaStream_t st);
 
 // ILU(0) preconditioner, host side (mlb_ilu.cu).  Factors of A in A's

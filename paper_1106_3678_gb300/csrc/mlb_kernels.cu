@@ -238,7 +238,7 @@ __device__ __forceinline__ void cta_sums(const ACC (&acc)[NV], int nv, double *s
     __syncthreads();   // scratch (the stages) is reused by the next pass
 }
 
-template <typename T, int NE>
+template <typename T, int NE, int PW>
 __global__ void __launch_bounds__(kThreads, 1)
     spmv_qdot_tiled_kernel(SysView<T> sys, int spt, const T *x, T *y, T *yout, double *partials, int *status,
                            unsigned *ticket, double *d) {
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int m = 0; m < NE; ++m) epi[m] = sys.Q + (int64_t)m * sys.ld;
         const int64_t nrows = sys.N;
         const bool keep = n > NE;   // later passes read y back
-        ok = sell_spmv<NE>(&ring, sq, sq, to, s_lo, s_hi, spt, sys.slice_ptr, sys.scol, sys.sval, x, epi,
+        ok = sell_spmv<NE, 1, PW>(&ring, sq, sq, to, s_lo, s_hi, spt, sys.slice_ptr, sys.scol, sys.sval, x, epi,
                            threadIdx.x & 31,
                            [=](int64_t row, T v, const T (&e)[NE], ACC (&a)[NE * DS]) {
                                if (keep) y[row] = v;                // padded copy
@@ -356,11 +356,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <typename T, int NE>
-static cudaError_t launch_qd_tiled_ne(const SysView<T> &sys, int spt, const T *x, T *y, T *yout, double *partials,
-                                      int grid, int *status, unsigned *ticket, double *d, cudaEvent_t ev,
-                                      cudaStream_t st) {
-    cudaError_t e = allow_ring((const void *)spmv_qdot_tiled_kernel<T, NE>);
+template <typename T, int NE, int PW>
+static cudaError_t launch_qd_tiled_pw(const SysView<T> &sys, int spt, const T *x, T *y, T *yout,
+                                      double *partials, int grid, int *status, unsigned *ticket, double *d,
+                                      cudaEvent_t ev, cudaStream_t st) {
+    cudaError_t e = allow_ring((const void *)spmv_qdot_tiled_kernel<T, NE, PW>);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev, st);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -373,23 +373,36 @@ static cudaError_t launch_qd_tiled_ne(const SysView<T> &sys, int spt, const T *x
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, spmv_qdot_tiled_kernel<T, NE>, sys, spt, x, y, yout, partials, status, ticket,
-                              d);
+    return cudaLaunchKernelEx(&cfg, spmv_qdot_tiled_kernel<T, NE, PW>, sys, spt, x, y, yout, partials, status,
+                              ticket, d);
+}
+
+// The pipelined width of the product: 7 when no slice is wider (two
+// registers of gathered x fewer than 8: 61 against 65 us per FP64 product
+// at 128^3, n = 4, 7-point stencil), else 8.
+template <typename T, int NE>
+static cudaError_t launch_qd_tiled_ne(const SysView<T> &sys, int64_t maxw, int spt, const T *x, T *y, T *yout,
+                                      double *partials, int grid, int *status, unsigned *ticket, double *d,
+                                      cudaEvent_t ev, cudaStream_t st) {
+    if (maxw <= 7)
+        return launch_qd_tiled_pw<T, NE, 7>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
+    return launch_qd_tiled_pw<T, NE, 8>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
 }
 
 template <typename T>
-cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int ne, int spt, const T *x, T *y, T *yout,
-                                   double *partials, int grid, int *status, unsigned *ticket, double *d,
+cudaError_t launch_spmv_qdot_tiled(const SysView<T> &sys, int ne, int64_t maxw, int spt, const T *x, T *y,
+                                   T *yout, double *partials, int grid, int *status, unsigned *ticket, double *d,
                                    cudaEvent_t ev, cudaStream_t st) {
     constexpr int DS = dslots<T>();
     if (ne < 1 || ne > sys.n || (ne != 1 && ne != 2 && ne != 4) || (DS == 2 && ne > 2))
         return cudaErrorInvalidValue;
     if constexpr (DS == 1) {
         if (ne == 4)
-            return launch_qd_tiled_ne<T, 4>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
+            return launch_qd_tiled_ne<T, 4>(sys, maxw, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
     }
-    if (ne == 2) return launch_qd_tiled_ne<T, 2>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
-    return launch_qd_tiled_ne<T, 1>(sys, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
+    if (ne == 2)
+        return launch_qd_tiled_ne<T, 2>(sys, maxw, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
+    return launch_qd_tiled_ne<T, 1>(sys, maxw, spt, x, y, yout, partials, grid, status, ticket, d, ev, st);
 }
 
 // ===========================================================================
@@ -434,17 +447,17 @@ template cudaError_t launch_ahq<double>(const int64_t *, const int32_t *, const 
                                         const double *, double *, int, cudaStream_t);
 template cudaError_t launch_ahq<cdouble>(const int64_t *, const int32_t *, const cdouble *, int64_t, int64_t,
                                          const cdouble *, cdouble *, int, cudaStream_t);
-template cudaError_t launch_spmv_qdot_tiled<double>(const SysView<double> &, int, int, const double *, double *,
-                                                    double *, double *, int, int *, unsigned *, double *,
-                                                    cudaEvent_t, cudaStream_t);
-template cudaError_t launch_spmv_qdot_tiled<cdouble>(const SysView<cdouble> &, int, int, const cdouble *, cdouble *,
-                                                     cdouble *, double *, int, int *, unsigned *, double *,
-                                                     cudaEvent_t, cudaStream_t);
-template cudaError_t launch_spmv_qdot_tiled<float>(const SysView<float> &, int, int, const float *, float *,
-                                                   float *, double *, int, int *, unsigned *, double *,
+template cudaError_t launch_spmv_qdot_tiled<double>(const SysView<double> &, int, int64_t, int, const double *,
+                                                    double *, double *, double *, int, int *, unsigned *,
+                                                    double *, cudaEvent_t, cudaStream_t);
+template cudaError_t launch_spmv_qdot_tiled<cdouble>(const SysView<cdouble> &, int, int64_t, int,
+                                                     const cdouble *, cdouble *, cdouble *, double *, int, int *,
+                                                     unsigned *, double *, cudaEvent_t, cudaStream_t);
+template cudaError_t launch_spmv_qdot_tiled<float>(const SysView<float> &, int, int64_t, int, const float *,
+                                                   float *, float *, double *, int, int *, unsigned *, double *,
                                                    cudaEvent_t, cudaStream_t);
-template cudaError_t launch_spmv_qdot_tiled<cfloat>(const SysView<cfloat> &, int, int, const cfloat *, cfloat *,
-                                                    cfloat *, double *, int, int *, unsigned *, double *,
+template cudaError_t launch_spmv_qdot_tiled<cfloat>(const SysView<cfloat> &, int, int64_t, int, const cfloat *,
+                                                    cfloat *, cfloat *, double *, int, int *, unsigned *, double *,
                                                     cudaEvent_t, cudaStream_t);
 template cudaError_t launch_refine<float, double>(const SysView<float> &, const RefView<double> &,
                                                   const SolveCtl &, const RefCtl &, int, cudaStream_t);
