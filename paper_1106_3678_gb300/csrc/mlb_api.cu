@@ -302,6 +302,7 @@ SysView<T> make_view(const mlb_handle *h) {
     v.sval = (const T *)h->sval;
     set_spt(v.spt, h->maxw, sizeof(T), h->spt_cap, h->ew);
     v.ew = h->ew;
+    v.narrow_rows = h->maxw <= 7 ? 1 : 0;
     v.Q = (const T *)h->Q;
     v.F = (const T *)h->F;
     v.G = (T *)h->G;
@@ -348,6 +349,7 @@ SysView<T32> make_view32(const mlb_handle *h) {
     v.sval = (const T32 *)h->sval32;
     set_spt(v.spt, h->maxw, sizeof(T32), h->spt_cap, h->ew);
     v.ew = h->ew;
+    v.narrow_rows = h->maxw <= 7 ? 1 : 0;
     v.Q = (const T32 *)h->Q32;
     v.F = (const T32 *)h->F32;
     v.G = (T32 *)h->G32;
