@@ -815,9 +815,11 @@ struct Engine {
         }
         unsigned sq = gs.seq();   // issued (producer lane) or consumed (consumers) tiles
         bool okw;
-        // FP32 engines: a pipelined width of 7 where the rows allow it (two
-        // registers fewer); the FP64 engines keep 8 (no gain at 7)
-        if constexpr (is_narrow<T>::value) {
+        // FP32 and complex engines: a pipelined width of 7 where the rows
+        // allow it (gathered x registers fewer: the refined solve 3 %, the
+        // complex one 3.5 % less time per iteration); the real FP64 engine
+        // keeps 8 (no gain at 7)
+        if constexpr (is_narrow<T>::value || is_cx<T>::value) {
             if (sys.narrow_rows)
                 okw = sell_spmv<NE, EW, 7>(gs.ring, sq, sq, gs.timeout_ns, s_lo, s_hi, sys.spt[NE], sys.slice_ptr,
                                            sys.scol, sys.sval, xin, epi, threadIdx.x & 31, fin, acc);
