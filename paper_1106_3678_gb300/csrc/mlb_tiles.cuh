@@ -170,14 +170,14 @@ __device__ __forceinline__ unsigned char *ring_buffer(unsigned char *dsm) {
     return (unsigned char *)(((uintptr_t)dsm + 127) & ~(uintptr_t)127);
 }
 
-// A streaming pass over the chunk range [c_lo, c_hi) of this CTA: `ni`
-// inputs of 16-byte chunks, tiles of `tc` chunks per input.
+// The producer lane's copy descriptor of a streaming pass over the chunk
+// range [c_lo, c_hi) of this CTA: `ni` inputs of 16-byte chunks, tiles of
+// `tc` chunks per input.
 struct TilePass {
     const void *in[kMaxInputs];
     int ni;
     int tc;
     int64_t c_lo, c_hi;
-    __device__ __forceinline__ int ntiles() const { return (int)((c_hi - c_lo + tc - 1) / tc); }
 };
 
 // Geometry of a streaming pass as the consumers see it: chunks per tile
