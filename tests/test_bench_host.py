@@ -34,3 +34,12 @@ def test_pairs_name_known_workloads_and_converged_rule():
     assert bench._converged({"flags": [0, 1], "true_relres": [1e-11, 9e-11]}, 1e-10) is False
     assert bench._converged({"flags": [0], "true_relres": [2e-10]}, 1e-10) is False
     assert bench._converged({"flags": [0], "true_relres_max": 5e-11}, 1e-10) is True
+
+
+def test_fused_column_rule_mirrors_the_library_rule():
+    # the rule documented with mlb_tuning.qd_fused in include/mlbicgstab.h
+    assert bench._qd_rule(4, False) == 4 and bench._qd_rule(4, False, True) == 4
+    assert bench._qd_rule(8, False) == 1 and bench._qd_rule(16, False) == 1
+    assert bench._qd_rule(8, False, True) == 2 and bench._qd_rule(16, False, True) == 2
+    assert bench._qd_rule(4, True) == 2 and bench._qd_rule(3, False) == 2
+    assert bench._qd_rule(1, False) == 1 and bench._qd_rule(1, True) == 1
