@@ -362,6 +362,21 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count,
                            const int64_t *maxit, mlb_result *res);
 
 /*
+ * The work plan mlbicgstab_solve_batch uses (host only, no GPU work): for
+ * `count` systems with N[s] rows, nnz[s] stored entries and preconditioner
+ * precond[s] (MLB_PRECOND_*), teams of `team` CTAs (the batch's
+ * batch_team) and `slots` co-resident CTAs (SMs x CTAs per SM of the batch
+ * kernel), ctas[s] = CTAs that will solve system s (1, or the team size);
+ * order = the team-solved systems (*nbig of them), then the others, each
+ * list largest first; *teams = teams formed, *grid = CTAs launched.
+ * MLB_ERR_ARG for a null pointer, count < 1, team < 1, slots < 1, N < 1 or
+ * nnz < 0.
+ */
+int mlbicgstab_batch_plan(const int64_t *N, const int64_t *nnz, const int32_t *precond, int32_t count,
+                          int32_t team, int32_t slots, int32_t *ctas, int32_t *order, int32_t *nbig,
+                          int32_t *teams, int32_t *grid);
+
+/*
  * Use the first n shadow vectors in the solves that follow
  * (1 <= n <= the n the handle was created with; MLB_ERR_ARG otherwise).
  * The handle's Q(:,1:n) and F(:,1:n-1) = A^H Q(:,1:n-1) are exactly the

@@ -1064,6 +1064,47 @@ int mlbicgstab_solve(mlb_handle *h, const void *b, void *x, int32_t on_device, d
     return MLB_OK;
 }
 
+int mlbicgstab_batch_plan(const int64_t *N, const int64_t *nnz, const int32_t *precond, int32_t count,
+                          int32_t team, int32_t slots, int32_t *ctas, int32_t *order, int32_t *nbig,
+                          int32_t *teams, int32_t *grid) {
+    if (!N || !nnz || !precond || count <= 0 || team < 1 || slots < 1 || !ctas || !order || !nbig || !teams ||
+        !grid)
+        return MLB_ERR_ARG;
+    for (int32_t s = 0; s < count; ++s)
+        if (N[s] < 1 || nnz[s] < 0) return MLB_ERR_ARG;
+    // Estimated work w = (nnz + N) N^(1/3); systems of at least
+    // kTeamMinRows rows per team CTA whose w exceeds kTeamShare of the
+    // average per CTA go to teams, the others to single CTAs; each list
+    // largest first (longest-processing-time order).  Natural-order ILU(0)
+    // systems stay on one CTA: their triangular solves take one barrier
+    // per level, which a team pays in global memory (measured: the 512-
+    // system ILU(0) batch 2.20 s with teams of 4, 1.96 s without).
+    const int tm = std::max(1, std::min(team, slots));
+    std::vector<double> w(count);
+    double wsum = 0.0;
+    for (int s = 0; s < count; ++s) {
+        w[s] = (double)(nnz[s] + N[s]) * std::cbrt((double)N[s]);
+        wsum += w[s];
+    }
+    std::vector<int> big, small;
+    for (int s = 0; s < count; ++s) {
+        const bool t = tm > 1 && precond[s] != MLB_PRECOND_ILU0 && N[s] >= (int64_t)kTeamMinRows * tm &&
+                       w[s] > kTeamShare * wsum / slots;
+        (t ? big : small).push_back(s);
+        ctas[s] = t ? tm : 1;
+    }
+    auto by_work = [&](int a, int c) { return w[a] > w[c]; };
+    std::stable_sort(big.begin(), big.end(), by_work);
+    std::stable_sort(small.begin(), small.end(), by_work);
+    int k = 0;
+    for (int s : big) order[k++] = s;
+    for (int s : small) order[k++] = s;
+    *nbig = (int32_t)big.size();
+    *teams = std::min<int>((int)big.size(), slots / tm);
+    *grid = std::min(slots, *teams * tm + (int)small.size());
+    return MLB_OK;
+}
+
 int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *const *b, void *const *x,
                            int32_t on_device, const double *tol, const int64_t *maxit, mlb_result *res) {
     if (!hs || count <= 0 || !b || !x || !tol || !maxit || !res) return MLB_ERR_ARG;
@@ -1090,32 +1131,20 @@ int mlbicgstab_solve_batch(mlb_handle *const *hs, int32_t count, const void *con
                                     : batch_refine_blocks_per_sm<float, double>())
                             : (cplx ? batch_blocks_per_sm<cdouble>() : batch_blocks_per_sm<double>());
     if (bps < 1) return MLB_ERR_CUDA;
-    // Work plan: estimated work w = (nnz + N) N^(1/3); systems of at least
-    // kTeamMinRows rows per team CTA whose w exceeds kTeamShare of the
-    // average per CTA go to teams, the others to single CTAs; each list
-    // largest first (longest-processing-time order).  Natural-order ILU(0)
-    // systems stay on one CTA: their triangular solves take one barrier
-    // per level, which a team pays in global memory (measured: the 512-
-    // system ILU(0) batch 2.20 s with teams of 4, 1.96 s without).
     const int slots = sms * bps;   // co-resident CTAs
+    std::vector<int64_t> pn(count), pz(count);
+    std::vector<int32_t> pp(count), pctas(count), porder(count);
+    for (int s = 0; s < count; ++s) {
+        pn[s] = hs[s]->N;
+        pz[s] = hs[s]->nnz;
+        pp[s] = hs[s]->precond;
+    }
+    int32_t teams = 0, grid = 0, nbig = 0;
+    if (int rcp = mlbicgstab_batch_plan(pn.data(), pz.data(), pp.data(), count, h0->batch_team, slots, pctas.data(),
+                                        porder.data(), &nbig, &teams, &grid))
+        return rcp;
     const int team = std::max(1, std::min(h0->batch_team, slots));
-    std::vector<double> w(count);
-    double wsum = 0.0;
-    for (int s = 0; s < count; ++s) {
-        w[s] = (double)(hs[s]->nnz + hs[s]->N) * std::cbrt((double)hs[s]->N);
-        wsum += w[s];
-    }
-    std::vector<int> big, small;
-    for (int s = 0; s < count; ++s) {
-        const bool t = team > 1 && hs[s]->precond != MLB_PRECOND_ILU0 && hs[s]->N >= (int64_t)kTeamMinRows * team &&
-                       w[s] > kTeamShare * wsum / slots;
-        (t ? big : small).push_back(s);
-    }
-    auto by_work = [&](int a, int c) { return w[a] > w[c]; };
-    std::stable_sort(big.begin(), big.end(), by_work);
-    std::stable_sort(small.begin(), small.end(), by_work);
-    const int teams = std::min<int>((int)big.size(), slots / team);
-    const int grid = std::min(slots, teams * team + (int)small.size());
+    const std::vector<int> big(porder.begin(), porder.begin() + nbig), small(porder.begin() + nbig, porder.end());
     // workspace: [queue (256 B)] [order_big] [order_small] [team barriers]
     // [team slots] [solve barriers] [results] (copied from the host:
     // zeroes, results marked as not run) [items] [team partial sums]

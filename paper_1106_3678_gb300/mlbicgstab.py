@@ -31,6 +31,7 @@ EXPORTS = (
     "mlbicgstab_set_n", "mlbicgstab_next_n", "mlbicgstab_solve_sequence",
     "mlbicgstab_autotune", "mlbicgstab_spmv_qdot_async", "mlbicgstab_get_perm",
     "mlbicgstab_autotune_batch", "mlbicgstab_get_tuning", "mlbicgstab_set_tuning",
+    "mlbicgstab_batch_plan",
 )
 
 
@@ -158,6 +159,9 @@ def load(path: str | None = None):
                                               C.POINTER(mlb_result), P]
     lib.mlbicgstab_autotune.restype = C.c_int
     lib.mlbicgstab_autotune.argtypes = [P, C.c_int32, C.c_int32, C.POINTER(mlb_tune_result)]
+    lib.mlbicgstab_batch_plan.restype = C.c_int
+    lib.mlbicgstab_batch_plan.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_int32, P, P,
+                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.mlbicgstab_get_tuning.restype = C.c_int
     lib.mlbicgstab_get_tuning.argtypes = [P, C.POINTER(mlb_tuning)]
     lib.mlbicgstab_set_tuning.restype = C.c_int
@@ -383,6 +387,22 @@ def mlbicgstab_autotune(h: Handle, iters: int = 20, use_cache: bool = True) -> d
     _check(load().mlbicgstab_autotune(h.ptr, int(iters), 1 if use_cache else 0, C.byref(r)),
            "mlbicgstab_autotune")
     return {f: getattr(r, f) for f, _ in r._fields_ if f != "reserved"}
+
+
+def mlbicgstab_batch_plan(N, nnz, precond, team: int = 4, slots: int = 152) -> dict:
+    """The batch work plan for systems of the given sizes (host only):
+    ctas per system, processing order, team count and grid."""
+    n = np.ascontiguousarray(N, dtype=np.int64)
+    z = np.ascontiguousarray(nnz, dtype=np.int64)
+    p = np.ascontiguousarray(precond, dtype=np.int32)
+    count = len(n)
+    ctas = np.zeros(count, dtype=np.int32)
+    order = np.zeros(count, dtype=np.int32)
+    nbig, teams, grid = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().mlbicgstab_batch_plan(n.ctypes.data, z.ctypes.data, p.ctypes.data, count, int(team),
+                                        int(slots), ctas.ctypes.data, order.ctypes.data, C.byref(nbig),
+                                        C.byref(teams), C.byref(grid)), "mlbicgstab_batch_plan")
+    return {"ctas": ctas, "order": order, "nbig": nbig.value, "teams": teams.value, "grid": grid.value}
 
 
 def mlbicgstab_get_tuning(h: Handle) -> dict:
