@@ -277,7 +277,8 @@ typedef struct {
 
 /* Result of mlbicgstab_autotune_batch. */
 typedef struct {
-    int32_t classes;      /* size classes of the batch (floor(log2 N)) */
+    int32_t classes;      /* size classes of the batch (floor(log2 N),
+                             round(nnz/N)) */
     int32_t trials;       /* batch launches timed (0 when all cached) */
     int32_t from_cache;   /* classes whose choice came from the cache */
     int32_t team;         /* CTAs per team chosen (batch_team of hs[0]) */
