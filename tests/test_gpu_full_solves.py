@@ -4,7 +4,7 @@ geometry the benchmark uses (all SMs for large N).
 
 The oracle is its multi-core build (fixed-block reductions, results
 independent of the thread count; pinned to the sequential oracle by
-tests/test_oracle_par.py).  Bars (the benchmark spec): flag 0 on both sides, the
+tests/test_oracle_par.py).  Bars: flag 0 on both sides, the
 true relative residual ||b - A x||/||b|| below tol = 1e-10 on both sides
 (the GPU's recomputed here with the oracle's product), and the GPU's x
 within 1e-8 relative of the oracle's.  The iteration counts of these long
