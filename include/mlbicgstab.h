@@ -45,7 +45,7 @@ extern "C" {
 #define MLB_ERR_TIMEOUT 4     /* a bounded device-side wait ran out; the
                                  kernel returned early and the context is
                                  still usable */
-#define MLB_ERR_UNSUPPORTED 5 /* valid request this build does not handle */
+#define MLB_ERR_UNSUPPORTED 5 /* valid request the library does not handle */
 
 /* ---- value types ------------------------------------------------------- */
 #define MLB_F64 0   /* double */
